@@ -1,0 +1,218 @@
+"""Pins of the oracle's tree build (Sec. 2.1) against the paper and plain mathematics."""
+import math
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_depth.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                a, b = line.split()
+                rows.append((int(a), int(b)))
+    return rows
+
+
+def test_depth_matches_table1():
+    # Sec. 3.2.1, Table 1: N = 500000, the L column for every N_ll.
+    for n_ll, L in _table1():
+        assert oracle.depth(500000, n_ll) == L
+
+
+def test_depth_rule_small_and_exact_boundaries():
+    assert oracle.depth(1, 12) == 1          # L >= 1 always
+    assert oracle.depth(11, 12) == 1
+    assert oracle.depth(24, 12) == 2         # 24 / 2 = 12 is not below 12
+    assert oracle.depth(23, 12) == 1
+    assert oracle.depth(4096, 12) == 9
+    assert oracle.depth(4194304, 12) == 19
+    assert oracle.depth(100_000_000, 12) == 23
+
+
+def test_i128_to_double_is_round_to_nearest_even():
+    rng = random.Random(5)
+    vals = [0, 1, -1, 2**53 + 1, 2**53 + 3, -(2**53 + 1), 2**100 + 2**47, 2**100 + 2**47 + 1,
+            -(2**120 + 2**67), 2**126 - 1, -(2**126)]
+    for _ in range(2000):
+        v = rng.getrandbits(rng.randrange(1, 127))
+        vals.append(v if rng.random() < 0.5 else -v)
+    for _ in range(500):  # exact ties: 53 significant bits followed by a single half-ulp bit
+        shift = rng.randrange(1, 70)
+        v = ((rng.getrandbits(52) | (1 << 52)) << shift) | (1 << (shift - 1))
+        vals.append(v if rng.random() < 0.5 else -v)
+    for v in vals:
+        assert oracle.i128_to_double(v) == float(v), v  # Python's int -> float is correctly rounded
+
+
+@pytest.fixture(scope="module")
+def small_tree():
+    x, m, h = synth.make_particles("plummer", 3000, synth.seed_for(9, 1), "loguniform10")
+    return x, m, h, oracle.OracleTree(x, m, h, n_ll=12)
+
+
+def test_fixed_point_definition(small_tree):
+    x, m, h, T = small_tree
+    P = T.fixed()
+    p = m[:, None] * x                                   # RN(m * x), float64
+    for d in range(3):
+        E = math.frexp(float(np.abs(p[:, d]).max()))[1]
+        assert E == T.E[d]
+        for i in range(0, len(m), 37):
+            exact = round(Fraction(float(p[i, d])) * Fraction(2) ** (62 - E))   # half to even
+            assert P[i, 1 + d] == exact
+    Em = math.frexp(float(m.max()))[1]
+    assert Em == T.Em
+    for i in range(0, len(m), 37):
+        assert P[i, 0] == round(Fraction(float(m[i])) * Fraction(2) ** (62 - Em))
+
+
+def _i128(pair):
+    lo, hi = int(pair[0]), int(pair[1])
+    return (hi << 64) + (lo & ((1 << 64) - 1))
+
+
+def test_sums_compose_and_com_is_exact(small_tree):
+    x, m, h, T = small_tree
+    nd = T.nodes()
+    P = T.fixed()
+    perm = T.perm()
+    # root sums = sum over all particles
+    for k in range(4):
+        assert _i128(nd["sums"][1, k]) == int(sum(int(v) for v in P[:, k]))
+    for n in range(1, 1 << T.L):
+        for k in range(4):
+            assert _i128(nd["sums"][n, k]) == _i128(nd["sums"][2 * n, k]) + _i128(nd["sums"][2 * n + 1, k])
+    # COM = RN(RN(S) 2^(E-62) / (RN(M) 2^(Em-62))) with Python's correctly rounded int->float
+    for n in range(1, 2 << T.L):
+        if nd["count"][n] == 0:
+            continue
+        M = _i128(nd["sums"][n, 0])
+        for d in range(3):
+            S = _i128(nd["sums"][n, 1 + d])
+            com = math.ldexp(float(S), T.E[d] - 62) / math.ldexp(float(M), T.Em - 62)
+            assert com == nd["com"][n, d]
+        # the cell's particle set sums to its node sums
+        f, c = nd["first"][n], nd["count"][n]
+        assert _i128(nd["sums"][n, 0]) == int(sum(int(v) for v in P[perm[f:f + c], 0]))
+
+
+def test_every_split_is_longest_side_through_com(small_tree):
+    # Sec. 2.1.3 / 2.1.4 checked by brute force on the particle sets of every cell.
+    x, m, h, T = small_tree
+    nd = T.nodes()
+    perm = T.perm()
+    for n in range(1, 1 << T.L):
+        f, c = nd["first"][n], nd["count"][n]
+        if c == 0:
+            assert nd["count"][2 * n] == 0 and nd["count"][2 * n + 1] == 0
+            continue
+        pts = x[perm[f:f + c]]
+        lo, hi = pts.min(0), pts.max(0)
+        assert np.array_equal(lo, nd["bmin"][n]) and np.array_equal(hi, nd["bmax"][n])
+        ext = hi - lo
+        ax = int(np.argmax(ext))                       # first maximum = lowest axis on ties
+        assert nd["axis"][n] == ax
+        s = nd["split"][n]
+        assert s == nd["com"][n, ax]
+        fl, cl = nd["first"][2 * n], nd["count"][2 * n]
+        fr, cr = nd["first"][2 * n + 1], nd["count"][2 * n + 1]
+        assert fl == f and fr == f + cl and cl + cr == c
+        assert np.all(x[perm[fl:fl + cl], ax] < s)
+        assert np.all(x[perm[fr:fr + cr], ax] >= s)
+        assert nd["H"][n] == ext.max()
+        assert np.array_equal(nd["rg"][n], 0.5 * (lo + hi))
+
+
+def test_labelling_identities(small_tree):
+    # Sec. 2.1.5: children 2n, 2n+1; level floor(log2 n); level k spans 2^k .. 2^(k+1)-1.
+    x, m, h, T = small_tree
+    nd = T.nodes()
+    L = T.L
+    assert nd["first"].shape[0] == 2 << L              # 2^(L+1) - 1 nodes plus the unused 0
+    for k in range(L + 1):
+        lvl = range(1 << k, 2 << k)
+        assert all(int(math.floor(math.log2(n))) == k for n in lvl)
+        assert sum(nd["count"][n] for n in lvl) == T.N  # every level covers every particle once
+        # 2^p - 2 descendants of a level-k cell, p = number of levels >= k
+        p = L + 1 - k
+        desc = sum(1 << j for j in range(1, p))
+        assert desc == 2**p - 2
+
+
+def test_quadrupole_eq2_equals_eq1(small_tree):
+    # Eq. 2 (shift-up) reproduces Eq. 1 summed directly over all particles of the parent.
+    x, m, h, T = small_tree
+    nd = T.nodes()
+    perm = T.perm()
+    for n in range(1, 2 << T.L):
+        c = nd["count"][n]
+        if c == 0:
+            continue
+        f = nd["first"][n]
+        idx = perm[f:f + c]
+        d = x[idx] - nd["com"][n]
+        Qf = 3 * np.einsum("k,ki,kj->ij", m[idx], d, d) - np.eye(3) * np.sum(m[idx] * np.einsum("ki,ki->k", d, d))
+        q6 = np.array([Qf[0, 0], Qf[0, 1], Qf[0, 2], Qf[1, 1], Qf[1, 2], Qf[2, 2]])
+        scale = np.sum(m[idx] * np.einsum("ki,ki->k", d, d)) + 1e-300
+        assert np.max(np.abs(nd["Q"][n] - q6)) <= 1e-11 * scale
+        assert abs(nd["Q"][n][0] + nd["Q"][n][3] + nd["Q"][n][5]) <= 1e-11 * scale   # traceless
+
+
+def test_radii(small_tree):
+    # Sec. 2.3.1: h_node(A) encloses every kernel of A, h_node_int(B) every particle of B.
+    x, m, h, T = small_tree
+    nd = T.nodes()
+    perm = T.perm()
+    leaf0 = 1 << T.L
+    for n in range(1, 2 << T.L):
+        c = nd["count"][n]
+        if c == 0:
+            continue
+        f = nd["first"][n]
+        idx = perm[f:f + c]
+        dv = x[idx] - nd["rg"][n]
+        dist = np.sqrt((dv[:, 0] * dv[:, 0] + dv[:, 1] * dv[:, 1]) + dv[:, 2] * dv[:, 2])
+        if n >= leaf0:
+            assert nd["hint"][n] == dist.max()
+            assert nd["hnode"][n] == np.max(dist + 2.0 * h[idx])
+        else:
+            assert nd["hint"][n] >= dist.max() * (1 - 1e-15)
+
+
+def test_input_validation():
+    x = np.zeros((4, 3))
+    m = np.ones(4)
+    h = np.ones(4)
+    with pytest.raises(ValueError):
+        oracle.OracleTree(np.array([[np.nan, 0, 0]] * 4), m, h)
+    with pytest.raises(ValueError):
+        oracle.OracleTree(x, -m, h)
+    with pytest.raises(ValueError):
+        oracle.OracleTree(x, m, 0 * h)
+    with pytest.raises(ValueError):
+        oracle.OracleTree(x[:0], m[:0], h[:0])
+
+
+def test_degenerate_inputs_build():
+    # single particle, two particles, all particles at one point
+    for N in (1, 2, 3):
+        x, m, h = synth.make_particles("cube", N, 3, "equal")
+        T = oracle.OracleTree(x, m, h)
+        assert T.L == 1 and T.nodes()["count"][1] == N
+    x = np.ones((50, 3))
+    T = oracle.OracleTree(x, np.ones(50), np.ones(50))
+    nd = T.nodes()
+    assert nd["count"][1] == 50 and nd["H"][1] == 0.0
+    leaf0 = 1 << T.L
+    assert sum(nd["count"][leaf0:]) == 50
