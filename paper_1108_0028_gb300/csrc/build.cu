@@ -1,0 +1,1168 @@
+// Tree build (Sec. 2.1) on the GPU.
+//
+// Data flow (all in device memory, one stream):
+//   ingest      validate inputs; per-axis fixed-point exponents; SoA records (x, y, z, the four
+//               62-bit fixed-point integers of m and m x, original index) in buffer 0; root sums
+//   level pass  for every cell larger than kTcta particles: per-chunk counts and partial sums of
+//               the left part (reduce), per-cell chunk offsets and both children's exact sums,
+//               boxes, centres of mass and splits (finalize), then a stable scatter of the
+//               chunk's records into the other buffer (scatter).  Cells that become small are
+//               queued as subtree roots.
+//   subtree     one CTA per queued root loads its <= kTcta records into shared memory and
+//               splits them level by level down to L (flags, block scan, stable move, exact
+//               children reductions), then writes the particles in tree order.
+//   leaves      per non-empty ll-cell: Eq. 1 quadrupole, radii h_node_int and h_node, float32
+//               cell-relative copies; then an arrival-counter climb computes every parent by
+//               Eq. 2 as soon as both of its children are done.
+// Every comparison of coordinates runs on order-preserving int64 keys; centre-of-mass sums are
+// exact 128-bit integer sums, so the particle sets of all cells are a pure function of the
+// input (Sec. 2.1.3-2.1.4 with the exact centre of mass).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "rcb_internal.cuh"
+
+namespace rcb {
+namespace {
+
+struct Red {  // exact reduction of a particle set
+    i128 S[4];
+    int64_t lo[3], hi[3];
+    int32_t n;
+};
+
+__device__ inline void red_init(Red &r) {
+    for (int k = 0; k < 4; ++k) r.S[k] = 0;
+    for (int d = 0; d < 3; ++d) { r.lo[d] = INT64_MAX; r.hi[d] = INT64_MIN; }
+    r.n = 0;
+}
+
+__device__ inline void red_add_particle(Red &r, const int64_t P[4], const int64_t key[3]) {
+    for (int k = 0; k < 4; ++k) r.S[k] += (i128)P[k];
+    for (int d = 0; d < 3; ++d) {
+        r.lo[d] = min(r.lo[d], key[d]);
+        r.hi[d] = max(r.hi[d], key[d]);
+    }
+    r.n += 1;
+}
+
+__device__ inline void red_merge(Red &a, const Red &b) {
+    for (int k = 0; k < 4; ++k) a.S[k] += b.S[k];
+    for (int d = 0; d < 3; ++d) {
+        a.lo[d] = min(a.lo[d], b.lo[d]);
+        a.hi[d] = max(a.hi[d], b.hi[d]);
+    }
+    a.n += b.n;
+}
+
+__device__ inline int64_t shfl_xor_ll(int64_t v, int m) {
+    return (int64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, m);
+}
+__device__ inline int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__device__ inline int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+__device__ inline void red_warp_allreduce(Red &r) {
+    for (int m = 16; m >= 1; m >>= 1) {
+        Red o;
+        for (int k = 0; k < 4; ++k) o.S[k] = shfl_xor_i128(r.S[k], m);
+        for (int d = 0; d < 3; ++d) {
+            o.lo[d] = shfl_xor_ll(r.lo[d], m);
+            o.hi[d] = shfl_xor_ll(r.hi[d], m);
+        }
+        o.n = __shfl_xor_sync(0xffffffffu, r.n, m);
+        red_merge(r, o);
+    }
+}
+
+// Block-wide reduction; every thread gets the result.  `scratch` holds blockDim/32 Reds.
+__device__ void red_block(Red &r, Red *scratch) {
+    red_warp_allreduce(r);
+    int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) scratch[w] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Red t = scratch[0];
+        for (int i = 1; i < nw; ++i) red_merge(t, scratch[i]);
+        scratch[0] = t;
+    }
+    __syncthreads();
+    r = scratch[0];
+    __syncthreads();
+}
+
+struct Ctx {  // device-side view of the tree arrays used by the build kernels
+    int L;
+    int64_t capN;
+    int64_t cap_big, cap_roots;
+    int *status;
+    const int *E;
+    int32_t *nfirst, *ncount, *naxis;
+    double *nsplit;
+    int64_t *nsplitkey;
+    i128 *nS;
+    int64_t *nbmin, *nbmax;
+    double *nmass, *ncom, *nrg, *nH;
+};
+
+// Write a cell created at `level` from its exact reduction: sums, box, centre of mass,
+// geometric centre, size and (above the lowest level) the split of Sec. 2.1.3.
+__device__ void write_cell(const Ctx &c, int node, int level, int first, const Red &r) {
+    c.nfirst[node] = first;
+    c.ncount[node] = r.n;
+    if (r.n == 0) return;
+    for (int k = 0; k < 4; ++k) c.nS[4 * (int64_t)node + k] = r.S[k];
+    double ext[3];
+    double H = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        c.nbmin[3 * (int64_t)node + d] = r.lo[d];
+        c.nbmax[3 * (int64_t)node + d] = r.hi[d];
+        double lo = dkey_inv(r.lo[d]), hi = dkey_inv(r.hi[d]);
+        c.ncom[3 * (int64_t)node + d] = com_from_sums(r.S[1 + d], c.E[d], r.S[0], c.E[3]);
+        c.nrg[3 * (int64_t)node + d] = __dmul_rn(0.5, __dadd_rn(lo, hi));
+        ext[d] = __dsub_rn(hi, lo);
+        H = fmax(H, ext[d]);
+    }
+    c.nmass[node] = mass_from_sum(r.S[0], c.E[3]);
+    c.nH[node] = H;
+    if (level < c.L) {
+        int ax = 0;
+        double best = -1.0;
+        for (int d = 0; d < 3; ++d)
+            if (ext[d] > best) { best = ext[d]; ax = d; }  // ties -> lowest axis
+        double s = c.ncom[3 * (int64_t)node + ax];
+        c.naxis[node] = ax;
+        c.nsplit[node] = s;
+        c.nsplitkey[node] = dkey(s);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Ingest.
+
+__global__ void k_ingest_scan(const double *__restrict__ x, const double *__restrict__ m,
+                              const double *__restrict__ h, int64_t N, int *status,
+                              unsigned long long *maxbits) {
+    unsigned long long mx[4] = {0, 0, 0, 0};
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double mi = m[i], hi = h[i];
+        if (!isfinite(mi) || !(mi > 0.0) || !isfinite(hi) || !(hi > 0.0)) bad = true;
+        for (int d = 0; d < 3; ++d) {
+            double xi = x[3 * i + d];
+            if (!isfinite(xi)) bad = true;
+            double p = fabs(__dmul_rn(mi, __dadd_rn(xi, 0.0)));
+            unsigned long long b = (unsigned long long)__double_as_longlong(p);
+            if (isfinite(p) && b > mx[d]) mx[d] = b;
+        }
+        unsigned long long bm = (unsigned long long)__double_as_longlong(mi);
+        if (mi > 0.0 && isfinite(mi) && bm > mx[3]) mx[3] = bm;
+    }
+    for (int k = 0; k < 4; ++k) {
+        unsigned long long v = mx[k];
+        for (int o = 16; o >= 1; o >>= 1) {
+            unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w > v ? w : v;
+        }
+        if ((threadIdx.x & 31) == 0 && v) atomicMax(&maxbits[k], v);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&status[ST_ERR], ERRBIT_ARG);
+}
+
+__global__ void k_exponents(const unsigned long long *maxbits, int *E) {
+    if (threadIdx.x < 4) {
+        double v = __longlong_as_double((long long)maxbits[threadIdx.x]);
+        int e = 0;
+        if (v != 0.0) (void)frexp(v, &e);
+        E[threadIdx.x] = e;
+    }
+}
+
+__global__ void k_ingest_write(const double *__restrict__ x, const double *__restrict__ m, int64_t N, int64_t capN,
+                               const int *E, double *bx, double *by, double *bz, int64_t *bP, int32_t *bidx,
+                               Red *partials, int *status) {
+    __shared__ Red scratch[32];
+    Red r;
+    red_init(r);
+    int sh[4] = {62 - E[0], 62 - E[1], 62 - E[2], 62 - E[3]};
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double mi = m[i];
+        double xc[3];
+        int64_t P[4], key[3];
+        for (int d = 0; d < 3; ++d) {
+            xc[d] = __dadd_rn(x[3 * i + d], 0.0);  // -0 -> +0
+            key[d] = dkey(xc[d]);
+            P[1 + d] = fixed_point(__dmul_rn(mi, xc[d]), sh[d]);
+        }
+        P[0] = fixed_point(mi, sh[3]);
+        if (P[0] < 1) bad = true;
+        bx[i] = xc[0];
+        by[i] = xc[1];
+        bz[i] = xc[2];
+        for (int k = 0; k < 4; ++k) bP[k * capN + i] = P[k];
+        bidx[i] = (int32_t)i;
+        red_add_particle(r, P, key);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&status[ST_ERR], ERRBIT_FIXED);
+    red_block(r, scratch);
+    if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// Root cell (level 0) from the ingest partials; queue it as a large cell or a subtree root.
+__global__ void k_root_finalize(Ctx c, const Red *partials, int nparts, int32_t *big_list, int32_t *roots) {
+    __shared__ Red scratch[32];
+    Red r;
+    red_init(r);
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) red_merge(r, partials[i]);
+    red_block(r, scratch);
+    if (threadIdx.x == 0) {
+        write_cell(c, 1, 0, 0, r);
+        if (r.n > kTcta && c.L > 0) {
+            big_list[0] = 1;
+            c.status[ST_NBIG] = 1;
+        } else {
+            roots[0] = (1 << 1) | 0;
+            c.status[ST_NROOTS] = 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Level passes over large cells.
+
+struct ChunkPart {
+    i128 SL[4];
+    int64_t loL[3], hiL[3], loR[3], hiR[3];
+    int32_t nL;
+    int32_t leftoff;
+};
+
+// Chunk list of the large cells of one level (single block).
+__global__ void k_chunk_plan(const int32_t *big, int nbig, const int32_t *nfirst, const int32_t *ncount,
+                             int32_t *cell_chunk0, int4 *chunks, int *status) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nbig; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int nch = 0;
+        if (i < nbig) nch = (ncount[big[i]] + kChunk - 1) / kChunk;
+        // block exclusive scan of nch
+        int v = nch;
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) warp_tot[w] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int s = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                int t = warp_tot[k];
+                warp_tot[k] = s;
+                s += t;
+            }
+        }
+        __syncthreads();
+        int excl = carry + warp_tot[w] + v - nch;
+        if (i < nbig) {
+            int node = big[i];
+            int f = nfirst[node], cnt = ncount[node];
+            cell_chunk0[i] = excl;
+            for (int k = 0; k < nch; ++k) {
+                int st = f + k * kChunk;
+                chunks[excl + k] = make_int4(node, st, min(kChunk, f + cnt - st), i);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + nch;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) status[ST_NCHUNKS] = carry;
+}
+
+// Per chunk: number of particles left of the split, their exact sums, and both sides' boxes.
+__global__ void __launch_bounds__(kChunkThreads) k_level_reduce(Ctx c, const int4 *chunks, const int *nchunks_ptr,
+                                                                const double *bx, const double *by, const double *bz,
+                                                                const int64_t *bP, ChunkPart *parts) {
+    __shared__ Red scratch[kChunkThreads / 32];
+    int nchunks = *nchunks_ptr;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        int4 cd = chunks[ch];
+        int node = cd.x, start = cd.y, cnt = cd.z;
+        int ax = c.naxis[node];
+        int64_t sk = c.nsplitkey[node];
+        Red rl, rr;
+        red_init(rl);
+        red_init(rr);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            int64_t e = start + i;
+            int64_t key[3] = {dkey(bx[e]), dkey(by[e]), dkey(bz[e])};
+            int64_t P[4];
+            for (int k = 0; k < 4; ++k) P[k] = bP[k * c.capN + e];
+            if (key[ax] < sk) red_add_particle(rl, P, key);
+            else {
+                for (int d = 0; d < 3; ++d) {
+                    rr.lo[d] = min(rr.lo[d], key[d]);
+                    rr.hi[d] = max(rr.hi[d], key[d]);
+                }
+            }
+        }
+        red_block(rl, scratch);
+        // right side: only the box is needed (its sums are parent minus left)
+        for (int m = 16; m >= 1; m >>= 1)
+            for (int d = 0; d < 3; ++d) {
+                rr.lo[d] = min64(rr.lo[d], shfl_xor_ll(rr.lo[d], m));
+                rr.hi[d] = max64(rr.hi[d], shfl_xor_ll(rr.hi[d], m));
+            }
+        __shared__ int64_t boxR[kChunkThreads / 32][6];
+        int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0)
+            for (int d = 0; d < 3; ++d) { boxR[w][d] = rr.lo[d]; boxR[w][3 + d] = rr.hi[d]; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ChunkPart p;
+            for (int k = 0; k < 4; ++k) p.SL[k] = rl.S[k];
+            for (int d = 0; d < 3; ++d) {
+                p.loL[d] = rl.lo[d];
+                p.hiL[d] = rl.hi[d];
+                int64_t lo = INT64_MAX, hi = INT64_MIN;
+                for (int k = 0; k < kChunkThreads / 32; ++k) {
+                    lo = min(lo, boxR[k][d]);
+                    hi = max(hi, boxR[k][3 + d]);
+                }
+                p.loR[d] = lo;
+                p.hiR[d] = hi;
+            }
+            p.nL = rl.n;
+            p.leftoff = 0;
+            parts[ch] = p;
+        }
+        __syncthreads();
+    }
+}
+
+// Per large cell (one warp each): chunk offsets, both children, and their classification.
+__global__ void k_level_finalize(Ctx c, int level, const int32_t *big, int nbig, const int32_t *cell_chunk0,
+                                 const int *nchunks_ptr, ChunkPart *parts, int32_t *big_next, int32_t *roots,
+                                 int parity_next) {
+    int lane = threadIdx.x & 31;
+    int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    int nchunks = *nchunks_ptr;
+    for (int i = gw; i < nbig; i += nw) {
+        int node = big[i];
+        int f = c.nfirst[node], cnt = c.ncount[node];
+        int c0 = cell_chunk0[i];
+        int nch = (cnt + kChunk - 1) / kChunk;
+        if (c0 + nch > nchunks) {  // inconsistent plan: report, do not touch memory
+            if (lane == 0) atomicOr(&c.status[ST_ERR], ERRBIT_STATE);
+            continue;
+        }
+        Red L;
+        red_init(L);
+        int64_t loR[3], hiR[3];
+        for (int d = 0; d < 3; ++d) { loR[d] = INT64_MAX; hiR[d] = INT64_MIN; }
+        int run = 0;  // left particles before the current group of 32 chunks
+        for (int base = 0; base < nch; base += 32) {
+            int k = base + lane;
+            int nl = 0;
+            if (k < nch) {
+                const ChunkPart &p = parts[c0 + k];
+                nl = p.nL;
+                Red t;
+                for (int q = 0; q < 4; ++q) t.S[q] = p.SL[q];
+                for (int d = 0; d < 3; ++d) {
+                    t.lo[d] = p.loL[d];
+                    t.hi[d] = p.hiL[d];
+                    loR[d] = min(loR[d], p.loR[d]);
+                    hiR[d] = max(hiR[d], p.hiR[d]);
+                }
+                t.n = nl;
+                red_merge(L, t);
+            }
+            int v = nl;
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            if (k < nch) parts[c0 + k].leftoff = run + v - nl;
+            run += __shfl_sync(0xffffffffu, v, 31);
+        }
+        red_warp_allreduce(L);
+        for (int m = 16; m >= 1; m >>= 1)
+            for (int d = 0; d < 3; ++d) {
+                loR[d] = min64(loR[d], shfl_xor_ll(loR[d], m));
+                hiR[d] = max64(hiR[d], shfl_xor_ll(hiR[d], m));
+            }
+        if (lane == 0) {
+            Red R;
+            for (int q = 0; q < 4; ++q) R.S[q] = c.nS[4 * (int64_t)node + q] - L.S[q];
+            for (int d = 0; d < 3; ++d) { R.lo[d] = loR[d]; R.hi[d] = hiR[d]; }
+            R.n = cnt - L.n;
+            write_cell(c, 2 * node, level + 1, f, L);
+            write_cell(c, 2 * node + 1, level + 1, f + L.n, R);
+            int kids[2] = {2 * node, 2 * node + 1};
+            int kn[2] = {L.n, R.n};
+            for (int s = 0; s < 2; ++s) {
+                if (kn[s] == 0) continue;
+                if (kn[s] > kTcta && level + 1 < c.L) {
+                    int slot = atomicAdd(&c.status[ST_NBIG], 1);
+                    if (slot < c.cap_big) big_next[slot] = kids[s];
+                    else atomicOr(&c.status[ST_ERR], ERRBIT_STATE);
+                } else {
+                    int slot = atomicAdd(&c.status[ST_NROOTS], 1);
+                    if (slot < c.cap_roots) roots[slot] = (kids[s] << 1) | parity_next;
+                    else atomicOr(&c.status[ST_ERR], ERRBIT_STATE);
+                }
+            }
+        }
+    }
+}
+
+// Stable scatter of each chunk's records to their children's ranges in the other buffer.
+__global__ void __launch_bounds__(kChunkThreads) k_level_scatter(Ctx c, const int4 *chunks, const int *nchunks_ptr,
+                                                                 const ChunkPart *parts, const double *bx,
+                                                                 const double *by, const double *bz,
+                                                                 const int64_t *bP, const int32_t *bidx,
+                                                                 double *ox, double *oy, double *oz, int64_t *oP,
+                                                                 int32_t *oidx) {
+    __shared__ int wsum[kChunkThreads / 32];
+    int nchunks = *nchunks_ptr;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int kPer = kChunk / kChunkThreads;  // elements per thread (8)
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        int4 cd = chunks[ch];
+        int node = cd.x, start = cd.y, cnt = cd.z;
+        int ax = c.naxis[node];
+        int64_t sk = c.nsplitkey[node];
+        int f = c.nfirst[node];
+        int nLcell = c.ncount[2 * node];
+        int leftoff = parts[ch].leftoff;
+        int rightoff = (start - f) - leftoff;
+        // element order: warp w owns [w*256, w*256+256), group j = 32 consecutive elements
+        unsigned masks[kPer];
+        int wcount = 0;
+        for (int j = 0; j < kPer; ++j) {
+            int i = w * 32 * kPer + j * 32 + lane;
+            bool left = false;
+            if (i < cnt) {
+                int64_t e = start + i;
+                double v = ax == 0 ? bx[e] : (ax == 1 ? by[e] : bz[e]);
+                left = dkey(v) < sk;
+            }
+            masks[j] = __ballot_sync(0xffffffffu, left);
+            wcount += __popc(masks[j]);
+        }
+        if (lane == 0) wsum[w] = wcount;
+        __syncthreads();
+        int before = 0;
+        for (int k = 0; k < w; ++k) before += wsum[k];
+        __syncthreads();
+        unsigned lt = (1u << lane) - 1u;
+        int run = before;
+        for (int j = 0; j < kPer; ++j) {
+            int i = w * 32 * kPer + j * 32 + lane;
+            bool left = (masks[j] >> lane) & 1u;
+            int lrank = run + __popc(masks[j] & lt);
+            run += __popc(masks[j]);
+            if (i < cnt) {
+                int64_t e = start + i;
+                int64_t dst = left ? (int64_t)f + leftoff + lrank : (int64_t)f + nLcell + rightoff + (i - lrank);
+                ox[dst] = bx[e];
+                oy[dst] = by[e];
+                oz[dst] = bz[e];
+                for (int k = 0; k < 4; ++k) oP[k * c.capN + dst] = bP[k * c.capN + e];
+                oidx[dst] = bidx[e];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Subtrees in shared memory.
+
+struct SubtreeSmem {
+    double x[kTcta], y[kTcta], z[kTcta];
+    int64_t P[4][kTcta];
+    int32_t idx[kTcta];
+    uint16_t perm[2][kTcta];
+    uint16_t cellOf[2][kTcta];
+    uint16_t scan[kTcta + 1];
+    int32_t cnode[2][kTcta];
+    uint16_t cfirst[2][kTcta], ccount[2][kTcta];
+    int64_t csplit[kTcta];
+    int8_t caxis[kTcta];
+    uint16_t newidx[2 * kTcta];
+    int warp_tot[33];
+    int nkids;
+};
+
+// Block exclusive scan of per-thread value v; returns this thread's exclusive prefix and writes
+// the block total to *total.  warp_tot holds 33 ints.
+__device__ int block_excl_scan(int v, int *warp_tot, int *total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    __syncthreads();
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            int t = warp_tot[k];
+            warp_tot[k] = s;
+            s += t;
+        }
+        warp_tot[32] = s;
+    }
+    __syncthreads();
+    int excl = warp_tot[w] + incl - v;
+    *total = warp_tot[32];
+    __syncthreads();
+    return excl;
+}
+
+__device__ inline void load_particle(const SubtreeSmem &s, int home, int64_t P[4], int64_t key[3]) {
+    for (int k = 0; k < 4; ++k) P[k] = s.P[k][home];
+    key[0] = dkey(s.x[home]);
+    key[1] = dkey(s.y[home]);
+    key[2] = dkey(s.z[home]);
+}
+
+struct Bufs {
+    const double *x[2], *y[2], *z[2];
+    const int64_t *P[2];
+    const int32_t *idx[2];
+};
+
+__global__ void __launch_bounds__(kCtaThreads, 1)
+    k_subtree(Ctx c, const int32_t *roots, const int *nroots_ptr, Bufs B, const double *__restrict__ m_in,
+              const double *__restrict__ h_in, double *px, double *py, double *pz, double *pm, double *ph,
+              int32_t *pidx) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SubtreeSmem &s = *reinterpret_cast<SubtreeSmem *>(smem_raw);
+    const int nroots = *nroots_ptr;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    for (int ri = blockIdx.x; ri < nroots; ri += gridDim.x) {
+        int packed = roots[ri];
+        int root = packed >> 1, parity = packed & 1;
+        int k0 = 31 - __clz(root);
+        int gfirst = c.nfirst[root], n = c.ncount[root];
+        const double *bx = B.x[parity], *by = B.y[parity], *bz = B.z[parity];
+        const int64_t *bP = B.P[parity];
+        const int32_t *bidx = B.idx[parity];
+        if (k0 >= c.L || n > kTcta) {
+            // an ll-cell: its particles only need to reach the output arrays
+            for (int i = tid; i < n; i += nt) {
+                int64_t e = gfirst + i;
+                int32_t o = bidx[e];
+                px[e] = bx[e];
+                py[e] = by[e];
+                pz[e] = bz[e];
+                pidx[e] = o;
+                pm[e] = m_in[o];
+                ph[e] = h_in[o];
+            }
+            continue;
+        }
+        for (int i = tid; i < n; i += nt) {
+            int64_t e = gfirst + i;
+            s.x[i] = bx[e];
+            s.y[i] = by[e];
+            s.z[i] = bz[e];
+            for (int k = 0; k < 4; ++k) s.P[k][i] = bP[k * c.capN + e];
+            s.idx[i] = bidx[e];
+            s.perm[0][i] = (uint16_t)i;
+            s.cellOf[0][i] = 0;
+        }
+        if (tid == 0) {
+            s.cnode[0][0] = root;
+            s.cfirst[0][0] = 0;
+            s.ccount[0][0] = (uint16_t)n;
+            s.caxis[0] = (int8_t)c.naxis[root];
+            s.csplit[0] = c.nsplitkey[root];
+            s.nkids = 1;
+        }
+        __syncthreads();
+        int cur = 0;
+        int K = 1;
+        for (int level = k0; level < c.L; ++level) {
+            const int nxt = cur ^ 1;
+            // 1. flags of the positions this thread owns (4 consecutive), block scan
+            constexpr int kPer = kTcta / kCtaThreads;
+            bool fl[kPer];
+            int cntl = 0;
+            for (int j = 0; j < kPer; ++j) {
+                int p = tid * kPer + j;
+                bool left = false;
+                if (p < n) {
+                    int ci = s.cellOf[cur][p];
+                    int home = s.perm[cur][p];
+                    int ax = s.caxis[ci];
+                    double v = ax == 0 ? s.x[home] : (ax == 1 ? s.y[home] : s.z[home]);
+                    left = dkey(v) < s.csplit[ci];
+                }
+                fl[j] = left;
+                cntl += left;
+            }
+            int total;
+            int excl = block_excl_scan(cntl, s.warp_tot, &total);
+            for (int j = 0; j < kPer; ++j) {
+                int p = tid * kPer + j;
+                if (p < n) s.scan[p] = (uint16_t)excl;
+                excl += fl[j];
+            }
+            if (tid == 0) s.scan[n] = (uint16_t)total;
+            __syncthreads();
+            // 2. children of every active cell; compact the non-empty ones
+            int nonempty_local = 0;
+            constexpr int kCellPer = 2 * kTcta / kCtaThreads;  // 8 child slots per thread
+            uint16_t cl[kCellPer];
+            for (int j = 0; j < kCellPer; ++j) {
+                int slot = tid * kCellPer + j;  // child slot = 2 * cell + side
+                uint16_t cc = 0;
+                if (slot < 2 * K) {
+                    int ci = slot >> 1;
+                    int f = s.cfirst[cur][ci], cn = s.ccount[cur][ci];
+                    int nl = s.scan[f + cn] - s.scan[f];
+                    cc = (slot & 1) ? (uint16_t)(cn - nl) : (uint16_t)nl;
+                }
+                cl[j] = cc;
+                nonempty_local += cc > 0;
+            }
+            int kexcl = block_excl_scan(nonempty_local, s.warp_tot, &total);
+            for (int j = 0; j < kCellPer; ++j) {
+                int slot = tid * kCellPer + j;
+                if (slot < 2 * K) {
+                    int ci = slot >> 1;
+                    if (cl[j] > 0) {
+                        int f = s.cfirst[cur][ci];
+                        int nl = s.scan[f + s.ccount[cur][ci]] - s.scan[f];
+                        s.newidx[slot] = (uint16_t)kexcl;
+                        s.cnode[nxt][kexcl] = 2 * s.cnode[cur][ci] + (slot & 1);
+                        s.cfirst[nxt][kexcl] = (uint16_t)((slot & 1) ? f + nl : f);
+                        s.ccount[nxt][kexcl] = cl[j];
+                        ++kexcl;
+                    } else {
+                        // an empty child: record its placement only
+                        int node = 2 * s.cnode[cur][ci] + (slot & 1);
+                        int f = s.cfirst[cur][ci];
+                        int nl = s.scan[f + s.ccount[cur][ci]] - s.scan[f];
+                        c.nfirst[node] = gfirst + ((slot & 1) ? f + nl : f);
+                    }
+                }
+            }
+            const int K2 = total;
+            __syncthreads();
+            // 3. stable move into the next order
+            for (int j = 0; j < kPer; ++j) {
+                int p = tid * kPer + j;
+                if (p < n) {
+                    int ci = s.cellOf[cur][p];
+                    int f = s.cfirst[cur][ci], cn = s.ccount[cur][ci];
+                    int base = s.scan[f];
+                    int nl = s.scan[f + cn] - base;
+                    int r = s.scan[p] - base;
+                    int np = fl[j] ? f + r : f + nl + (p - f - r);
+                    s.perm[nxt][np] = s.perm[cur][p];
+                    s.cellOf[nxt][np] = s.newidx[2 * ci + (fl[j] ? 0 : 1)];
+                }
+            }
+            __syncthreads();
+            // 4. exact reductions of the children: a warp for large ones, a thread for small ones
+            for (int ci = warp; ci < K2; ci += nwarps) {
+                int cn = s.ccount[nxt][ci];
+                if (cn <= 32) continue;
+                int f = s.cfirst[nxt][ci];
+                Red r;
+                red_init(r);
+                for (int q = lane; q < cn; q += 32) {
+                    int64_t P[4], key[3];
+                    load_particle(s, s.perm[nxt][f + q], P, key);
+                    red_add_particle(r, P, key);
+                }
+                red_warp_allreduce(r);
+                if (lane == 0) {
+                    int node = s.cnode[nxt][ci];
+                    write_cell(c, node, level + 1, gfirst + f, r);
+                    if (level + 1 < c.L) {
+                        s.caxis[ci] = (int8_t)c.naxis[node];
+                        s.csplit[ci] = c.nsplitkey[node];
+                    }
+                }
+            }
+            for (int ci = tid; ci < K2; ci += nt) {
+                int cn = s.ccount[nxt][ci];
+                if (cn > 32) continue;
+                int f = s.cfirst[nxt][ci];
+                Red r;
+                red_init(r);
+                for (int q = 0; q < cn; ++q) {
+                    int64_t P[4], key[3];
+                    load_particle(s, s.perm[nxt][f + q], P, key);
+                    red_add_particle(r, P, key);
+                }
+                int node = s.cnode[nxt][ci];
+                write_cell(c, node, level + 1, gfirst + f, r);
+                if (level + 1 < c.L) {
+                    s.caxis[ci] = (int8_t)c.naxis[node];
+                    s.csplit[ci] = c.nsplitkey[node];
+                }
+            }
+            __syncthreads();
+            cur = nxt;
+            K = K2;
+        }
+        // write the particles in tree order
+        for (int p = tid; p < n; p += nt) {
+            int home = s.perm[cur][p];
+            int64_t e = gfirst + p;
+            int32_t o = s.idx[home];
+            px[e] = s.x[home];
+            py[e] = s.y[home];
+            pz[e] = s.z[home];
+            pidx[e] = o;
+            pm[e] = m_in[o];
+            ph[e] = h_in[o];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Sinks, leaf moments and the bottom-up pass.
+
+__global__ void k_count_sinks(const int32_t *ncount, int64_t leaf0, int64_t nleaves, int32_t *flags) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nleaves; j += (int64_t)gridDim.x * blockDim.x)
+        flags[j] = ncount[leaf0 + j] > 0;
+}
+
+__global__ void k_write_sinks(const int32_t *flags, const int32_t *pos, int64_t leaf0, int64_t nleaves,
+                              int32_t *sinks, int32_t *sink_of_leaf) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nleaves; j += (int64_t)gridDim.x * blockDim.x) {
+        if (flags[j]) {
+            sinks[pos[j]] = (int32_t)(leaf0 + j);
+            sink_of_leaf[j] = pos[j];
+        } else {
+            sink_of_leaf[j] = -1;
+        }
+    }
+}
+
+struct LeafCtx {
+    int32_t *nfirst, *ncount;
+    double *nmass, *ncom, *nrg, *nH, *nhint, *nhnode, *nQ;
+    int32_t *narrive;
+    const double *px, *py, *pz, *pm, *ph;
+    float4 *p32;
+    float *h32;
+};
+
+// Eq. 2 and the parent's enclosing radius from its non-empty children.
+__device__ void parent_moments(const LeafCtx &c, int P) {
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    double hint = 0.0;
+    double cp[3] = {__ldcg(&c.ncom[3 * (int64_t)P]), __ldcg(&c.ncom[3 * (int64_t)P + 1]), __ldcg(&c.ncom[3 * (int64_t)P + 2])};
+    double gp[3] = {__ldcg(&c.nrg[3 * (int64_t)P]), __ldcg(&c.nrg[3 * (int64_t)P + 1]), __ldcg(&c.nrg[3 * (int64_t)P + 2])};
+    for (int C = 2 * P; C <= 2 * P + 1; ++C) {
+        if (__ldcg(&c.ncount[C]) == 0) continue;
+        double dx[3];
+        for (int d = 0; d < 3; ++d) dx[d] = __dsub_rn(__ldcg(&c.ncom[3 * (int64_t)C + d]), cp[d]);
+        double dr2 = __dadd_rn(__dadd_rn(__dmul_rn(dx[0], dx[0]), __dmul_rn(dx[1], dx[1])), __dmul_rn(dx[2], dx[2]));
+        double MC = __ldcg(&c.nmass[C]);
+        double tM = __dmul_rn(3.0, MC);
+        int k = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = i; j < 3; ++j, ++k) {
+                double v = __ldcg(&c.nQ[6 * (int64_t)C + k]) + tM * dx[i] * dx[j];
+                if (i == j) v -= MC * dr2;
+                Q[k] += v;
+            }
+        double r = __dsqrt_rn(dist2_rn(gp[0], gp[1], gp[2], __ldcg(&c.nrg[3 * (int64_t)C]), __ldcg(&c.nrg[3 * (int64_t)C + 1]),
+                                       __ldcg(&c.nrg[3 * (int64_t)C + 2])));
+        r = __dadd_rn(r, __ldcg(&c.nhint[C]));
+        hint = fmax(hint, r);
+    }
+    for (int k = 0; k < 6; ++k) c.nQ[6 * (int64_t)P + k] = Q[k];
+    c.nhint[P] = hint;
+    c.nhnode[P] = 0.0;
+}
+
+// One thread per sink: Eq. 1, radii, float32 copies; then climb while this thread is the
+// second child to finish.
+__global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsinks) return;
+    int n = sinks[s];
+    int f = c.nfirst[n], cnt = c.ncount[n];
+    double com[3] = {c.ncom[3 * (int64_t)n], c.ncom[3 * (int64_t)n + 1], c.ncom[3 * (int64_t)n + 2]};
+    double rg[3] = {c.nrg[3 * (int64_t)n], c.nrg[3 * (int64_t)n + 1], c.nrg[3 * (int64_t)n + 2]};
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    double hint = 0.0, hnode = 0.0;
+    for (int a = f; a < f + cnt; ++a) {
+        double x = c.px[a], y = c.py[a], z = c.pz[a], m = c.pm[a], h = c.ph[a];
+        double dx[3] = {__dsub_rn(x, com[0]), __dsub_rn(y, com[1]), __dsub_rn(z, com[2])};
+        double dr2 = __dadd_rn(__dadd_rn(__dmul_rn(dx[0], dx[0]), __dmul_rn(dx[1], dx[1])), __dmul_rn(dx[2], dx[2]));
+        double tm = __dmul_rn(3.0, m);
+        int k = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = i; j < 3; ++j, ++k) {
+                double v = tm * dx[i] * dx[j];
+                if (i == j) v -= m * dr2;
+                Q[k] += v;
+            }
+        double d = __dsqrt_rn(dist2_rn(x, y, z, rg[0], rg[1], rg[2]));
+        hint = fmax(hint, d);
+        hnode = fmax(hnode, __dadd_rn(d, __dmul_rn(2.0, h)));
+        c.p32[a] = make_float4(__double2float_rn(dx[0]), __double2float_rn(dx[1]), __double2float_rn(dx[2]),
+                               __double2float_rn(m));
+        c.h32[a] = __double2float_rn(h);
+    }
+    for (int k = 0; k < 6; ++k) c.nQ[6 * (int64_t)n + k] = Q[k];
+    c.nhint[n] = hint;
+    c.nhnode[n] = hnode;
+    // climb
+    while (n > 1) {
+        int sib = n ^ 1, P = n >> 1;
+        __threadfence();
+        if (__ldcg(&c.ncount[sib]) > 0) {
+            int old = atomicAdd(&c.narrive[P], 1);
+            if (old == 0) return;  // the sibling's thread will compute the parent
+            __threadfence();
+        }
+        parent_moments(c, P);
+        n = P;
+    }
+}
+
+struct PackCtx {
+    const int32_t *ncount;
+    const double *nmass, *ncom, *nrg, *nH, *nhint, *nQ;
+    float4 *w32a, *w32b, *mq32a, *mq32b;
+    float2 *ncomdf;
+};
+
+__global__ void k_pack_nodes(PackCtx c, int64_t nn) {
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn; n += (int64_t)gridDim.x * blockDim.x) {
+        if (n == 0 || c.ncount[n] == 0) {
+            c.w32a[n] = make_float4(0.f, 0.f, 0.f, -1.f);
+            c.w32b[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+            c.mq32a[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+            c.mq32b[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int d = 0; d < 3; ++d) c.ncomdf[3 * n + d] = make_float2(0.f, 0.f);
+            continue;
+        }
+        c.w32a[n] = make_float4(__double2float_rn(c.nrg[3 * n]), __double2float_rn(c.nrg[3 * n + 1]),
+                                __double2float_rn(c.nrg[3 * n + 2]), __double2float_rn(c.nhint[n]));
+        c.w32b[n] = make_float4(__double2float_rn(c.ncom[3 * n]), __double2float_rn(c.ncom[3 * n + 1]),
+                                __double2float_rn(c.ncom[3 * n + 2]), __double2float_rn(c.nH[n]));
+        c.mq32a[n] = make_float4(__double2float_rn(c.nmass[n]), __double2float_rn(c.nQ[6 * n]),
+                                 __double2float_rn(c.nQ[6 * n + 1]), __double2float_rn(c.nQ[6 * n + 2]));
+        c.mq32b[n] = make_float4(__double2float_rn(c.nQ[6 * n + 3]), __double2float_rn(c.nQ[6 * n + 4]),
+                                 __double2float_rn(c.nQ[6 * n + 5]), 0.f);
+        for (int d = 0; d < 3; ++d) c.ncomdf[3 * n + d] = to_df(c.ncom[3 * n + d]);
+    }
+}
+
+
+// ------------------------------------------------------------------------------------------
+// Three-phase device-wide exclusive scans (int32 -> int32 and int64 -> int64).
+constexpr int kScanThreads = 1024, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
+
+template <typename T>
+__device__ T block_scan_excl_t(T v, T *warp_tot, T *total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    __syncthreads();
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T s = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            T t = warp_tot[k];
+            warp_tot[k] = s;
+            s += t;
+        }
+        warp_tot[32] = s;
+    }
+    __syncthreads();
+    T excl = warp_tot[w] + incl - v;
+    *total = warp_tot[32];
+    __syncthreads();
+    return excl;
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const TI *in, int64_t n, TO *tile_sums) {
+    __shared__ TO wt[33];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    TO v = 0;
+    for (int j = 0; j < kScanPer; ++j)
+        if (base + j < n) v += (TO)in[base + j];
+    TO tot;
+    block_scan_excl_t<TO>(v, wt, &tot);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(TO *tile_sums, int64_t ntiles, TO *total_out) {
+    __shared__ TO wt[33];
+    __shared__ TO carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < ntiles; b += kScanThreads) {
+        int64_t i = b + threadIdx.x;
+        TO v = i < ntiles ? tile_sums[i] : (TO)0;
+        TO tot;
+        TO ex = block_scan_excl_t<TO>(v, wt, &tot);
+        if (i < ntiles) tile_sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const TI *in, int64_t n, const TO *tile_sums, TO *out) {
+    __shared__ TO wt[33];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    TO loc[kScanPer];
+    TO v = 0;
+    for (int j = 0; j < kScanPer; ++j) {
+        loc[j] = base + j < n ? (TO)in[base + j] : (TO)0;
+        v += loc[j];
+    }
+    TO tot;
+    TO ex = block_scan_excl_t<TO>(v, wt, &tot) + tile_sums[blockIdx.x];
+    for (int j = 0; j < kScanPer; ++j) {
+        if (base + j < n) out[base + j] = ex;
+        ex += loc[j];
+    }
+}
+
+Ctx make_ctx(rcb_tree *t) {
+    Ctx c;
+    c.L = t->L;
+    c.capN = t->cap_N;
+    c.cap_big = t->cap_N / (kTcta + 1) + 2;
+    c.cap_roots = t->cap_roots;
+    c.status = t->d_status;
+    c.E = t->d_E;
+    c.nfirst = t->nfirst;
+    c.ncount = t->ncount;
+    c.naxis = t->naxis;
+    c.nsplit = t->nsplit;
+    c.nsplitkey = t->nsplitkey;
+    c.nS = t->nS;
+    c.nbmin = t->nbmin;
+    c.nbmax = t->nbmax;
+    c.nmass = t->nmass;
+    c.ncom = t->ncom;
+    c.nrg = t->nrg;
+    c.nH = t->nH;
+    return c;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+int read_status(rcb_tree *t) {
+    RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status, t->d_status, ST_NWORDS * sizeof(int), cudaMemcpyDeviceToHost, t->stream));
+    RCB_CUDA_TRY(cudaStreamSynchronize(t->stream));
+    return RCB_OK;
+}
+
+}  // namespace
+
+
+size_t subtree_smem_bytes() { return sizeof(SubtreeSmem); }
+
+size_t chunk_part_bytes(int64_t cap_chunks) {
+    return std::max<size_t>((size_t)cap_chunks * sizeof(ChunkPart), (size_t)4096 * sizeof(Red));
+}
+
+int64_t scan_tmp_bytes(int64_t n) { return ((n + kScanTile - 1) / kScanTile + 2) * (int64_t)sizeof(int64_t); }
+
+int scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, void *tmp, cudaStream_t st) {
+    int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    int32_t *sums = reinterpret_cast<int32_t *>(tmp);
+    if (ntiles == 0) return cudaMemsetAsync(total, 0, sizeof(int32_t), st) == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
+    k_scan_tiles<int32_t, int32_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums);
+    k_scan_sums<int32_t><<<1, kScanThreads, 0, st>>>(sums, ntiles, total);
+    k_scan_apply<int32_t, int32_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums, out);
+    return cudaGetLastError() == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
+}
+
+int scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, void *tmp, cudaStream_t st) {
+    int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    int64_t *sums = reinterpret_cast<int64_t *>(tmp);
+    if (ntiles == 0) return cudaMemsetAsync(total, 0, sizeof(int64_t), st) == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
+    k_scan_tiles<int64_t, int64_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums);
+    k_scan_sums<int64_t><<<1, kScanThreads, 0, st>>>(sums, ntiles, total);
+    k_scan_apply<int64_t, int64_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums, out);
+    return cudaGetLastError() == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
+}
+
+int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
+    cudaStream_t st = t->stream;
+    const int64_t N = t->N;
+    const int nsm = sm_count();
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, ST_NWORDS * sizeof(int), st));
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_maxbits, 0, 4 * sizeof(unsigned long long), st));
+    RCB_CUDA_TRY(cudaMemsetAsync(t->ncount, 0, t->nn * sizeof(int32_t), st));
+    RCB_CUDA_TRY(cudaMemsetAsync(t->narrive, 0, t->nn * sizeof(int32_t), st));
+
+    int grid = (int)std::min<int64_t>((N + 255) / 256, (int64_t)nsm * 8);
+    if (grid < 1) grid = 1;
+    k_ingest_scan<<<grid, 256, 0, st>>>(x, m, h, N, t->d_status, t->d_maxbits);
+    k_exponents<<<1, 32, 0, st>>>(t->d_maxbits, t->d_E);
+    Red *partials = reinterpret_cast<Red *>(t->chunk_part);  // reused: grid <= cap_chunks
+    k_ingest_write<<<grid, 256, 0, st>>>(x, m, N, t->cap_N, t->d_E, t->bx[0], t->by[0], t->bz[0], t->bP[0],
+                                         t->bidx[0], partials, t->d_status);
+    Ctx c = make_ctx(t);
+    k_root_finalize<<<1, 256, 0, st>>>(c, partials, grid, t->big_list[0], t->roots);
+    RCB_CUDA_TRY(cudaGetLastError());
+    int rc = read_status(t);
+    if (rc) return rc;
+    if (t->h_status[ST_ERR] & (ERRBIT_ARG | ERRBIT_FIXED)) return RCB_ERR_ARG;
+
+    // level passes while large cells remain
+    int nbig = t->h_status[ST_NBIG];
+    int level = 0;
+    int cur = 0;
+    ChunkPart *parts = reinterpret_cast<ChunkPart *>(t->chunk_part);
+    while (nbig > 0) {
+        if (level >= t->L) return RCB_ERR_LIMIT;
+        int64_t bound = (N + kChunk - 1) / kChunk + nbig + 1;
+        if (bound > t->cap_chunks) return RCB_ERR_LIMIT;
+        k_chunk_plan<<<1, 1024, 0, st>>>(t->big_list[cur], nbig, t->nfirst, t->ncount, t->cell_chunk0, t->chunks,
+                                         t->d_status);
+        int g = (int)std::min<int64_t>(bound, (int64_t)nsm * 8);
+        k_level_reduce<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, t->bx[cur], t->by[cur],
+                                                    t->bz[cur], t->bP[cur], parts);
+        RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_NBIG, 0, sizeof(int), st));
+        int gf = (nbig * 32 + 255) / 256;
+        k_level_finalize<<<gf, 256, 0, st>>>(c, level, t->big_list[cur], nbig, t->cell_chunk0,
+                                             t->d_status + ST_NCHUNKS, parts, t->big_list[cur ^ 1], t->roots,
+                                             (level + 1) & 1);
+        k_level_scatter<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, parts, t->bx[cur],
+                                                     t->by[cur], t->bz[cur], t->bP[cur], t->bidx[cur], t->bx[cur ^ 1],
+                                                     t->by[cur ^ 1], t->bz[cur ^ 1], t->bP[cur ^ 1],
+                                                     t->bidx[cur ^ 1]);
+        RCB_CUDA_TRY(cudaGetLastError());
+        rc = read_status(t);
+        if (rc) return rc;
+        if (t->h_status[ST_ERR] & ERRBIT_STATE) return RCB_ERR_LIMIT;
+        nbig = t->h_status[ST_NBIG];
+        cur ^= 1;
+        ++level;
+    }
+    int nroots = t->h_status[ST_NROOTS];
+    if (nroots > t->cap_roots || (t->h_status[ST_ERR] & ERRBIT_STATE)) return RCB_ERR_LIMIT;
+    t->nroots_last = nroots;
+
+    // subtrees in shared memory
+    {
+        Bufs B;
+        for (int q = 0; q < 2; ++q) {
+            B.x[q] = t->bx[q];
+            B.y[q] = t->by[q];
+            B.z[q] = t->bz[q];
+            B.P[q] = t->bP[q];
+            B.idx[q] = t->bidx[q];
+        }
+        size_t smem = sizeof(SubtreeSmem);
+        RCB_CUDA_TRY(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int g = std::max(1, std::min(nroots, nsm));
+        k_subtree<<<g, kCtaThreads, smem, st>>>(c, t->roots, t->d_status + ST_NROOTS, B, m, h, t->px, t->py, t->pz,
+                                                t->pm, t->ph, t->pidx);
+        RCB_CUDA_TRY(cudaGetLastError());
+    }
+
+    // sinks: non-empty ll-cells in label order
+    {
+        int32_t *flags = reinterpret_cast<int32_t *>(t->near_nr);  // scratch: >= nleaves entries
+        int32_t *pos = t->sink_of_leaf;
+        int64_t leaf0 = t->nleaves;
+        int g = (int)std::min<int64_t>((t->nleaves + 255) / 256, (int64_t)nsm * 8);
+        k_count_sinks<<<g, 256, 0, st>>>(t->ncount, leaf0, t->nleaves, flags);
+        rc = scan_i32(flags, pos, t->nleaves, t->d_status + ST_NSINKS, t->scan_tmp, st);
+        if (rc) return rc;
+        k_write_sinks<<<g, 256, 0, st>>>(flags, pos, leaf0, t->nleaves, t->sinks, t->sink_of_leaf);
+        RCB_CUDA_TRY(cudaGetLastError());
+        rc = read_status(t);
+        if (rc) return rc;
+        t->nsinks = t->h_status[ST_NSINKS];
+    }
+
+    // leaf moments and bottom-up
+    {
+        LeafCtx lc;
+        lc.nfirst = t->nfirst;
+        lc.ncount = t->ncount;
+        lc.nmass = t->nmass;
+        lc.ncom = t->ncom;
+        lc.nrg = t->nrg;
+        lc.nH = t->nH;
+        lc.nhint = t->nhint;
+        lc.nhnode = t->nhnode;
+        lc.nQ = t->nQ;
+        lc.narrive = t->narrive;
+        lc.px = t->px;
+        lc.py = t->py;
+        lc.pz = t->pz;
+        lc.pm = t->pm;
+        lc.ph = t->ph;
+        lc.p32 = t->p32;
+        lc.h32 = t->h32;
+        if (t->nsinks > 0) k_leaves_up<<<(t->nsinks + 127) / 128, 128, 0, st>>>(lc, t->sinks, t->nsinks);
+        PackCtx pc;
+        pc.ncount = t->ncount;
+        pc.nmass = t->nmass;
+        pc.ncom = t->ncom;
+        pc.nrg = t->nrg;
+        pc.nH = t->nH;
+        pc.nhint = t->nhint;
+        pc.nQ = t->nQ;
+        pc.w32a = t->w32a;
+        pc.w32b = t->w32b;
+        pc.mq32a = t->mq32a;
+        pc.mq32b = t->mq32b;
+        pc.ncomdf = t->ncomdf;
+        int g = (int)std::min<int64_t>((t->nn + 255) / 256, (int64_t)nsm * 8);
+        k_pack_nodes<<<g, 256, 0, st>>>(pc, t->nn);
+        RCB_CUDA_TRY(cudaGetLastError());
+    }
+    return RCB_OK;
+}
+
+int refit_tree(rcb_tree *t, const double *x, const double *m) {
+    (void)t;
+    (void)x;
+    (void)m;
+    return RCB_ERR_STATE;
+}
+
+}  // namespace rcb

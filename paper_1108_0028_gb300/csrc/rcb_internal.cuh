@@ -1,0 +1,276 @@
+// Internal declarations of the GB300 RCB tree library: the tree object, exact-arithmetic
+// helpers shared by the build kernels, and the launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rcb.h"
+
+namespace rcb {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+constexpr int kMaxL = 28;           // deepest supported lowest level (node labels < 2^29)
+constexpr int kTcta = 2048;         // largest cell whose subtree one CTA builds in shared memory
+constexpr int kCtaThreads = 512;    // threads of that CTA
+constexpr int kChunk = 2048;        // particles per chunk in the level passes over large cells
+constexpr int kChunkThreads = 256;
+
+// Device status words (int32), zeroed at the start of each build.
+enum StatusWord {
+    ST_ERR = 0,        // bitmask of ERRBIT_*
+    ST_MAXNEAR = 1,    // largest near-list length seen by the walk
+    ST_MAXFAR = 2,     // largest far-list length seen by the walk
+    ST_FALLBACK = 3,   // walk decisions taken in FP64 after an inconclusive FP32 filter
+    ST_NBIG = 4,       // number of large cells at the next level (level passes)
+    ST_NROOTS = 5,     // subtree roots queued for the shared-memory builder
+    ST_NCHUNKS = 6,    // chunks of the current level pass
+    ST_NSINKS = 7,     // non-empty ll-cells
+    ST_NBFALLBACK = 8, // neighbour decisions taken in FP64
+    ST_LONGROWS = 9,   // neighbour rows too long for the in-warp sort
+    ST_NWORDS = 16
+};
+enum ErrBits { ERRBIT_ARG = 1, ERRBIT_LIMIT = 2, ERRBIT_FIXED = 4, ERRBIT_STATE = 8 };
+
+// ------------------------------------------------------------------------------------------
+// Exact helpers.
+
+// Order-preserving map of a float64 to int64 (valid for non-NaN values with -0 removed): lets
+// comparisons, minima and maxima of coordinates run on the integer pipes.
+__host__ __device__ inline int64_t dkey(double x) {
+#ifdef __CUDA_ARCH__
+    int64_t b = __double_as_longlong(x);
+#else
+    int64_t b;
+    __builtin_memcpy(&b, &x, 8);
+#endif
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__host__ __device__ inline double dkey_inv(int64_t k) {
+    int64_t b = k ^ ((k >> 63) & 0x7fffffffffffffffLL);
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double x;
+    __builtin_memcpy(&x, &b, 8);
+    return x;
+#endif
+}
+
+// v * 2^shift rounded to the nearest integer (ties to even), for |v| * 2^shift < 2^62, using
+// integer operations on the IEEE-754 fields only (the value is exact before rounding).
+__device__ inline int64_t fixed_point(double v, int shift) {
+    uint64_t b = (uint64_t)__double_as_longlong(v);
+    int e = (int)((b >> 52) & 0x7ff);
+    uint64_t mant = b & ((1ull << 52) - 1);
+    if (e == 0) {
+        if (mant == 0) return 0;
+        e = 1;  // subnormal
+    } else {
+        mant |= 1ull << 52;
+    }
+    int s = e - 1075 + shift;  // value = mant * 2^s
+    uint64_t r;
+    if (s >= 0) {
+        r = mant << s;  // s <= 9 because the result is below 2^62
+    } else {
+        int rs = -s;
+        if (rs > 63) {
+            r = 0;
+        } else {
+            uint64_t q = mant >> rs;
+            uint64_t rem = mant & ((1ull << rs) - 1);
+            uint64_t half = 1ull << (rs - 1);
+            if (rem > half || (rem == half && (q & 1ull))) ++q;
+            r = q;
+        }
+    }
+    return (b >> 63) ? -(int64_t)r : (int64_t)r;
+}
+
+__device__ inline double pow2i(int k) {  // exact 2^k for -1022 <= k <= 1023
+    return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
+// Nearest float64 (ties to even) of a signed 128-bit integer with |v| < 2^127.
+__device__ inline double i128_to_double(i128 v) {
+    bool neg = v < 0;
+    u128 u = neg ? (u128)(-v) : (u128)v;
+    uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+    double d;
+    if (hi == 0 && lo < (1ull << 53)) {
+        d = __ull2double_rn(lo);
+    } else {
+        int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // top bit index
+        int sh = p - 52;                                                            // >= 1
+        u128 q = u >> sh;
+        u128 rem = u & ((((u128)1) << sh) - 1);
+        u128 half = ((u128)1) << (sh - 1);
+        uint64_t m = (uint64_t)q;
+        if (rem > half || (rem == half && (m & 1ull))) ++m;
+        d = __dmul_rn(__ull2double_rn(m), pow2i(sh));
+    }
+    return neg ? -d : d;
+}
+
+// Centre-of-mass coordinate from the exact sums: RN(RN(S) 2^(E-62) / (RN(M) 2^(Em-62))).
+__device__ inline double com_from_sums(i128 S, int E, i128 M, int Em) {
+    double num = scalbn(i128_to_double(S), E - 62);
+    double den = scalbn(i128_to_double(M), Em - 62);
+    return __ddiv_rn(num, den);
+}
+__device__ inline double mass_from_sum(i128 M, int Em) { return scalbn(i128_to_double(M), Em - 62); }
+
+// |a - b|^2 rounded after every operation (no contraction).
+__device__ inline double dist2_rn(double ax, double ay, double az, double bx, double by, double bz) {
+    double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by), dz = __dsub_rn(az, bz);
+    double s = __dmul_rn(dx, dx);
+    s = __dadd_rn(s, __dmul_rn(dy, dy));
+    s = __dadd_rn(s, __dmul_rn(dz, dz));
+    return s;
+}
+
+__device__ inline i128 shfl_xor_i128(i128 v, int lane_mask) {
+    u128 u = (u128)v;
+    unsigned w0 = (unsigned)u, w1 = (unsigned)(u >> 32), w2 = (unsigned)(u >> 64), w3 = (unsigned)(u >> 96);
+    w0 = __shfl_xor_sync(0xffffffffu, w0, lane_mask);
+    w1 = __shfl_xor_sync(0xffffffffu, w1, lane_mask);
+    w2 = __shfl_xor_sync(0xffffffffu, w2, lane_mask);
+    w3 = __shfl_xor_sync(0xffffffffu, w3, lane_mask);
+    return (i128)(((u128)w3 << 96) | ((u128)w2 << 64) | ((u128)w1 << 32) | (u128)w0);
+}
+
+// Double-float (hi + lo, both float32) representation of a float64.
+__device__ inline float2 to_df(double v) {
+    float hi = __double2float_rn(v);
+    float lo = __double2float_rn(__dsub_rn(v, (double)hi));
+    return make_float2(hi, lo);
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ inline void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// Compensated accumulation of x into (s, c).
+__device__ inline void comp_add(float &s, float &c, float x) {
+    float t, e;
+    two_sum(s, x, t, e);
+    s = t;
+    c = __fadd_rn(c, e);
+}
+
+}  // namespace rcb
+
+// ------------------------------------------------------------------------------------------
+// The tree object behind the opaque rcb_tree handle.
+struct rcb_tree {
+    // allocator and stream of the last build
+    rcb_alloc_fn alloc;
+    rcb_free_fn release;
+    void *ctx;
+    cudaStream_t stream;
+
+    rcb_params params;
+    int64_t N;
+    int L;
+    int64_t nn;       // 2^(L+1) node slots
+    int64_t nleaves;  // 2^L
+    int64_t cap_N;    // capacities of the current allocation
+    int cap_L;
+
+    // status
+    int *d_status;  // [ST_NWORDS]
+    int *h_status;  // pinned mirror
+    int *d_E;       // [4] fixed-point exponents E_x, E_y, E_z, E_m
+    unsigned long long *d_maxbits;  // [4] bit patterns of max |m x_d| and max m
+
+    // ping-pong particle records of the build (SoA)
+    double *bx[2], *by[2], *bz[2];
+    int64_t *bP[2];  // [4][cap_N]: m, m x, m y, m z fixed-point integers
+    int32_t *bidx[2];
+
+    // final particles in tree order
+    double *px, *py, *pz, *pm, *ph;
+    int32_t *pidx;
+    float4 *p32;  // (x - com_leaf, m) in float32
+    float *h32;
+
+    // nodes, indexed by heap label
+    int32_t *nfirst, *ncount, *naxis;
+    double *nsplit;
+    int64_t *nsplitkey;
+    rcb::i128 *nS;          // [nn][4] exact sums
+    int64_t *nbmin, *nbmax;  // [nn][3] keys of the tight box
+    double *nmass, *ncom, *nrg, *nH, *nhint, *nhnode, *nQ;  // com, rg: [nn][3]; Q: [nn][6]
+    float4 *w32a, *w32b;     // walk packs: (rg, hint), (com, H) in float32
+    float4 *mq32a, *mq32b;   // (M, Qxx, Qxy, Qxz), (Qyy, Qyz, Qzz, 0) in float32
+    float2 *ncomdf;          // [nn][3] double-float centre of mass
+    int32_t *narrive;        // bottom-up arrival counters
+
+    // level passes over large cells
+    int32_t *big_list[2];
+    int32_t *roots;      // packed (node << 1 | parity)
+    int4 *chunks;        // (cell node, start, count, chunk index within cell)
+    int32_t *cell_chunk0;  // first chunk of each large cell (parallel to big_list)
+    void *chunk_part;    // per-chunk partial reductions
+    int64_t cap_chunks, cap_roots;
+
+    // sinks and lists
+    int32_t nsinks;
+    int32_t *sinks;       // node labels of non-empty ll-cells, in label order
+    int32_t *sink_of_leaf;  // [nleaves] sink index or -1
+    int32_t cap_near, cap_far;
+    int32_t *near_list, *far_list;  // [nsinks][cap]
+    int32_t *near_nr, *near_nn, *far_n;  // per sink: reachable, non-reachable, far counts
+    int64_t cap_lists_near, cap_lists_far;  // allocated entries
+
+    // gravity / neighbours scratch
+    double *coef;  // [nsinks][20]
+    int64_t *nb_count;
+    int32_t *nb_long;  // [N] rows queued for the block-level sort
+    void *scan_tmp;
+    int64_t cap_scan;
+    int64_t nb_total;
+    int nb_valid;
+
+    // backward
+    int32_t *tnear_off, *tnear_sink, *tfar_off, *tfar_sink;
+    int bwd_valid;
+    double *adj;  // per-node adjoints
+
+    int64_t stats_fallback;
+    int64_t nroots_last;
+};
+
+namespace rcb {
+
+// memory helpers (rcb_api.cu)
+void *dev_alloc(rcb_tree *t, size_t bytes);
+void dev_free(rcb_tree *t, void *p);
+
+// build.cu
+int64_t scan_tmp_bytes(int64_t n);
+int scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, void *tmp, cudaStream_t st);
+int scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, void *tmp, cudaStream_t st);
+int build_tree(rcb_tree *t, const double *x, const double *m, const double *h);
+int refit_tree(rcb_tree *t, const double *x, const double *m);
+// walk.cu
+int walk_tree(rcb_tree *t);
+// neighbours.cu
+int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *needed);
+// gravity.cu
+int gravity(rcb_tree *t, double *acc, double *pot);
+// backward.cu
+int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double *gx, double *gm);
+
+#define RCB_CUDA_TRY(expr)                          \
+    do {                                            \
+        cudaError_t _e = (expr);                    \
+        if (_e != cudaSuccess) return RCB_ERR_CUDA; \
+    } while (0)
+
+}  // namespace rcb

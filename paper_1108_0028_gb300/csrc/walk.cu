@@ -1,0 +1,228 @@
+// Per-sink tree walk (Sec. 2.2, Sec. 2.3.1, Sec. 2.4.1) emitting near and far lists.
+//
+// One warp walks for 32 consecutive sinks (non-empty ll-cells in label order, hence spatial
+// neighbours).  The warp visits nodes in the depth-first order of Sec. 2.2 starting at node 2;
+// at a node, only the lanes whose walk reached it (every ancestor opened by that lane) decide;
+// the warp descends when any lane opens the node and skips the subtree otherwise.  Each lane's
+// decisions -- and therefore its lists -- are exactly those of its own single-sink walk, while
+// control flow stays uniform and node loads are broadcasts.
+//
+// Decisions (in this order, Sec. 2.4.1):
+//   reachable   |r_gA - r_gB|^2 < (h_node(A) + h_node_int(B))^2   -> ll-cell: near + candidate
+//                                                                    internal: open
+//   MAC         H_B^2 < theta^2 R_AB^2                            -> far
+//   otherwise   ll-cell: near; internal: open
+// Each test is first evaluated in float32 with a forward error bound B = 2^-20 F, where F is
+// the same expression evaluated on magnitudes (input rounding, ~7 roundings and the final
+// subtraction stay below 8u F with u = 2^-24, so B is twice the worst case).  Only when
+// |value| <= B is the test repeated in float64, rounded after every operation exactly as the
+// definition is written; the lists are therefore identical to an all-float64 walk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "rcb_internal.cuh"
+
+namespace rcb {
+namespace {
+
+constexpr int kWalkWarps = 4;
+
+struct WalkCtx {
+    int L;
+    int64_t nn;
+    double theta2;
+    float theta2f;
+    const int32_t *ncount;
+    const float4 *w32a, *w32b;
+    const double *nrg, *nhint, *ncom, *nH, *nhnode;
+    const int32_t *sinks;
+    int nsinks;
+    int cap_near, cap_far;
+    int32_t *near_list, *far_list, *near_nr, *near_nn, *far_n;
+    int *status;
+};
+
+__device__ inline float sq(float v) { return v * v; }
+
+__global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
+    __shared__ uint32_t masks[kWalkWarps][kMaxL + 2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kWalkWarps + w;
+    const int s = gw * 32 + lane;
+    const bool valid = s < c.nsinks;
+    const uint32_t valid_mask = __ballot_sync(0xffffffffu, valid);
+    if (valid_mask == 0) return;
+    const int A = valid ? c.sinks[s] : c.sinks[0];
+    const float4 a32 = c.w32a[A], b32 = c.w32b[A];
+    const float3 rgA = make_float3(a32.x, a32.y, a32.z);
+    const float3 comA = make_float3(b32.x, b32.y, b32.z);
+    const float hA = __double2float_rn(c.nhnode[A]);
+    const float3 rgAabs = make_float3(fabsf(rgA.x), fabsf(rgA.y), fabsf(rgA.z));
+    const float3 comAabs = make_float3(fabsf(comA.x), fabsf(comA.y), fabsf(comA.z));
+    const int64_t near_base = (int64_t)s * c.cap_near;
+    const int64_t far_base = (int64_t)s * c.cap_far;
+    int nr = 0, nnr = 0, nf = 0, nfallback = 0;
+
+    if (lane == 0) masks[w][0] = valid_mask;
+    __syncwarp();
+    int n = 2, lev = 1;
+    int64_t iter = 0;
+    const int64_t max_iter = 2 * c.nn + 8;
+    bool limit = false;
+    while (true) {
+        if (++iter > max_iter) {
+            limit = true;
+            break;
+        }
+        const uint32_t act = masks[w][lev - 1];
+        const int cnt = c.ncount[n];
+        bool open = false;
+        if (cnt > 0) {
+            const float4 na = c.w32a[n], nb = c.w32b[n];
+            if ((act >> lane) & 1u) {
+                const bool is_leaf = lev == c.L;
+                // reachability
+                float dx = rgA.x - na.x, dy = rgA.y - na.y, dz = rgA.z - na.z;
+                float d2 = dx * dx + dy * dy + dz * dz;
+                float rr = hA + na.w;
+                float f = d2 - rr * rr;
+                float F = sq(rgAabs.x + fabsf(na.x)) + sq(rgAabs.y + fabsf(na.y)) + sq(rgAabs.z + fabsf(na.z)) + rr * rr;
+                float B = F * 0x1p-20f + 1e-30f;
+                bool reach;
+                if (f < -B) reach = true;
+                else if (f > B) reach = false;
+                else {
+                    ++nfallback;
+                    double e2 = dist2_rn(c.nrg[3 * (int64_t)A], c.nrg[3 * (int64_t)A + 1], c.nrg[3 * (int64_t)A + 2],
+                                         c.nrg[3 * (int64_t)n], c.nrg[3 * (int64_t)n + 1], c.nrg[3 * (int64_t)n + 2]);
+                    double r = __dadd_rn(c.nhnode[A], c.nhint[n]);
+                    reach = e2 < __dmul_rn(r, r);
+                }
+                if (reach) {
+                    if (is_leaf) {
+                        if (nr + nnr < c.cap_near) c.near_list[near_base + nr] = n;
+                        ++nr;
+                    } else {
+                        open = true;
+                    }
+                } else {
+                    float ex = comA.x - nb.x, ey = comA.y - nb.y, ez = comA.z - nb.z;
+                    float R2 = ex * ex + ey * ey + ez * ez;
+                    float fm = nb.w * nb.w - c.theta2f * R2;
+                    float Fm = nb.w * nb.w +
+                               c.theta2f * (sq(comAabs.x + fabsf(nb.x)) + sq(comAabs.y + fabsf(nb.y)) + sq(comAabs.z + fabsf(nb.z)));
+                    float Bm = Fm * 0x1p-20f + 1e-30f;
+                    bool mac;
+                    if (fm < -Bm) mac = true;
+                    else if (fm > Bm) mac = false;
+                    else {
+                        ++nfallback;
+                        double R2d = dist2_rn(c.ncom[3 * (int64_t)A], c.ncom[3 * (int64_t)A + 1], c.ncom[3 * (int64_t)A + 2],
+                                              c.ncom[3 * (int64_t)n], c.ncom[3 * (int64_t)n + 1], c.ncom[3 * (int64_t)n + 2]);
+                        double H = c.nH[n];
+                        mac = __dmul_rn(H, H) < __dmul_rn(c.theta2, R2d);
+                    }
+                    if (mac) {
+                        if (nf < c.cap_far) c.far_list[far_base + nf] = n;
+                        ++nf;
+                    } else if (is_leaf) {
+                        if (nr + nnr < c.cap_near) c.near_list[near_base + c.cap_near - 1 - nnr] = n;
+                        ++nnr;
+                    } else {
+                        open = true;
+                    }
+                }
+            }
+        }
+        const uint32_t om = __ballot_sync(0xffffffffu, open);
+        if (om) {
+            __syncwarp();
+            if (lane == 0) masks[w][lev] = om;
+            __syncwarp();
+            n = 2 * n;
+            ++lev;
+            continue;
+        }
+        while (n & 1) {
+            n >>= 1;
+            --lev;
+        }
+        n += 1;
+        if (n == 1) break;
+    }
+    if (valid) {
+        c.near_nr[s] = nr;
+        c.near_nn[s] = nnr;
+        c.far_n[s] = nf;
+    }
+    int mn = valid ? nr + nnr : 0, mf = valid ? nf : 0;
+    for (int o = 16; o >= 1; o >>= 1) {
+        mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mf = max(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+        nfallback += __shfl_xor_sync(0xffffffffu, nfallback, o);
+    }
+    if (lane == 0) {
+        atomicMax(&c.status[ST_MAXNEAR], mn);
+        atomicMax(&c.status[ST_MAXFAR], mf);
+        if (nfallback) atomicAdd(&c.status[ST_FALLBACK], nfallback);
+        if (limit) atomicOr(&c.status[ST_ERR], ERRBIT_LIMIT);
+    }
+}
+
+}  // namespace
+
+int walk_tree(rcb_tree *t) {
+    cudaStream_t st = t->stream;
+    WalkCtx c;
+    c.L = t->L;
+    c.nn = t->nn;
+    c.theta2 = t->params.theta * t->params.theta;
+    c.theta2f = (float)c.theta2;
+    c.ncount = t->ncount;
+    c.w32a = t->w32a;
+    c.w32b = t->w32b;
+    c.nrg = t->nrg;
+    c.nhint = t->nhint;
+    c.ncom = t->ncom;
+    c.nH = t->nH;
+    c.nhnode = t->nhnode;
+    c.sinks = t->sinks;
+    c.nsinks = t->nsinks;
+    c.status = t->d_status;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        c.cap_near = t->cap_near;
+        c.cap_far = t->cap_far;
+        c.near_list = t->near_list;
+        c.far_list = t->far_list;
+        c.near_nr = t->near_nr;
+        c.near_nn = t->near_nn;
+        c.far_n = t->far_n;
+        RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_MAXNEAR, 0, 3 * sizeof(int), st));
+        int warps = (t->nsinks + 31) / 32;
+        int blocks = (warps + kWalkWarps - 1) / kWalkWarps;
+        if (blocks > 0) k_walk<<<blocks, kWalkWarps * 32, 0, st>>>(c);
+        RCB_CUDA_TRY(cudaGetLastError());
+        RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status, t->d_status, ST_NWORDS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        RCB_CUDA_TRY(cudaStreamSynchronize(st));
+        if (t->h_status[ST_ERR] & ERRBIT_LIMIT) return RCB_ERR_LIMIT;
+        int need_near = t->h_status[ST_MAXNEAR], need_far = t->h_status[ST_MAXFAR];
+        t->stats_fallback = t->h_status[ST_FALLBACK];
+        if (need_near <= t->cap_near && need_far <= t->cap_far) return RCB_OK;
+        // grow the per-sink list capacities and walk again
+        int cn = std::max(t->cap_near, ((need_near + 31) / 32) * 32 + 32);
+        int cf = std::max(t->cap_far, ((need_far + 31) / 32) * 32 + 32);
+        dev_free(t, t->near_list);
+        dev_free(t, t->far_list);
+        t->near_list = (int32_t *)dev_alloc(t, (size_t)t->nsinks * cn * sizeof(int32_t) + 16);
+        t->far_list = (int32_t *)dev_alloc(t, (size_t)t->nsinks * cf * sizeof(int32_t) + 16);
+        if (!t->near_list || !t->far_list) return RCB_ERR_ALLOC;
+        t->cap_near = cn;
+        t->cap_far = cf;
+        t->cap_lists_near = (int64_t)t->nsinks * cn;
+        t->cap_lists_far = (int64_t)t->nsinks * cf;
+    }
+    return RCB_ERR_LIMIT;
+}
+
+}  // namespace rcb

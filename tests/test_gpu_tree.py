@@ -1,0 +1,117 @@
+"""GPU parity of the tree build and the interaction lists against the oracle (bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(x, m, h):
+    import torch
+    dev = torch.device("cuda:0")
+    return tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (x, m, h))
+
+
+def _compare_topology(tree, ref):
+    g = tree.export_topology()
+    o = ref.nodes()
+    assert tree.info()["L"] == ref.L
+    assert np.array_equal(g["leaf_of"], ref.leaf_of())
+    assert np.array_equal(g["count"], o["count"])
+    live = o["count"] > 0
+    live[0] = False
+    leaf0 = 1 << ref.L
+    internal = live.copy()
+    internal[leaf0:] = False
+    assert np.array_equal(g["first"][live], o["first"][live])
+    assert np.array_equal(g["axis"][internal], o["axis"][internal])
+    assert np.array_equal(g["split"][internal].view(np.int64), o["split"][internal].view(np.int64))
+    assert np.array_equal(g["sums"][live], o["sums"][live])
+    for k in ("mass", "com", "bmin", "bmax", "rg", "H", "hint"):
+        assert np.array_equal(g[k][live].view(np.int64), o[k][live].view(np.int64)), k
+    leaves = live.copy()
+    leaves[:leaf0] = False
+    assert np.array_equal(g["hnode"][leaves].view(np.int64), o["hnode"][leaves].view(np.int64))
+    # Q: FP64 sums in a different order -> rounding-level agreement
+    scale = np.abs(o["Q"][live]).max(axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(g["Q"][live] - o["Q"][live]) / scale) < 1e-10
+    # the sorted particle order holds every particle once, each inside its own leaf range
+    perm = g["perm"]
+    assert np.array_equal(np.sort(perm), np.arange(ref.N))
+
+
+def _compare_lists(tree, ref):
+    g = tree.export_lists()
+    o = ref.lists()
+    nl = ref.nleaves
+    assert np.array_equal(np.diff(g["near_off"]), np.diff(o["near_off"]))
+    assert np.array_equal(np.diff(g["far_off"]), np.diff(o["far_off"]))
+    for j in range(nl):
+        a, b = g["near_off"][j], g["near_off"][j + 1]
+        c, d = o["near_off"][j], o["near_off"][j + 1]
+        if b == a:
+            continue
+        gn = sorted(zip(g["near_ids"][a:b].tolist(), g["near_reach"][a:b].tolist()))
+        on = sorted(zip(o["near_ids"][c:d].tolist(), o["near_reach"][c:d].tolist()))
+        assert gn == on, j
+        fa, fb = g["far_off"][j], g["far_off"][j + 1]
+        oa, ob = o["far_off"][j], o["far_off"][j + 1]
+        assert sorted(g["far_ids"][fa:fb].tolist()) == sorted(o["far_ids"][oa:ob].tolist()), j
+
+
+CASES = [
+    ("plummer", 4096, "equal", 0.5),        # the small workload, one shared-memory subtree pass
+    ("plummer", 2049, "loguniform10", 0.7),  # one level pass, then subtrees
+    ("cube", 3000, "equal", 0.5),
+    ("sphere", 20000, "loguniform10", 0.7),
+    ("plummer", 150000, "loguniform10", 0.5),  # several level passes, thousands of sinks
+    ("cube", 13, "equal", 0.5),
+    ("sphere", 1, "equal", 0.5),
+    ("sphere", 2, "equal", 0.5),
+]
+
+
+@pytest.mark.parametrize("kind,N,mass,theta", CASES)
+def test_tree_and_lists_bit_exact(kind, N, mass, theta):
+    import paper_1108_0028_gb300 as rcb
+    x, m, h = synth.make_particles(kind, N, synth.seed_for(3, N), mass)
+    ref = oracle.OracleTree(x, m, h, n_ll=12)
+    ref.walk(theta)
+    tree = rcb.RCBTree(*_gpu(x, m, h), n_ll=12, theta=theta, precision="mixed")
+    _compare_topology(tree, ref)
+    _compare_lists(tree, ref)
+    # a rebuild in place gives the same tree
+    tree.rebuild(*_gpu(x, m, h))
+    _compare_topology(tree, ref)
+
+
+def test_degenerate_coincident_and_theta_zero():
+    import paper_1108_0028_gb300 as rcb
+    x = np.ones((300, 3))
+    x[150:] += 1e-3
+    m = np.full(300, 1.0 / 300)
+    h = np.full(300, 0.01)
+    for theta in (0.0, 0.6):
+        ref = oracle.OracleTree(x, m, h)
+        ref.walk(theta)
+        tree = rcb.RCBTree(*_gpu(x, m, h), theta=theta)
+        _compare_topology(tree, ref)
+        _compare_lists(tree, ref)
+
+
+def test_invalid_inputs_rejected():
+    import paper_1108_0028_gb300 as rcb
+    x, m, h = synth.make_particles("cube", 100, 1)
+    for bad in ("nan", "mass", "h"):
+        xx, mm, hh = x.copy(), m.copy(), h.copy()
+        if bad == "nan":
+            xx[5, 1] = np.nan
+        elif bad == "mass":
+            mm[3] = 0.0
+        else:
+            hh[7] = -1.0
+        with pytest.raises(rcb.RCBError) as e:
+            rcb.RCBTree(*_gpu(xx, mm, hh))
+        assert e.value.status == rcb.RCB_ERR_ARG
