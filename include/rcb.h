@@ -38,6 +38,8 @@ extern "C" {
 #define RCB_ERR_LIMIT (-5)    /* a bounded device loop gave up (see the call's description) */
 #define RCB_ERR_STATE (-6)    /* the call needs state the tree does not have */
 
+#define RCB_FLAG_TIMING 1u /* record CUDA events around every stage (see rcb_stage_times) */
+
 #define RCB_FP64 0  /* gravity in FP64 throughout */
 #define RCB_MIXED 1 /* FP32 near field on cell-relative offsets with compensated sums; FP32
                        multipole tensors; Taylor coefficients accumulated with compensation
@@ -50,7 +52,7 @@ typedef struct {
                           N < n_ll * 2^L (Table 1) */
     int32_t precision; /* RCB_FP64 or RCB_MIXED: form used by rcb_gravity and the backward */
     double theta;      /* opening angle of the geometric MAC, Eq. 4 (theta = 0: direct sum) */
-    uint32_t flags;    /* reserved, must be 0 */
+    uint32_t flags;    /* 0 or RCB_FLAG_TIMING */
     uint32_t reserved;
 } rcb_params;
 
@@ -142,7 +144,10 @@ int rcb_set_precision(rcb_tree *tree, int32_t precision);
  *   4 number of sinks (non-empty ll-cells), 5 near-list capacity per sink, 6 far-list capacity
  *   per sink, 7 total near entries, 8 total far entries, 9 total reachable near entries,
  *   10 walk decisions settled in FP64 (after the FP32 filter was inconclusive),
- *   11 number of subtrees built in shared memory, 12 precision, 13..15 reserved.
+ *   11 number of subtrees built in shared memory, 12 precision, 13 near-field pair count
+ *   (sum over sinks of sink particles x near-list particles, self pairs included),
+ *   14 neighbour-candidate pair count (the same over reachable cells), 15 number of kernel
+ *   launches issued by the library in this process so far.
  */
 int rcb_tree_info(const rcb_tree *tree, int64_t *info);
 
@@ -172,6 +177,17 @@ int rcb_export_topology(rcb_tree *tree, int32_t *leaf_of, int32_t *perm, int64_t
  */
 int rcb_export_lists(rcb_tree *tree, int64_t *near_off, int32_t *near_ids, uint8_t *near_reach, int64_t cap_near,
                      int64_t *far_off, int32_t *far_ids, int64_t cap_far, void *stream);
+
+/*
+ * rcb_stage_times -- host, out [16] float64: device time in milliseconds of the last call of
+ *   each stage, measured with CUDA events on the call's stream when the tree was built with
+ *   RCB_FLAG_TIMING (zeros otherwise):
+ *   0 ingest + root, 1 level passes, 2 shared-memory subtrees, 3 leaf moments + bottom-up +
+ *   packing, 4 walk, 5 whole build (0..4), 6 neighbour count + scan, 7 neighbour fill,
+ *   8 neighbour row sort, 9 far field, 10 near field (+ Taylor evaluation and scatter),
+ *   11 backward, 12..15 reserved.  Synchronises `stream`.
+ */
+int rcb_stage_times(rcb_tree *tree, double *ms, void *stream);
 
 /* Release the tree and everything it owns (NULL is allowed). */
 void rcb_free(rcb_tree *tree);

@@ -24,8 +24,11 @@ RCB_OK, RCB_ERR_ARG, RCB_ERR_ALLOC, RCB_ERR_CAPACITY, RCB_ERR_CUDA, RCB_ERR_LIMI
 RCB_FP64, RCB_MIXED = 0, 1
 _PRECISION = {"fp64": RCB_FP64, "mixed": RCB_MIXED, RCB_FP64: RCB_FP64, RCB_MIXED: RCB_MIXED}
 
+RCB_FLAG_TIMING = 1
 SYMBOLS = ["rcb_build", "rcb_neighbours", "rcb_gravity", "rcb_gravity_backward", "rcb_refit", "rcb_set_precision",
-           "rcb_tree_info", "rcb_export_topology", "rcb_export_lists", "rcb_free", "rcb_strerror"]
+           "rcb_tree_info", "rcb_export_topology", "rcb_export_lists", "rcb_stage_times", "rcb_free", "rcb_strerror"]
+STAGES = ["ingest", "levels", "subtrees", "leaves", "walk", "build", "nb_count", "nb_fill", "nb_sort", "far", "near",
+          "backward"]
 
 _lock = threading.Lock()
 _lib = None
@@ -66,6 +69,7 @@ def lib():
                 "rcb_tree_info": (ctypes.c_int, [P, P]),
                 "rcb_export_topology": (ctypes.c_int, [P] + [P] * 16 + [P]),
                 "rcb_export_lists": (ctypes.c_int, [P, P, P, P, I64, P, P, I64, P]),
+                "rcb_stage_times": (ctypes.c_int, [P, P, P]),
                 "rcb_free": (None, [P]),
                 "rcb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             }
@@ -117,13 +121,13 @@ def _cuda_f64(t, shape, name):
 # ---------------------------------------------------------------------------------------------
 # C-ABI mirrors (argument marshalling only)
 
-def rcb_build(x, m, h, n_ll=12, theta=0.7, precision="mixed", tree=None, stream=None):
+def rcb_build(x, m, h, n_ll=12, theta=0.7, precision="mixed", tree=None, stream=None, flags=0):
     """Build (or rebuild in place) a tree; returns the handle (ctypes.c_void_p)."""
     N = x.shape[0] if x.dim() == 2 else 0
     _cuda_f64(x, (N, 3), "x")
     _cuda_f64(m, (N,), "m")
     _cuda_f64(h, (N,), "h")
-    p = rcb_params(int(n_ll), _PRECISION[precision], float(theta), 0, 0)
+    p = rcb_params(int(n_ll), _PRECISION[precision], float(theta), int(flags), 0)
     handle = tree if tree is not None else ctypes.c_void_p(None)
     st = lib().rcb_build(_dptr(x), _dptr(m), _dptr(h), N, ctypes.byref(p), None, None, None, _stream_ptr(stream),
                          ctypes.byref(handle))
@@ -159,8 +163,14 @@ def rcb_tree_info(tree) -> dict:
     info = np.zeros(16, np.int64)
     _check(lib().rcb_tree_info(tree, _hptr(info)), "rcb_tree_info")
     keys = ["N", "L", "nn", "nleaves", "nsinks", "cap_near", "cap_far", "near_total", "far_total", "reach_total",
-            "walk_fp64_decisions", "smem_subtrees", "precision"]
+            "walk_fp64_decisions", "smem_subtrees", "precision", "near_pairs", "candidate_pairs", "launches"]
     return {k: int(info[i]) for i, k in enumerate(keys)}
+
+
+def rcb_stage_times(tree, stream=None) -> dict:
+    ms = np.zeros(16)
+    _check(lib().rcb_stage_times(tree, _hptr(ms), _stream_ptr(stream)), "rcb_stage_times")
+    return {k: float(ms[i]) for i, k in enumerate(STAGES)}
 
 
 def rcb_free(tree) -> None:
@@ -172,17 +182,22 @@ def rcb_free(tree) -> None:
 class RCBTree:
     """An RCB tree over CUDA tensors x[N,3], m[N], h[N] (float64)."""
 
-    def __init__(self, x, m, h, n_ll: int = 12, theta: float = 0.7, precision="mixed", stream=None):
+    def __init__(self, x, m, h, n_ll: int = 12, theta: float = 0.7, precision="mixed", stream=None,
+                 timing: bool = False):
         self._h = None
         self.n_ll, self.theta, self.precision = n_ll, theta, precision
-        self._h = rcb_build(x, m, h, n_ll, theta, precision, None, stream)
+        self.flags = RCB_FLAG_TIMING if timing else 0
+        self._h = rcb_build(x, m, h, n_ll, theta, precision, None, stream, self.flags)
         self.N = x.shape[0]
         self.device = x.device
         self._nb_cap = 0
 
     def rebuild(self, x, m, h, stream=None):
-        self._h = rcb_build(x, m, h, self.n_ll, self.theta, self.precision, self._h, stream)
+        self._h = rcb_build(x, m, h, self.n_ll, self.theta, self.precision, self._h, stream, self.flags)
         self.N = x.shape[0]
+
+    def stage_times(self, stream=None) -> dict:
+        return rcb_stage_times(self._h, stream)
 
     @property
     def handle(self):

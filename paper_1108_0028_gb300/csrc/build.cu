@@ -1009,9 +1009,9 @@ int scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, void *t
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     int32_t *sums = reinterpret_cast<int32_t *>(tmp);
     if (ntiles == 0) return cudaMemsetAsync(total, 0, sizeof(int32_t), st) == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
-    k_scan_tiles<int32_t, int32_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums);
-    k_scan_sums<int32_t><<<1, kScanThreads, 0, st>>>(sums, ntiles, total);
-    k_scan_apply<int32_t, int32_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums, out);
+    k_scan_tiles<int32_t, int32_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums); note_launch();
+    k_scan_sums<int32_t><<<1, kScanThreads, 0, st>>>(sums, ntiles, total); note_launch();
+    k_scan_apply<int32_t, int32_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums, out); note_launch();
     return cudaGetLastError() == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
 }
 
@@ -1019,9 +1019,9 @@ int scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, void *t
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     int64_t *sums = reinterpret_cast<int64_t *>(tmp);
     if (ntiles == 0) return cudaMemsetAsync(total, 0, sizeof(int64_t), st) == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
-    k_scan_tiles<int64_t, int64_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums);
-    k_scan_sums<int64_t><<<1, kScanThreads, 0, st>>>(sums, ntiles, total);
-    k_scan_apply<int64_t, int64_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums, out);
+    k_scan_tiles<int64_t, int64_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums); note_launch();
+    k_scan_sums<int64_t><<<1, kScanThreads, 0, st>>>(sums, ntiles, total); note_launch();
+    k_scan_apply<int64_t, int64_t><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums, out); note_launch();
     return cudaGetLastError() == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
 }
 
@@ -1036,17 +1036,20 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
 
     int grid = (int)std::min<int64_t>((N + 255) / 256, (int64_t)nsm * 8);
     if (grid < 1) grid = 1;
-    k_ingest_scan<<<grid, 256, 0, st>>>(x, m, h, N, t->d_status, t->d_maxbits);
-    k_exponents<<<1, 32, 0, st>>>(t->d_maxbits, t->d_E);
+    stage_begin(t, SG_INGEST);
+    k_ingest_scan<<<grid, 256, 0, st>>>(x, m, h, N, t->d_status, t->d_maxbits); note_launch();
+    k_exponents<<<1, 32, 0, st>>>(t->d_maxbits, t->d_E); note_launch();
     Red *partials = reinterpret_cast<Red *>(t->chunk_part);  // reused: grid <= cap_chunks
     k_ingest_write<<<grid, 256, 0, st>>>(x, m, N, t->cap_N, t->d_E, t->bx[0], t->by[0], t->bz[0], t->bP[0],
-                                         t->bidx[0], partials, t->d_status);
+                                         t->bidx[0], partials, t->d_status); note_launch();
     Ctx c = make_ctx(t);
-    k_root_finalize<<<1, 256, 0, st>>>(c, partials, grid, t->big_list[0], t->roots);
+    k_root_finalize<<<1, 256, 0, st>>>(c, partials, grid, t->big_list[0], t->roots); note_launch();
     RCB_CUDA_TRY(cudaGetLastError());
+    stage_end(t, SG_INGEST);
     int rc = read_status(t);
     if (rc) return rc;
     if (t->h_status[ST_ERR] & (ERRBIT_ARG | ERRBIT_FIXED)) return RCB_ERR_ARG;
+    stage_begin(t, SG_LEVELS);
 
     // level passes while large cells remain
     int nbig = t->h_status[ST_NBIG];
@@ -1058,19 +1061,19 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
         int64_t bound = (N + kChunk - 1) / kChunk + nbig + 1;
         if (bound > t->cap_chunks) return RCB_ERR_LIMIT;
         k_chunk_plan<<<1, 1024, 0, st>>>(t->big_list[cur], nbig, t->nfirst, t->ncount, t->cell_chunk0, t->chunks,
-                                         t->d_status);
+                                         t->d_status); note_launch();
         int g = (int)std::min<int64_t>(bound, (int64_t)nsm * 8);
         k_level_reduce<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, t->bx[cur], t->by[cur],
-                                                    t->bz[cur], t->bP[cur], parts);
+                                                    t->bz[cur], t->bP[cur], parts); note_launch();
         RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_NBIG, 0, sizeof(int), st));
         int gf = (nbig * 32 + 255) / 256;
         k_level_finalize<<<gf, 256, 0, st>>>(c, level, t->big_list[cur], nbig, t->cell_chunk0,
                                              t->d_status + ST_NCHUNKS, parts, t->big_list[cur ^ 1], t->roots,
-                                             (level + 1) & 1);
+                                             (level + 1) & 1); note_launch();
         k_level_scatter<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, parts, t->bx[cur],
                                                      t->by[cur], t->bz[cur], t->bP[cur], t->bidx[cur], t->bx[cur ^ 1],
                                                      t->by[cur ^ 1], t->bz[cur ^ 1], t->bP[cur ^ 1],
-                                                     t->bidx[cur ^ 1]);
+                                                     t->bidx[cur ^ 1]); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());
         rc = read_status(t);
         if (rc) return rc;
@@ -1079,6 +1082,7 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
         cur ^= 1;
         ++level;
     }
+    stage_end(t, SG_LEVELS);
     int nroots = t->h_status[ST_NROOTS];
     if (nroots > t->cap_roots || (t->h_status[ST_ERR] & ERRBIT_STATE)) return RCB_ERR_LIMIT;
     t->nroots_last = nroots;
@@ -1093,24 +1097,27 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
             B.P[q] = t->bP[q];
             B.idx[q] = t->bidx[q];
         }
+        stage_begin(t, SG_SUBTREE);
         size_t smem = sizeof(SubtreeSmem);
         RCB_CUDA_TRY(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int g = std::max(1, std::min(nroots, nsm));
         k_subtree<<<g, kCtaThreads, smem, st>>>(c, t->roots, t->d_status + ST_NROOTS, B, m, h, t->px, t->py, t->pz,
-                                                t->pm, t->ph, t->pidx);
+                                                t->pm, t->ph, t->pidx); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());
+        stage_end(t, SG_SUBTREE);
     }
 
     // sinks: non-empty ll-cells in label order
+    stage_begin(t, SG_LEAVES);
     {
         int32_t *flags = reinterpret_cast<int32_t *>(t->near_nr);  // scratch: >= nleaves entries
         int32_t *pos = t->sink_of_leaf;
         int64_t leaf0 = t->nleaves;
         int g = (int)std::min<int64_t>((t->nleaves + 255) / 256, (int64_t)nsm * 8);
-        k_count_sinks<<<g, 256, 0, st>>>(t->ncount, leaf0, t->nleaves, flags);
+        k_count_sinks<<<g, 256, 0, st>>>(t->ncount, leaf0, t->nleaves, flags); note_launch();
         rc = scan_i32(flags, pos, t->nleaves, t->d_status + ST_NSINKS, t->scan_tmp, st);
         if (rc) return rc;
-        k_write_sinks<<<g, 256, 0, st>>>(flags, pos, leaf0, t->nleaves, t->sinks, t->sink_of_leaf);
+        k_write_sinks<<<g, 256, 0, st>>>(flags, pos, leaf0, t->nleaves, t->sinks, t->sink_of_leaf); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());
         rc = read_status(t);
         if (rc) return rc;
@@ -1137,7 +1144,7 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
         lc.ph = t->ph;
         lc.p32 = t->p32;
         lc.h32 = t->h32;
-        if (t->nsinks > 0) k_leaves_up<<<(t->nsinks + 127) / 128, 128, 0, st>>>(lc, t->sinks, t->nsinks);
+        if (t->nsinks > 0) k_leaves_up<<<(t->nsinks + 127) / 128, 128, 0, st>>>(lc, t->sinks, t->nsinks); note_launch();
         PackCtx pc;
         pc.ncount = t->ncount;
         pc.nmass = t->nmass;
@@ -1152,9 +1159,10 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
         pc.mq32b = t->mq32b;
         pc.ncomdf = t->ncomdf;
         int g = (int)std::min<int64_t>((t->nn + 255) / 256, (int64_t)nsm * 8);
-        k_pack_nodes<<<g, 256, 0, st>>>(pc, t->nn);
+        k_pack_nodes<<<g, 256, 0, st>>>(pc, t->nn); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());
     }
+    stage_end(t, SG_LEAVES);
     return RCB_OK;
 }
 

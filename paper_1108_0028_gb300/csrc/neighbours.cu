@@ -312,11 +312,13 @@ int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, in
     const int blocks = std::max(1, std::min((t->nsinks + kNbWarps - 1) / kNbWarps, nsm * 16));
     RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_NBFALLBACK, 0, 2 * sizeof(int), st));
     if (!t->nb_valid) {
+        stage_begin(t, SG_NB_COUNT);
         RCB_CUDA_TRY(cudaFuncSetAttribute(k_neighbours<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_neighbours<false><<<blocks, kNbWarps * 32, smem, st>>>(c);
+        k_neighbours<false><<<blocks, kNbWarps * 32, smem, st>>>(c); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());
         int rc = scan_i64(t->nb_count, t->nb_count, t->N, t->nb_count + t->N, t->scan_tmp, st);
         if (rc) return rc;
+        stage_end(t, SG_NB_COUNT);
         RCB_CUDA_TRY(cudaMemcpyAsync(&t->nb_total, t->nb_count + t->N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         RCB_CUDA_TRY(cudaStreamSynchronize(st));
         t->nb_valid = 1;
@@ -332,12 +334,16 @@ int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, in
         return RCB_ERR_CAPACITY;
     }
     RCB_CUDA_TRY(cudaFuncSetAttribute(k_neighbours<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_neighbours<true><<<blocks, kNbWarps * 32, smem, st>>>(c);
+    stage_begin(t, SG_NB_FILL);
+    k_neighbours<true><<<blocks, kNbWarps * 32, smem, st>>>(c); note_launch();
     const int rb = (int)std::min<int64_t>((t->N + kNbWarps - 1) / kNbWarps, (int64_t)nsm * 16);
     int32_t *lr = t->nb_long;
     const int cap_long = (int)t->N;
-    k_sort_rows<<<std::max(rb, 1), kNbWarps * 32, 0, st>>>(offsets, t->N, idx, lr, t->d_status, cap_long);
-    k_sort_long<<<std::max(1, nsm * 2), 1024, 0, st>>>(offsets, idx, lr, t->d_status + ST_LONGROWS, cap_long);
+    stage_end(t, SG_NB_FILL);
+    stage_begin(t, SG_NB_SORT);
+    k_sort_rows<<<std::max(rb, 1), kNbWarps * 32, 0, st>>>(offsets, t->N, idx, lr, t->d_status, cap_long); note_launch();
+    k_sort_long<<<std::max(1, nsm * 2), 1024, 0, st>>>(offsets, idx, lr, t->d_status + ST_LONGROWS, cap_long); note_launch();
+    stage_end(t, SG_NB_SORT);
     RCB_CUDA_TRY(cudaGetLastError());
     RCB_CUDA_TRY(cudaStreamSynchronize(st));
     return RCB_OK;

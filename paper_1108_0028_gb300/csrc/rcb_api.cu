@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -30,6 +31,26 @@ void dev_free(rcb_tree *t, void *p) {
 }
 
 size_t chunk_part_bytes(int64_t cap_chunks);  // build.cu
+int count_pairs(rcb_tree *t);                  // walk.cu
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+void stage_begin(rcb_tree *t, int stage) {
+    if (!(t->params.flags & RCB_FLAG_TIMING)) return;
+    if (!t->ev_ready) {
+        for (int i = 0; i < 32; ++i) cudaEventCreate(&t->ev[i]);
+        t->ev_ready = true;
+    }
+    cudaEventRecord(t->ev[2 * stage], t->stream);
+    t->ev_used[stage] = true;
+}
+
+void stage_end(rcb_tree *t, int stage) {
+    if (!(t->params.flags & RCB_FLAG_TIMING) || !t->ev_ready) return;
+    cudaEventRecord(t->ev[2 * stage + 1], t->stream);
+}
 
 namespace {
 
@@ -48,6 +69,7 @@ void for_each_array(rcb_tree *t, F f) {
     f((void **)&t->d_status);
     f((void **)&t->d_E);
     f((void **)&t->d_maxbits);
+    f((void **)&t->d_pairs);
     for (int b = 0; b < 2; ++b) {
         f((void **)&t->bx[b]);
         f((void **)&t->by[b]);
@@ -65,7 +87,7 @@ void for_each_array(rcb_tree *t, F f) {
                   (void **)&t->narrive, (void **)&t->roots, (void **)&t->chunks, (void **)&t->cell_chunk0,
                   (void **)&t->chunk_part, (void **)&t->sinks, (void **)&t->sink_of_leaf, (void **)&t->near_nr,
                   (void **)&t->near_nn, (void **)&t->far_n, (void **)&t->near_list, (void **)&t->far_list,
-                  (void **)&t->coef, (void **)&t->nb_count, (void **)&t->nb_long, (void **)&t->scan_tmp, (void **)&t->tnear_off,
+                  (void **)&t->coef, (void **)&t->coef32, (void **)&t->nb_count, (void **)&t->nb_long, (void **)&t->scan_tmp, (void **)&t->tnear_off,
                   (void **)&t->tnear_sink, (void **)&t->tfar_off, (void **)&t->tfar_sink, (void **)&t->adj};
     for (void **q : p) f(q);
 }
@@ -95,6 +117,7 @@ int allocate_arrays(rcb_tree *t, int64_t N, int L) {
     A((void **)&t->d_status, ST_NWORDS * sizeof(int));
     A((void **)&t->d_E, 4 * sizeof(int));
     A((void **)&t->d_maxbits, 4 * sizeof(unsigned long long));
+    A((void **)&t->d_pairs, 2 * sizeof(int64_t));
     for (int b = 0; b < 2; ++b) {
         A((void **)&t->bx[b], capN * sizeof(double));
         A((void **)&t->by[b], capN * sizeof(double));
@@ -142,6 +165,7 @@ int allocate_arrays(rcb_tree *t, int64_t N, int L) {
     A((void **)&t->near_nn, nl * sizeof(int32_t));
     A((void **)&t->far_n, nl * sizeof(int32_t));
     A((void **)&t->coef, 20 * nl * sizeof(double));
+    A((void **)&t->coef32, 20 * nl * sizeof(float));
     A((void **)&t->nb_count, (capN + 1) * sizeof(int64_t));
     A((void **)&t->nb_long, capN * sizeof(int32_t));
     A((void **)&t->scan_tmp, (size_t)scan_tmp_bytes(std::max<int64_t>(capN + 1, nl)) + 256);
@@ -203,7 +227,7 @@ int rcb_build(const double *x, const double *m, const double *h, int64_t N, cons
     if (N < 1 || N >= ((int64_t)1 << 31)) return RCB_ERR_ARG;
     if (params->n_ll < 1 || !(params->theta >= 0.0) || !std::isfinite(params->theta)) return RCB_ERR_ARG;
     if (params->precision != RCB_FP64 && params->precision != RCB_MIXED) return RCB_ERR_ARG;
-    if (params->flags != 0) return RCB_ERR_ARG;
+    if ((params->flags & ~RCB_FLAG_TIMING) != 0) return RCB_ERR_ARG;
     if ((alloc == nullptr) != (release == nullptr)) return RCB_ERR_ARG;
     const int L = depth_rule(N, params->n_ll);
     if (L > kMaxL) return RCB_ERR_ARG;
@@ -232,11 +256,18 @@ int rcb_build(const double *x, const double *m, const double *h, int64_t N, cons
     t->nleaves = (int64_t)1 << L;
     t->nb_valid = 0;
     t->bwd_valid = 0;
+    t->near_pairs = t->cand_pairs = -1;
     int rc = RCB_OK;
     if (t->cap_N == 0) rc = allocate_arrays(t, N, L);
+    stage_begin(t, SG_BUILD);
     if (rc == RCB_OK) rc = build_tree(t, x, m, h);
     if (rc == RCB_OK) rc = ensure_lists(t);
-    if (rc == RCB_OK) rc = walk_tree(t);
+    if (rc == RCB_OK) {
+        stage_begin(t, SG_WALK);
+        rc = walk_tree(t);
+        stage_end(t, SG_WALK);
+    }
+    stage_end(t, SG_BUILD);
     if (rc != RCB_OK) {
         if (created) {
             rcb_free(t);
@@ -309,6 +340,26 @@ int rcb_tree_info(const rcb_tree *t, int64_t *info) {
     info[10] = t->stats_fallback;
     info[11] = t->nroots_last;
     info[12] = t->params.precision;
+    if (t->near_pairs < 0 && t->nsinks > 0) {
+        if (count_pairs(const_cast<rcb_tree *>(t)) != RCB_OK) return RCB_ERR_CUDA;
+    }
+    info[13] = t->near_pairs;
+    info[14] = t->cand_pairs;
+    info[15] = launch_count();
+    return RCB_OK;
+}
+
+int rcb_stage_times(rcb_tree *t, double *ms, void *stream) {
+    if (!t || !ms) return RCB_ERR_ARG;
+    for (int i = 0; i < 16; ++i) ms[i] = 0.0;
+    if (!t->ev_ready) return RCB_OK;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return RCB_ERR_CUDA;
+    if (cudaStreamSynchronize(t->stream) != cudaSuccess) return RCB_ERR_CUDA;
+    for (int i = 0; i < 16; ++i) {
+        if (!t->ev_used[i]) continue;
+        float v = 0.f;
+        if (cudaEventElapsedTime(&v, t->ev[2 * i], t->ev[2 * i + 1]) == cudaSuccess) ms[i] = v;
+    }
     return RCB_OK;
 }
 
@@ -421,6 +472,8 @@ int rcb_export_lists(rcb_tree *t, int64_t *near_off, int32_t *near_ids, uint8_t 
 void rcb_free(rcb_tree *tree) {
     if (!tree) return;
     release_arrays(tree);
+    if (tree->ev_ready)
+        for (int i = 0; i < 32; ++i) cudaEventDestroy(tree->ev[i]);
     if (tree->h_status) cudaFreeHost(tree->h_status);
     tree->h_status = nullptr;
     delete tree;

@@ -229,7 +229,8 @@ struct rcb_tree {
     int64_t cap_lists_near, cap_lists_far;  // allocated entries
 
     // gravity / neighbours scratch
-    double *coef;  // [nsinks][20]
+    double *coef;    // [nsinks][20] far-field Taylor coefficients
+    float *coef32;   // their float32 values (mixed form)
     int64_t *nb_count;
     int32_t *nb_long;  // [N] rows queued for the block-level sort
     void *scan_tmp;
@@ -244,6 +245,12 @@ struct rcb_tree {
 
     int64_t stats_fallback;
     int64_t nroots_last;
+    int64_t launches;        // kernel launches issued by the library for this tree
+    int64_t near_pairs, cand_pairs;
+    int64_t *d_pairs;        // [2] device counters of the two pair totals
+    cudaEvent_t ev[2 * 16];  // start/stop per stage (RCB_FLAG_TIMING)
+    bool ev_ready;
+    bool ev_used[16];
 };
 
 namespace rcb {
@@ -266,6 +273,16 @@ int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, in
 int gravity(rcb_tree *t, double *acc, double *pot);
 // backward.cu
 int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double *gx, double *gm);
+
+// Stage timing (RCB_FLAG_TIMING): events recorded on the tree's stream.
+enum Stage {
+    SG_INGEST = 0, SG_LEVELS = 1, SG_SUBTREE = 2, SG_LEAVES = 3, SG_WALK = 4, SG_BUILD = 5,
+    SG_NB_COUNT = 6, SG_NB_FILL = 7, SG_NB_SORT = 8, SG_FAR = 9, SG_NEAR = 10, SG_BWD = 11
+};
+void stage_begin(rcb_tree *t, int stage);
+void note_launch();  // counts kernel launches of the library (process-wide)
+long long launch_count();
+void stage_end(rcb_tree *t, int stage);
 
 #define RCB_CUDA_TRY(expr)                          \
     do {                                            \

@@ -170,7 +170,50 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
     }
 }
 
+// Per sink: (sink particles) x (particles of all near cells) and x (of reachable cells).
+__global__ void k_pair_counts(const int32_t *sinks, int nsinks, const int32_t *ncount, const int32_t *near_list,
+                              const int32_t *near_nr, const int32_t *near_nn, int cap_near,
+                              unsigned long long *out) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long all = 0, reach = 0;
+    for (int s = gw; s < nsinks; s += nw) {
+        const int nA = ncount[sinks[s]];
+        const int nr = near_nr[s], nn = near_nn[s];
+        const int64_t base = (int64_t)s * cap_near;
+        for (int k = lane; k < nr + nn; k += 32) {
+            const int B = k < nr ? near_list[base + k] : near_list[base + cap_near - 1 - (k - nr)];
+            const unsigned long long p = (unsigned long long)nA * ncount[B];
+            all += p;
+            if (k < nr) reach += p;
+        }
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+        reach += __shfl_xor_sync(0xffffffffu, reach, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&out[0], all);
+        atomicAdd(&out[1], reach);
+    }
+}
+
 }  // namespace
+
+int count_pairs(rcb_tree *t) {
+    cudaStream_t st = t->stream;
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_pairs, 0, 2 * sizeof(int64_t), st));
+    int blocks = std::max(1, std::min((t->nsinks + 7) / 8, 152 * 8));
+    k_pair_counts<<<blocks, 256, 0, st>>>(t->sinks, t->nsinks, t->ncount, t->near_list, t->near_nr, t->near_nn,
+                                          t->cap_near, (unsigned long long *)t->d_pairs); note_launch();
+    int64_t h[2];
+    RCB_CUDA_TRY(cudaMemcpyAsync(h, t->d_pairs, sizeof(h), cudaMemcpyDeviceToHost, st));
+    RCB_CUDA_TRY(cudaStreamSynchronize(st));
+    t->near_pairs = h[0];
+    t->cand_pairs = h[1];
+    return RCB_OK;
+}
 
 int walk_tree(rcb_tree *t) {
     cudaStream_t st = t->stream;
@@ -201,7 +244,7 @@ int walk_tree(rcb_tree *t) {
         RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_MAXNEAR, 0, 3 * sizeof(int), st));
         int warps = (t->nsinks + 31) / 32;
         int blocks = (warps + kWalkWarps - 1) / kWalkWarps;
-        if (blocks > 0) k_walk<<<blocks, kWalkWarps * 32, 0, st>>>(c);
+        if (blocks > 0) k_walk<<<blocks, kWalkWarps * 32, 0, st>>>(c); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());
         RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status, t->d_status, ST_NWORDS * sizeof(int), cudaMemcpyDeviceToHost, st));
         RCB_CUDA_TRY(cudaStreamSynchronize(st));
