@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput of the RCB tree pipeline (build + neighbour search + gravity) on GB300.
+
+One step = rebuild the tree from device-resident particles (Sec. 2.1 build and the per-sink
+walk), neighbour search (Sec. 2.3) and gravity (Sec. 2.4).  The headline workload is the
+uniform-density unit sphere with N = 4,194,304 particles, log-uniform masses over a 10x range,
+h for ~50 neighbours, N_ll = 12, theta = 0.7, mixed form; the FP64 form is timed on the same
+tree and reported beside it with the mixed form's error against it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank runs an independent replica on its own GPU
+(the path has no exchange step: replicas only); value = particles processed by all ranks / the
+slowest rank's time.  --impl reference times the CPU oracle on the host cores instead.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mparticles/s (RCB build+neighbours+gravity) at N=4M, mixed vs FP64 at stated err"
+UNIT = "Mparticles/s"
+N_LL = 12
+FLOPS_PER_PAIR = 24        # float32 flops of one near-field pair on its Newtonian branch (FMA = 2, MUFU = 1)
+SMS = 152
+FP32_LANES = 128           # FP32 lanes per SM
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=4194304)
+    p.add_argument("--kind", default="sphere")
+    p.add_argument("--mass", default="loguniform10")
+    p.add_argument("--theta", type=float, default=0.7)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-sinks", type=int, default=256)
+    return p.parse_args()
+
+
+def workload_name(a):
+    kinds = {"sphere": "uniform-density unit sphere", "plummer": "Plummer sphere", "cube": "uniform unit cube"}
+    return (f"{kinds.get(a.kind, a.kind)}, N={a.n}, {a.mass} masses, h for ~50 neighbours, N_ll={N_LL}, "
+            f"theta={a.theta}")
+
+
+# ------------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append({"sm": float(parts[1]), "max": float(parts[2]), "util": float(parts[4]),
+                             "hw": parts[6], "hwt": parts[7], "swt": parts[8], "pcap": parts[9]})
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r["util"] > 0] or rows
+        reasons = set()
+        for r in load:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                            ("pcap", "sw_power_cap")):
+                if r[k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["max"] for r in rows),
+                "samples_under_load": len(load), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------ CPU oracle
+def oracle_sample_run(x, m, h, theta, n_sinks, seed=7):
+    """The oracle as it stands on the host cores: full build, then walk + neighbours + gravity
+    for a seeded sample of sinks; returns (seconds for a full-N step extrapolated, details)."""
+    import numpy as np
+
+    import oracle
+    N = x.shape[0]
+    t0 = time.perf_counter()
+    T = oracle.OracleTree(x, m, h, n_ll=N_LL)
+    t_build = time.perf_counter() - t0
+    nd = T.nodes()
+    leaf0 = 1 << T.L
+    live = np.flatnonzero(nd["count"][leaf0:] > 0)
+    rng = np.random.default_rng(seed)
+    sinks = np.sort(rng.choice(live, min(n_sinks, len(live)), replace=False))
+    n_part = int(nd["count"][leaf0 + sinks].sum())
+    t0 = time.perf_counter()
+    T.walk(theta, sinks)
+    T.neighbours()
+    T.gravity()
+    t_sample = time.perf_counter() - t0
+    t_step = t_build + t_sample * N / max(n_part, 1)
+    return t_step, {"t_build_s": t_build, "t_sample_s": t_sample, "sample_particles": n_part,
+                    "sample_sinks": int(len(sinks))}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    x, m, h = synth.make_particles(a.kind, a.n, synth.seed_for(3, 0), a.mass)
+    oracle.build()
+    times = []
+    det = None
+    for i in range(a.warmup + a.steps):
+        t, det = oracle_sample_run(x, m, h, a.theta, a.cpu_sample_sinks, seed=100 + i)
+        if i >= a.warmup:
+            times.append(t)
+    t = statistics.mean(times)
+    value = a.n / t / 1e6
+    sample = (f"full-N oracle build, then walk+neighbours+gravity for {det['sample_sinks']} random sinks "
+              f"({det['sample_particles']} particles), extrapolated to N per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------ GPU
+def run_ours(a, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1108_0028_gb300 as rcb
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    rcb.lib()
+    x, m, h = synth.make_particles(a.kind, a.n, synth.seed_for(3, 0), a.mass)
+    xt = torch.from_numpy(x).to(dev)
+    mt = torch.from_numpy(m).to(dev)
+    ht = torch.from_numpy(h).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    tree = rcb.RCBTree(xt, mt, ht, n_ll=N_LL, theta=a.theta, precision="mixed", timing=True)
+
+    def step():
+        tree.rebuild(xt, mt, ht)
+        off, idx = tree.neighbours()
+        acc, pot = tree.gravity()
+        return off, idx, acc, pot
+
+    for _ in range(a.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    launches0 = tree.info()["launches"]
+    step_ms, stages = [], []
+    for _ in range(a.steps):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stages.append(tree.stage_times())
+    barrier()
+    launches = tree.info()["launches"] - launches0
+    ms = statistics.mean(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * a.n / (ms * 1e-3) / 1e6
+    stage_ms = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
+    info = tree.info()
+
+    # FP64 form on the same tree (gravity only differs), and the mixed form's error against it
+    acc_m, pot_m = tree.gravity()
+    tree.set_precision("fp64")
+    acc_d, pot_d = tree.gravity()
+    f64_grav = []
+    for _ in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        tree.gravity()
+        st = tree.stage_times()
+        f64_grav.append(st["far"] + st["near"])
+    tree.set_precision("mixed")
+    torch.cuda.synchronize()
+    e = (torch.linalg.norm(acc_m - acc_d, dim=1) / torch.linalg.norm(acc_d, dim=1)).cpu().numpy()
+    ep = (torch.abs(pot_m - pot_d) / torch.abs(pot_d)).cpu().numpy()
+    t_fp64 = ms - (stage_ms["far"] + stage_ms["near"]) + statistics.mean(f64_grav)
+    fp64 = {"value": world * a.n / (t_fp64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": t_fp64,
+            "gravity_ms": statistics.mean(f64_grav)}
+    accuracy = {"reference": "FP64 GPU form on the same tree (parity of the FP64 form with the FP64 oracle is "
+                             "tested separately: RMS 1e-15)",
+                "rms": float(np.sqrt(np.mean(e * e))), "p99.9": float(np.percentile(e, 99.9)),
+                "max": float(e.max()), "pot_rms": float(np.sqrt(np.mean(ep * ep)))}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    xh, mh, hh = (torch.from_numpy(v).pin_memory() for v in (x, m, h))
+    xd, md, hd = torch.empty_like(xt), torch.empty_like(mt), torch.empty_like(ht)
+    off0, idx0, acc0, pot0 = step()
+    offh = torch.empty(off0.shape, dtype=off0.dtype).pin_memory()
+    idxh = torch.empty(idx0.shape, dtype=idx0.dtype).pin_memory()
+    acch = torch.empty(acc0.shape, dtype=acc0.dtype).pin_memory()
+    poth = torch.empty(pot0.shape, dtype=pot0.dtype).pin_memory()
+    e2e_ms = []
+    for _ in range(max(3, a.steps // 2)):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        md.copy_(mh, non_blocking=True)
+        hd.copy_(hh, non_blocking=True)
+        tree.rebuild(xd, md, hd)
+        off, idx = tree.neighbours()
+        acc, pot = tree.gravity()
+        offh.copy_(off, non_blocking=True)
+        idxh[:idx.numel()].copy_(idx, non_blocking=True)
+        acch.copy_(acc, non_blocking=True)
+        poth.copy_(pot, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    ems = statistics.mean(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([ems], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    h2d = (x.nbytes + m.nbytes + h.nbytes)
+    d2h = offh.numel() * 8 + idx0.numel() * 4 + acch.numel() * 8 + poth.numel() * 8
+    clocks = sampler.stop() if sampler else None
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    # roofline of the dominant kernel: the near field (float32 ALU)
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    near_s = stage_ms["near"] * 1e-3
+    achieved = info["near_pairs"] * FLOPS_PER_PAIR / near_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_near_mixed",
+                "basis": f"{info['near_pairs']} near pairs x {FLOPS_PER_PAIR} FP32 flops / near-kernel event time; "
+                         f"peak = {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock under load "
+                         f"({sm_mhz:.0f} MHz)"}
+    # build: algorithmic bytes of the build kernels over their event time, against measured HBM
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        t_step, det = oracle_sample_run(x, m, h, a.theta, a.cpu_sample_sinks)
+        cpu = {"value": a.n / t_step / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": (f"full-N build ({det['t_build_s']:.2f} s), then walk+neighbours+gravity for "
+                          f"{det['sample_sinks']} random sinks ({det['sample_particles']} particles, "
+                          f"{det['t_sample_s']:.2f} s) extrapolated to N")}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: f32 near/far tensors, f64 build + Taylor coefficients; int64/int128 tree keys",
+        "data": "synthetic",
+        "config": {"workload": workload_name(a), "N": a.n, "theta": a.theta, "n_ll": N_LL, "form": "mixed",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs (164 MB) exceed L2 and a 256 MB buffer is written between timed steps"},
+        "e2e": {"value": world * a.n / (ems * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ems,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "stages_ms": stage_ms,
+        "fp64": fp64,
+        "accuracy_mixed_vs_fp64": accuracy,
+        "tree": {k: info[k] for k in ("L", "nsinks", "near_total", "far_total", "reach_total", "near_pairs",
+                                        "candidate_pairs", "walk_fp64_decisions", "smem_subtrees")},
+        "neighbours_total": int(idx0.numel()),
+        "hbm_peak_gbs": hbm,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_ours(a, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()
