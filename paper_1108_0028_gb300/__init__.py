@@ -26,7 +26,8 @@ _PRECISION = {"fp64": RCB_FP64, "mixed": RCB_MIXED, RCB_FP64: RCB_FP64, RCB_MIXE
 
 RCB_FLAG_TIMING = 1
 SYMBOLS = ["rcb_build", "rcb_neighbours", "rcb_gravity", "rcb_gravity_backward", "rcb_refit", "rcb_set_precision",
-           "rcb_tree_info", "rcb_export_topology", "rcb_export_lists", "rcb_stage_times", "rcb_free", "rcb_strerror"]
+           "rcb_tree_info", "rcb_export_topology", "rcb_export_lists", "rcb_stage_times", "rcb_free", "rcb_strerror",
+           "rcb_neighbour_offsets_noalloc"]
 STAGES = ["ingest", "levels", "subtrees", "leaves", "walk", "build", "nb_count", "nb_fill", "nb_sort", "far", "near",
           "backward"]
 
@@ -70,6 +71,7 @@ def lib():
                 "rcb_export_topology": (ctypes.c_int, [P] + [P] * 16 + [P]),
                 "rcb_export_lists": (ctypes.c_int, [P, P, P, P, I64, P, P, I64, P]),
                 "rcb_stage_times": (ctypes.c_int, [P, P, P]),
+                "rcb_neighbour_offsets_noalloc": (ctypes.c_int, [P, P, ctypes.POINTER(I64), P]),
                 "rcb_free": (None, [P]),
                 "rcb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             }

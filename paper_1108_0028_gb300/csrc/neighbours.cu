@@ -286,6 +286,35 @@ int sm_count_nb() {
 
 }  // namespace
 
+int neighbour_counts(rcb_tree *t, int64_t *counts, int *status) {
+    NbCtx c;
+    c.nsinks = t->nsinks;
+    c.sinks = t->sinks;
+    c.near_list = t->near_list;
+    c.near_nr = t->near_nr;
+    c.cap_near = t->cap_near;
+    c.nfirst = t->nfirst;
+    c.ncount = t->ncount;
+    c.ncom = t->ncom;
+    c.px = t->px;
+    c.py = t->py;
+    c.pz = t->pz;
+    c.ph = t->ph;
+    c.pidx = t->pidx;
+    c.p32 = t->p32;
+    c.counts = counts;
+    c.offsets = nullptr;
+    c.idx = nullptr;
+    c.status = status;
+    const int nsm = sm_count_nb();
+    const size_t smem = sizeof(NbSmem);
+    const int blocks = std::max(1, std::min((t->nsinks + kNbWarps - 1) / kNbWarps, nsm * 16));
+    RCB_CUDA_TRY(cudaFuncSetAttribute(k_neighbours<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_neighbours<false><<<blocks, kNbWarps * 32, smem, t->stream>>>(c); note_launch();
+    RCB_CUDA_TRY(cudaGetLastError());
+    return RCB_OK;
+}
+
 int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *needed) {
     cudaStream_t st = t->stream;
     NbCtx c;

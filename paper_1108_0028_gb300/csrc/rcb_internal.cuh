@@ -268,6 +268,7 @@ int refit_tree(rcb_tree *t, const double *x, const double *m);
 // walk.cu
 int walk_tree(rcb_tree *t);
 // neighbours.cu
+int neighbour_counts(rcb_tree *t, int64_t *counts, int *status);  // count pass into caller memory
 int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *needed);
 // gravity.cu
 int gravity(rcb_tree *t, double *acc, double *pot);
