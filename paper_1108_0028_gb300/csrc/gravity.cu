@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "far_math.cuh"
 #include "rcb_internal.cuh"
@@ -35,6 +36,8 @@ namespace rcb {
 namespace {
 
 constexpr int kGWarps = 4;
+constexpr int kGroupMixed = 8;  // sink particles per group (mixed near kernel)
+constexpr int kGroupF64 = 4;
 constexpr int kNearTileMixed = 1024;
 constexpr int kNearTileF64 = 384;
 
@@ -180,18 +183,66 @@ __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_
     return staged;
 }
 
-constexpr int kGroupMixed = 8;  // sink particles per register group (mixed)
-constexpr int kGroupF64 = 4;
 
-__global__ void __launch_bounds__(kGWarps * 32) k_near_mixed(GCtx c) {
+constexpr int kNearWarps = 8;     // warps per block of the mixed near kernel
+constexpr int kNearTile = 512;    // staged sources per warp
+constexpr size_t kNearWarpBytes = kNearTile * (sizeof(float4) + sizeof(float) + sizeof(int32_t)) +
+                                  kGroupMixed * (sizeof(float4) + sizeof(int32_t));
+
+// Stage sources [t0, t0 + kNearTile) of the sink's near cells, one lane per cell: float32
+// offsets from the sink's centre of mass (double-float difference of the two centres of mass
+// plus the particle's float32 offset from its own cell's centre), mass, h, sorted index.
+__device__ int stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, int64_t t0, float4 *src, float *hs,
+                                int32_t *si) {
+    const int lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)s * c.cap_near;
+    const float2 a0 = c.ncomdf[3 * (int64_t)A], a1 = c.ncomdf[3 * (int64_t)A + 1], a2 = c.ncomdf[3 * (int64_t)A + 2];
+    int64_t pos = 0;
+    for (int k0 = 0; k0 < nlist && pos < t0 + kNearTile; k0 += 32) {
+        const int k = k0 + lane;
+        int f = 0, n = 0;
+        float ox = 0.f, oy = 0.f, oz = 0.f;
+        if (k < nlist) {
+            const int B = near_entry(c, base, nr, k);
+            f = c.nfirst[B];
+            n = c.ncount[B];
+            const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1], b2 = c.ncomdf[3 * (int64_t)B + 2];
+            ox = (b0.x - a0.x) + (b0.y - a0.y);
+            oy = (b1.x - a1.x) + (b1.y - a1.y);
+            oz = (b2.x - a2.x) + (b2.y - a2.y);
+        }
+        int incl = n;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int64_t my0 = pos + incl - n;
+        for (int q = 0; q < n; ++q) {
+            const int64_t slot = my0 + q - t0;
+            if (slot >= 0 && slot < kNearTile) {
+                const float4 pb = c.p32[f + q];
+                src[slot] = make_float4(ox + pb.x, oy + pb.y, oz + pb.z, pb.w);
+                hs[slot] = c.h32[f + q];
+                si[slot] = f + q;
+            }
+        }
+        pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    const int64_t left = pos - t0;
+    return (int)(left < kNearTile ? left : kNearTile);
+}
+
+__global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // per-warp region: src float4[T], hs float[T], sidx int[T]
-    unsigned char *smw = smem_raw + (size_t)w * kNearTileMixed * (sizeof(float4) + sizeof(float) + sizeof(int32_t));
+    unsigned char *smw = smem_raw + (size_t)w * kNearWarpBytes;
     float4 *src = reinterpret_cast<float4 *>(smw);
-    float *hs = reinterpret_cast<float *>(src + kNearTileMixed);
-    int32_t *si = reinterpret_cast<int32_t *>(hs + kNearTileMixed);
-    for (int s = blockIdx.x * kGWarps + w; s < c.nsinks; s += gridDim.x * kGWarps) {
+    float *hs = reinterpret_cast<float *>(src + kNearTile);
+    int32_t *si = reinterpret_cast<int32_t *>(hs + kNearTile);
+    float4 *snk = reinterpret_cast<float4 *>(si + kNearTile);  // (d_a, h_a) of the current group
+    int32_t *sid = reinterpret_cast<int32_t *>(snk + kGroupMixed);
+    for (int s = blockIdx.x * kNearWarps + w; s < c.nsinks; s += gridDim.x * kNearWarps) {
         const int A = c.sinks[s];
         const int fA = c.nfirst[A], nA = c.ncount[A];
         const int nr = c.near_nr[s], nlist = nr + c.near_nn[s];
@@ -199,36 +250,22 @@ __global__ void __launch_bounds__(kGWarps * 32) k_near_mixed(GCtx c) {
         int64_t S = 0;
         for (int k = lane; k < nlist; k += 32) S += c.ncount[near_entry(c, base, nr, k)];
         for (int o = 16; o >= 1; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
-        bool staged_all = false;
-        int ns_all = 0;
+        int ns_once = -1;  // staged tile count when all sources fit one tile
         for (int a0 = 0; a0 < nA; a0 += kGroupMixed) {
             const int na = min(kGroupMixed, nA - a0);
-            float sx[kGroupMixed], sy[kGroupMixed], sz[kGroupMixed], sh[kGroupMixed];
-            int sid[kGroupMixed];
-#pragma unroll
-            for (int i = 0; i < kGroupMixed; ++i) {
-                const int a = fA + a0 + min(i, na - 1);
-                const float4 pa = c.p32[a];
-                sx[i] = pa.x;
-                sy[i] = pa.y;
-                sz[i] = pa.z;
-                sh[i] = c.h32[a];
-                sid[i] = i < na ? a : -1;
+            if (lane < kGroupMixed) {
+                const int i = min(lane, na - 1);
+                const float4 pa = c.p32[fA + a0 + i];
+                snk[lane] = make_float4(pa.x, pa.y, pa.z, c.h32[fA + a0 + i]);
+                sid[lane] = lane < na ? fA + a0 + i : -1;
             }
-            float As[4][kGroupMixed], Ac[4][kGroupMixed];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int i = 0; i < kGroupMixed; ++i) As[q][i] = Ac[q][i] = 0.f;
-            for (int64_t t0 = 0; t0 < S; t0 += kNearTileMixed) {
-                int ns;
-                if (staged_all) ns = ns_all;
-                else {
-                    ns = stage_near<true>(c, s, A, nlist, nr, t0, kNearTileMixed, smw);
-                    if (S <= kNearTileMixed) {
-                        staged_all = true;
-                        ns_all = ns;
-                    }
+            __syncwarp();
+            float rs = 0.f, rc = 0.f;  // compensated total of value `lane` (= 4 i + q)
+            for (int64_t t0 = 0; t0 < S; t0 += kNearTile) {
+                int ns = ns_once;
+                if (ns < 0) {
+                    ns = stage_near_mixed(c, s, A, nlist, nr, t0, src, hs, si);
+                    if (S <= kNearTile) ns_once = ns;
                 }
                 float In[4][kGroupMixed];
 #pragma unroll
@@ -248,9 +285,10 @@ __global__ void __launch_bounds__(kGWarps * 32) k_near_mixed(GCtx c) {
 #pragma unroll
                     for (int i = 0; i < kGroupMixed; ++i) {
                         if (i < na) {
+                            const float4 sa = snk[i];
                             const float mb = bid == sid[i] ? 0.f : b.w;
                             float ax, ay, az, ph;
-                            pair_force<float>(sx[i] - b.x, sy[i] - b.y, sz[i] - b.z, sh[i] + hb, mb, ax, ay, az, ph);
+                            pair_force<float>(sa.x - b.x, sa.y - b.y, sa.z - b.z, sa.w + hb, mb, ax, ay, az, ph);
                             In[0][i] += ax;
                             In[1][i] += ay;
                             In[2][i] += az;
@@ -258,27 +296,27 @@ __global__ void __launch_bounds__(kGWarps * 32) k_near_mixed(GCtx c) {
                         }
                     }
                 }
+                // fold this tile: compensated reduce-scatter across lanes, then into (rs, rc)
+                float Vs[32], Vc[32];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
+                for (int i = 0; i < kGroupMixed; ++i)
 #pragma unroll
-                    for (int i = 0; i < kGroupMixed; ++i) comp_add(As[q][i], Ac[q][i], In[q][i]);
+                    for (int q = 0; q < 4; ++q) {
+                        Vs[4 * i + q] = In[q][i];
+                        Vc[4 * i + q] = 0.f;
+                    }
+                reduce_scatter_df<32>(Vs, Vc);
+                float t, e;
+                two_sum(rs, Vs[0], t, e);
+                rs = t;
+                rc = __fadd_rn(__fadd_rn(rc, Vc[0]), e);
                 __syncwarp();
             }
-            // reduce: value v = 4 i + q
-            float Vs[32], Vc[32];
-#pragma unroll
-            for (int i = 0; i < kGroupMixed; ++i)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    Vs[4 * i + q] = As[q][i];
-                    Vc[4 * i + q] = Ac[q][i];
-                }
-            reduce_scatter_df<32>(Vs, Vc);
-            const double tot = __dadd_rn((double)Vs[0], (double)Vc[0]);  // lane l: particle l/4, quantity l%4
-            double q0v = __shfl_sync(0xffffffffu, tot, (4 * lane) & 31);
-            double q1v = __shfl_sync(0xffffffffu, tot, (4 * lane + 1) & 31);
-            double q2v = __shfl_sync(0xffffffffu, tot, (4 * lane + 2) & 31);
-            double q3v = __shfl_sync(0xffffffffu, tot, (4 * lane + 3) & 31);
+            const double tot = __dadd_rn((double)rs, (double)rc);  // lane l: particle l/4, quantity l%4
+            const double q0v = __shfl_sync(0xffffffffu, tot, (4 * lane) & 31);
+            const double q1v = __shfl_sync(0xffffffffu, tot, (4 * lane + 1) & 31);
+            const double q2v = __shfl_sync(0xffffffffu, tot, (4 * lane + 2) & 31);
+            const double q3v = __shfl_sync(0xffffffffu, tot, (4 * lane + 3) & 31);
             if (lane < na) {
                 const int a = fA + a0 + lane;
                 const float4 pa = c.p32[a];
@@ -294,8 +332,8 @@ __global__ void __launch_bounds__(kGWarps * 32) k_near_mixed(GCtx c) {
                 c.acc[3 * (int64_t)o + 2] = q2v + (double)af[2];
                 if (c.pot) c.pot[o] = q3v + (double)phf;
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
@@ -400,6 +438,27 @@ int sm_count_g() {
 
 }  // namespace
 
+// FP64 Taylor coefficients of every sink into t->coef (used by the backward pass).
+int far_coefficients_fp64(rcb_tree *t) {
+    GCtx c;
+    std::memset(&c, 0, sizeof(c));
+    c.nsinks = t->nsinks;
+    c.sinks = t->sinks;
+    c.far_list = t->far_list;
+    c.far_n = t->far_n;
+    c.cap_far = t->cap_far;
+    c.ncom = t->ncom;
+    c.nmass = t->nmass;
+    c.nQ = t->nQ;
+    c.coef = t->coef;
+    if (t->nsinks == 0) return RCB_OK;
+    const int nsm = sm_count_g();
+    const int blocks = std::max(1, std::min((t->nsinks + kGWarps - 1) / kGWarps, nsm * 32));
+    k_far<false><<<blocks, kGWarps * 32, 0, t->stream>>>(c); note_launch();
+    RCB_CUDA_TRY(cudaGetLastError());
+    return RCB_OK;
+}
+
 int gravity(rcb_tree *t, double *acc, double *pot) {
     cudaStream_t st = t->stream;
     GCtx c;
@@ -439,11 +498,12 @@ int gravity(rcb_tree *t, double *acc, double *pot) {
     if (mixed) {
         stage_begin(t, SG_FAR);
         k_far<true><<<blocks, kGWarps * 32, 0, st>>>(c); note_launch();
-        const size_t smem = (size_t)kGWarps * kNearTileMixed * (sizeof(float4) + sizeof(float) + sizeof(int32_t));
+        const size_t smem = (size_t)kNearWarps * kNearWarpBytes;
         RCB_CUDA_TRY(cudaFuncSetAttribute(k_near_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         stage_end(t, SG_FAR);
         stage_begin(t, SG_NEAR);
-        k_near_mixed<<<blocks, kGWarps * 32, smem, st>>>(c); note_launch();
+        const int nb = std::max(1, std::min((t->nsinks + kNearWarps - 1) / kNearWarps, nsm * 2 * 16));
+        k_near_mixed<<<nb, kNearWarps * 32, smem, st>>>(c); note_launch();
     } else {
         stage_begin(t, SG_FAR);
         k_far<false><<<blocks, kGWarps * 32, 0, st>>>(c); note_launch();

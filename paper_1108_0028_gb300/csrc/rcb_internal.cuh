@@ -233,6 +233,9 @@ struct rcb_tree {
     float *coef32;   // their float32 values (mixed form)
     int64_t *nb_count;
     int32_t *nb_long;  // [N] rows queued for the block-level sort
+    int64_t *nb_maskoff;  // [nleaves + 1] word offsets of each sink's neighbour masks
+    uint32_t *nb_masks;   // ballot masks of the count pass (grown on demand)
+    int64_t cap_masks;
     void *scan_tmp;
     int64_t cap_scan;
     int64_t nb_total;
