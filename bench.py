@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--theta", type=float, default=0.7)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-sinks", type=int, default=256)
+    p.add_argument("--headline-only", action="store_true",
+                   help="time only the headline step (no FP64 form, accuracy, e2e or CPU legs); for profiling")
     return p.parse_args()
 
 
@@ -166,68 +168,10 @@ def run_reference(a, rank, world):
 
 
 # ------------------------------------------------------------------------------------------ GPU
-def run_ours(a, rank, world, local_rank):
+def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, barrier, ms, stage_ms):
+    """FP64 form on the same tree, the mixed form's error against it, and the end-to-end leg."""
     import numpy as np
     import torch
-
-    import paper_1108_0028_gb300 as rcb
-    import synth
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    rcb.lib()
-    x, m, h = synth.make_particles(a.kind, a.n, synth.seed_for(3, 0), a.mass)
-    xt = torch.from_numpy(x).to(dev)
-    mt = torch.from_numpy(m).to(dev)
-    ht = torch.from_numpy(h).to(dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-
-    tree = rcb.RCBTree(xt, mt, ht, n_ll=N_LL, theta=a.theta, precision="mixed", timing=True)
-
-    def step():
-        tree.rebuild(xt, mt, ht)
-        off, idx = tree.neighbours()
-        acc, pot = tree.gravity()
-        return off, idx, acc, pot
-
-    for _ in range(a.warmup):
-        step()
-    barrier()
-    sampler = ClockSampler(local_rank) if rank == 0 else None
-    launches0 = tree.info()["launches"]
-    step_ms, stages = [], []
-    for _ in range(a.steps):
-        flush.zero_()
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        stages.append(tree.stage_times())
-    barrier()
-    launches = tree.info()["launches"] - launches0
-    ms = statistics.mean(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * a.n / (ms * 1e-3) / 1e6
-    stage_ms = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
-    info = tree.info()
 
     # FP64 form on the same tree (gravity only differs), and the mixed form's error against it
     acc_m, pot_m = tree.gravity()
@@ -271,8 +215,7 @@ def run_ours(a, rank, world, local_rank):
         md.copy_(mh, non_blocking=True)
         hd.copy_(hh, non_blocking=True)
         tree.rebuild(xd, md, hd)
-        off, idx = tree.neighbours()
-        acc, pot = tree.gravity()
+        acc, pot, off, idx = tree.gravity_neighbours()
         offh.copy_(off, non_blocking=True)
         idxh[:idx.numel()].copy_(idx, non_blocking=True)
         acch.copy_(acc, non_blocking=True)
@@ -282,11 +225,82 @@ def run_ours(a, rank, world, local_rank):
         e2e_ms.append(e0.elapsed_time(e1))
     ems = statistics.mean(e2e_ms)
     if dist is not None:
-        t = torch.tensor([ems], device=dev)
+        t = torch.tensor([ems], device=xt.device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ems = float(t.item())
     h2d = (x.nbytes + m.nbytes + h.nbytes)
     d2h = offh.numel() * 8 + idx0.numel() * 4 + acch.numel() * 8 + poth.numel() * 8
+    e2e = {"value": world * a.n / (ems * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ems,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    return fp64, accuracy, e2e, int(idx0.numel())
+
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+
+    import paper_1108_0028_gb300 as rcb
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    rcb.lib()
+    x, m, h = synth.make_particles(a.kind, a.n, synth.seed_for(3, 0), a.mass)
+    xt = torch.from_numpy(x).to(dev)
+    mt = torch.from_numpy(m).to(dev)
+    ht = torch.from_numpy(h).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    tree = rcb.RCBTree(xt, mt, ht, n_ll=N_LL, theta=a.theta, precision="mixed", timing=True)
+
+    def step():
+        tree.rebuild(xt, mt, ht)
+        acc, pot, off, idx = tree.gravity_neighbours()
+        return off, idx, acc, pot
+
+    for _ in range(a.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    launches0 = tree.info()["launches"]
+    step_ms, stages = [], []
+    for _ in range(a.steps):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stages.append(tree.stage_times())
+    barrier()
+    launches = tree.info()["launches"] - launches0
+    ms = statistics.mean(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * a.n / (ms * 1e-3) / 1e6
+    stage_ms = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
+    info = tree.info()
+
+    fp64 = accuracy = e2e = None
+    idx_total = None
+    if not a.headline_only:
+        fp64, accuracy, e2e, idx_total = extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step,
+                                                    barrier, ms, stage_ms)
     clocks = sampler.stop() if sampler else None
 
     if rank != 0:
@@ -300,7 +314,8 @@ def run_ours(a, rank, world, local_rank):
     achieved = info["near_pairs"] * FLOPS_PER_PAIR / near_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "k_near_mixed",
-                "basis": f"{info['near_pairs']} near pairs x {FLOPS_PER_PAIR} FP32 flops / near-kernel event time; "
+                "basis": f"{info['near_pairs']} near pairs x {FLOPS_PER_PAIR} FP32 flops (the neighbour tests fused into "
+                         f"the same kernel not counted) / near-kernel event time; "
                          f"peak = {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock under load "
                          f"({sm_mhz:.0f} MHz)"}
     # build: algorithmic bytes of the build kernels over their event time, against measured HBM
@@ -311,7 +326,7 @@ def run_ours(a, rank, world, local_rank):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     cpu = None
-    if not a.no_cpu_baseline and world == 1:
+    if not a.no_cpu_baseline and not a.headline_only and world == 1:
         import oracle
         oracle.build()
         t_step, det = oracle_sample_run(x, m, h, a.theta, a.cpu_sample_sinks)
@@ -327,8 +342,7 @@ def run_ours(a, rank, world, local_rank):
         "config": {"workload": workload_name(a), "N": a.n, "theta": a.theta, "n_ll": N_LL, "form": "mixed",
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs (164 MB) exceed L2 and a 256 MB buffer is written between timed steps"},
-        "e2e": {"value": world * a.n / (ems * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ems,
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": roofline,
@@ -338,7 +352,7 @@ def run_ours(a, rank, world, local_rank):
         "accuracy_mixed_vs_fp64": accuracy,
         "tree": {k: info[k] for k in ("L", "nsinks", "near_total", "far_total", "reach_total", "near_pairs",
                                         "candidate_pairs", "walk_fp64_decisions", "smem_subtrees")},
-        "neighbours_total": int(idx0.numel()),
+        "neighbours_total": idx_total,
         "hbm_peak_gbs": hbm,
     }
     print(json.dumps(line), flush=True)

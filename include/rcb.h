@@ -115,6 +115,21 @@ int rcb_neighbours(rcb_tree *tree, int64_t *offsets, int32_t *idx, int64_t capac
 int rcb_gravity(rcb_tree *tree, double *acc, double *pot, void *stream);
 
 /*
+ * rcb_gravity_neighbours -- rcb_gravity and the counting half of rcb_neighbours in one call
+ *   (Sec. 2.3 and Sec. 2.4 over the same near list).  In the mixed form one kernel stages each
+ *   sink's near-list particles once, evaluates the near field and tests the candidate pairs for
+ *   |r_a - r_b| < 2 h_a (the same exact decisions as rcb_neighbours); the FP64 form runs the two
+ *   passes one after the other.
+ *   acc, pot  as for rcb_gravity
+ *   offsets   device, [N + 1] int64, written as rcb_neighbours writes it
+ *   needed    host, the total number of neighbour entries
+ *   A following rcb_neighbours call with the same tree writes the index list without counting
+ *   again (until the next rcb_build or rcb_refit).
+ */
+int rcb_gravity_neighbours(rcb_tree *tree, double *acc, double *pot, int64_t *offsets, int64_t *needed,
+                           void *stream);
+
+/*
  * rcb_gravity_backward -- vector-Jacobian product of rcb_gravity with respect to positions and
  *   masses, with the tree's particle sets and interaction lists held fixed (no paper
  *   counterpart; the forward it differentiates is Sec. 2.4).  Node moments are differentiated

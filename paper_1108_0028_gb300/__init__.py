@@ -25,7 +25,7 @@ RCB_FP64, RCB_MIXED = 0, 1
 _PRECISION = {"fp64": RCB_FP64, "mixed": RCB_MIXED, RCB_FP64: RCB_FP64, RCB_MIXED: RCB_MIXED}
 
 RCB_FLAG_TIMING = 1
-SYMBOLS = ["rcb_build", "rcb_neighbours", "rcb_gravity", "rcb_gravity_backward", "rcb_refit", "rcb_set_precision",
+SYMBOLS = ["rcb_build", "rcb_neighbours", "rcb_gravity", "rcb_gravity_neighbours", "rcb_gravity_backward", "rcb_refit", "rcb_set_precision",
            "rcb_tree_info", "rcb_export_topology", "rcb_export_lists", "rcb_stage_times", "rcb_free", "rcb_strerror",
            "rcb_neighbour_offsets_noalloc"]
 STAGES = ["ingest", "levels", "subtrees", "leaves", "walk", "build", "nb_count", "nb_fill", "nb_sort", "far", "near",
@@ -64,6 +64,7 @@ def lib():
                 "rcb_build": (ctypes.c_int, [P, P, P, I64, ctypes.POINTER(rcb_params), P, P, P, P, ctypes.POINTER(P)]),
                 "rcb_neighbours": (ctypes.c_int, [P, P, P, I64, ctypes.POINTER(I64), P]),
                 "rcb_gravity": (ctypes.c_int, [P, P, P, P]),
+                "rcb_gravity_neighbours": (ctypes.c_int, [P, P, P, P, ctypes.POINTER(I64), P]),
                 "rcb_gravity_backward": (ctypes.c_int, [P, P, P, P, P, P]),
                 "rcb_refit": (ctypes.c_int, [P, P, P, P]),
                 "rcb_set_precision": (ctypes.c_int, [P, I32]),
@@ -146,6 +147,13 @@ def rcb_neighbours(tree, offsets, idx, capacity, stream=None):
 
 def rcb_gravity(tree, acc, pot=None, stream=None):
     _check(lib().rcb_gravity(tree, _dptr(acc), _dptr(pot), _stream_ptr(stream)), "rcb_gravity")
+
+
+def rcb_gravity_neighbours(tree, acc, pot, offsets, stream=None):
+    needed = ctypes.c_int64(0)
+    _check(lib().rcb_gravity_neighbours(tree, _dptr(acc), _dptr(pot), _dptr(offsets), ctypes.byref(needed),
+                                        _stream_ptr(stream)), "rcb_gravity_neighbours")
+    return needed.value
 
 
 def rcb_gravity_backward(tree, g_acc, g_pot, g_x, g_m, stream=None):
@@ -232,6 +240,19 @@ class RCBTree:
         pot = torch.empty(self.N, dtype=torch.float64, device=self.device) if with_pot else None
         rcb_gravity(self._h, acc, pot, stream)
         return acc, pot
+
+    def gravity_neighbours(self, stream=None, with_pot: bool = True):
+        """Forces and neighbour lists from one pass over the near lists: (acc, pot, offsets, idx)."""
+        torch = _torch()
+        acc = torch.empty((self.N, 3), dtype=torch.float64, device=self.device)
+        pot = torch.empty(self.N, dtype=torch.float64, device=self.device) if with_pot else None
+        offsets = torch.empty(self.N + 1, dtype=torch.int64, device=self.device)
+        needed = rcb_gravity_neighbours(self._h, acc, pot, offsets, stream)
+        idx = torch.empty(max(needed, 1), dtype=torch.int32, device=self.device)
+        st, needed = rcb_neighbours(self._h, offsets, idx, idx.numel(), stream)
+        _check(st, "rcb_neighbours")
+        self._nb_cap = max(self._nb_cap, needed)
+        return acc, pot, offsets, idx[:needed]
 
     def gravity_backward(self, g_acc, g_pot=None, stream=None):
         torch = _torch()

@@ -153,43 +153,20 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_taylor(BCtx c) {
                 const double d[3] = {c.px[a] - cA[0], c.py[a] - cA[1], c.pz[a] - cA[2]};
                 const double v[3] = {c.gA[3 * (int64_t)a], c.gA[3 * (int64_t)a + 1], c.gA[3 * (int64_t)a + 2]};
                 const double w = c.gP[a];
-                double g[3], H[3][3];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    g[i] = C[1 + i];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        H[i][j] = C[4 + s2(i, j)];
-                        g[i] += C[4 + s2(i, j)] * d[j];
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            g[i] += 0.5 * C[10 + s3(i, j, k)] * d[j] * d[k];
-                            H[i][j] += C[10 + s3(i, j, k)] * d[k];
-                        }
-                    }
-                }
-                double gd[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) gd[k] = w * g[k] - (v[0] * H[0][k] + v[1] * H[1][k] + v[2] * H[2][k]);
+                double g[3], H[6];
+                taylor_grad_hess<double>(C, d[0], d[1], d[2], g, H);
+                // dL/dd_k = w grad_k - sum_i v_i Hess_ik
+                const double gd[3] = {w * g[0] - (v[0] * H[0] + v[1] * H[1] + v[2] * H[2]),
+                                      w * g[1] - (v[0] * H[1] + v[1] * H[3] + v[2] * H[4]),
+                                      w * g[2] - (v[0] * H[2] + v[1] * H[4] + v[2] * H[5])};
                 c.gxs[3 * (int64_t)a] = gd[0];
                 c.gxs[3 * (int64_t)a + 1] = gd[1];
                 c.gxs[3 * (int64_t)a + 2] = gd[2];
                 c.gms[a] = 0.0;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) comb[k] -= gd[k];
-                // dL/dC: Phi = C0 + C1.d + 1/2 C2:dd + 1/6 C3:ddd, a_i = -(dPhi/dd_i)
-                cb[0] += w;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    cb[1 + i] += w * d[i] - v[i];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        cb[4 + s2(i, j)] += 0.5 * w * d[i] * d[j] - v[i] * d[j];
-#pragma unroll
-                        for (int k = 0; k < 3; ++k)
-                            cb[10 + s3(i, j, k)] += w * d[i] * d[j] * d[k] * (1.0 / 6.0) - 0.5 * v[i] * d[j] * d[k];
-                    }
-                }
+                comb[0] -= gd[0];
+                comb[1] -= gd[1];
+                comb[2] -= gd[2];
+                taylor_cbar<double>(d[0], d[1], d[2], v[0], v[1], v[2], w, cb);
             }
         }
 #pragma unroll
@@ -519,18 +496,15 @@ __global__ void k_bwd_nodes(BCtx c) {
             for (int k = 0; k < 3; ++k) d[k] = x[k] - c.ncom[3 * (int64_t)n + k];
             const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             gm += Mb + (Cb[0] * d[0] + Cb[1] * d[1] + Cb[2] * d[2]) / M;
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = i; j < 3; ++j) {
-                    const double qb = Qb[s2(i, j)];
-                    gm += qb * (3.0 * d[i] * d[j] - (i == j ? d2 : 0.0));
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const double dq = 3.0 * ((i == k ? d[j] : 0.0) + (j == k ? d[i] : 0.0)) - (i == j ? 2.0 * d[k] : 0.0);
-                        gx[k] += qb * mb * dq;
-                    }
-                }
+            // slots xx, xy, xz, yy, yz, zz of Q = sum m (3 d d - d^2 I):
+            //   dQ_ij/dm = 3 d_i d_j - d^2 d_ij
+            //   dQ_ij/dx_k = m (3 (d_ik d_j + d_i d_jk) - 2 d_k d_ij)
+            gm += Qb[0] * (3.0 * d[0] * d[0] - d2) + Qb[1] * 3.0 * d[0] * d[1] + Qb[2] * 3.0 * d[0] * d[2] +
+                  Qb[3] * (3.0 * d[1] * d[1] - d2) + Qb[4] * 3.0 * d[1] * d[2] + Qb[5] * (3.0 * d[2] * d[2] - d2);
+            const double tr = Qb[0] + Qb[3] + Qb[5];
+            gx[0] += mb * (6.0 * Qb[0] * d[0] + 3.0 * Qb[1] * d[1] + 3.0 * Qb[2] * d[2] - 2.0 * tr * d[0]);
+            gx[1] += mb * (3.0 * Qb[1] * d[0] + 6.0 * Qb[3] * d[1] + 3.0 * Qb[4] * d[2] - 2.0 * tr * d[1]);
+            gx[2] += mb * (3.0 * Qb[2] * d[0] + 3.0 * Qb[4] * d[1] + 6.0 * Qb[5] * d[2] - 2.0 * tr * d[2]);
 #pragma unroll
             for (int k = 0; k < 3; ++k) gx[k] += Cb[k] * mb / M;
         }

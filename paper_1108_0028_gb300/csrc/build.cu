@@ -211,7 +211,8 @@ __global__ void k_ingest_write(const double *__restrict__ x, const double *__res
 }
 
 // Root cell (level 0) from the ingest partials; queue it as a large cell or a subtree root.
-__global__ void k_root_finalize(Ctx c, const Red *partials, int nparts, int32_t *big_list, int32_t *roots) {
+__global__ void k_root_finalize(Ctx c, const Red *partials, int nparts, int32_t *big_list, int32_t *roots,
+                                int32_t *nbig_lvl) {
     __shared__ Red scratch[32];
     Red r;
     red_init(r);
@@ -222,6 +223,7 @@ __global__ void k_root_finalize(Ctx c, const Red *partials, int nparts, int32_t 
         if (r.n > kTcta && c.L > 0) {
             big_list[0] = 1;
             c.status[ST_NBIG] = 1;
+            nbig_lvl[0] = 1;
         } else {
             roots[0] = (1 << 1) | 0;
             c.status[ST_NROOTS] = 1;
@@ -240,8 +242,9 @@ struct ChunkPart {
 };
 
 // Chunk list of the large cells of one level (single block).
-__global__ void k_chunk_plan(const int32_t *big, int nbig, const int32_t *nfirst, const int32_t *ncount,
+__global__ void k_chunk_plan(const int32_t *big, const int32_t *nbig_ptr, const int32_t *nfirst, const int32_t *ncount,
                              int32_t *cell_chunk0, int4 *chunks, int *status) {
+    const int nbig = *nbig_ptr;
     __shared__ int warp_tot[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -347,9 +350,10 @@ __global__ void __launch_bounds__(kChunkThreads) k_level_reduce(Ctx c, const int
 }
 
 // Per large cell (one warp each): chunk offsets, both children, and their classification.
-__global__ void k_level_finalize(Ctx c, int level, const int32_t *big, int nbig, const int32_t *cell_chunk0,
-                                 const int *nchunks_ptr, ChunkPart *parts, int32_t *big_next, int32_t *roots,
-                                 int parity_next) {
+__global__ void k_level_finalize(Ctx c, int level, const int32_t *big, const int32_t *nbig_ptr,
+                                 const int32_t *cell_chunk0, const int *nchunks_ptr, ChunkPart *parts,
+                                 int32_t *big_next, int32_t *nbig_next, int32_t *roots, int parity_next) {
+    const int nbig = *nbig_ptr;
     int lane = threadIdx.x & 31;
     int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nw = (gridDim.x * blockDim.x) >> 5;
@@ -411,7 +415,7 @@ __global__ void k_level_finalize(Ctx c, int level, const int32_t *big, int nbig,
             for (int s = 0; s < 2; ++s) {
                 if (kn[s] == 0) continue;
                 if (kn[s] > kTcta && level + 1 < c.L) {
-                    int slot = atomicAdd(&c.status[ST_NBIG], 1);
+                    int slot = atomicAdd(nbig_next, 1);
                     if (slot < c.cap_big) big_next[slot] = kids[s];
                     else atomicOr(&c.status[ST_ERR], ERRBIT_STATE);
                 } else {
@@ -849,6 +853,7 @@ struct PackCtx {
     const double *nmass, *ncom, *nrg, *nH, *nhint, *nQ;
     float4 *w32a, *w32b, *mq32a, *mq32b;
     float2 *ncomdf;
+    float4 *nfar;
 };
 
 __global__ void k_pack_nodes(PackCtx c, int64_t nn) {
@@ -859,6 +864,7 @@ __global__ void k_pack_nodes(PackCtx c, int64_t nn) {
             c.mq32a[n] = make_float4(0.f, 0.f, 0.f, 0.f);
             c.mq32b[n] = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int d = 0; d < 3; ++d) c.ncomdf[3 * n + d] = make_float2(0.f, 0.f);
+            for (int k = 0; k < 4; ++k) c.nfar[4 * n + k] = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
         }
         c.w32a[n] = make_float4(__double2float_rn(c.nrg[3 * n]), __double2float_rn(c.nrg[3 * n + 1]),
@@ -869,7 +875,16 @@ __global__ void k_pack_nodes(PackCtx c, int64_t nn) {
                                  __double2float_rn(c.nQ[6 * n + 1]), __double2float_rn(c.nQ[6 * n + 2]));
         c.mq32b[n] = make_float4(__double2float_rn(c.nQ[6 * n + 3]), __double2float_rn(c.nQ[6 * n + 4]),
                                  __double2float_rn(c.nQ[6 * n + 5]), 0.f);
-        for (int d = 0; d < 3; ++d) c.ncomdf[3 * n + d] = to_df(c.ncom[3 * n + d]);
+        float2 df[3];
+        for (int d = 0; d < 3; ++d) {
+            df[d] = to_df(c.ncom[3 * n + d]);
+            c.ncomdf[3 * n + d] = df[d];
+        }
+        const float4 qa = c.mq32a[n], qb = c.mq32b[n];
+        c.nfar[4 * n] = make_float4(df[0].x, df[1].x, df[2].x, qa.x);
+        c.nfar[4 * n + 1] = make_float4(df[0].y, df[1].y, df[2].y, qa.y);
+        c.nfar[4 * n + 2] = make_float4(qa.z, qa.w, qb.x, qb.y);
+        c.nfar[4 * n + 3] = make_float4(qb.z, 0.f, 0.f, 0.f);
     }
 }
 
@@ -951,6 +966,107 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const TI *in, int64
     for (int j = 0; j < kScanPer; ++j) {
         if (base + j < n) out[base + j] = ex;
         ex += loc[j];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Refit (Sec. 2.1.8): same particle sets, new positions and masses.
+
+__global__ void k_refit_scan(const double *__restrict__ x, const double *__restrict__ m, int64_t N, int *status,
+                             unsigned long long *maxbits) {
+    unsigned long long mx[4] = {0, 0, 0, 0};
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double mi = m[i];
+        if (!isfinite(mi) || !(mi > 0.0)) bad = true;
+        for (int d = 0; d < 3; ++d) {
+            const double xi = x[3 * i + d];
+            if (!isfinite(xi)) bad = true;
+            const double p = fabs(__dmul_rn(mi, __dadd_rn(xi, 0.0)));
+            const unsigned long long b = (unsigned long long)__double_as_longlong(p);
+            if (isfinite(p) && b > mx[d]) mx[d] = b;
+        }
+        const unsigned long long bm = (unsigned long long)__double_as_longlong(mi);
+        if (mi > 0.0 && isfinite(mi) && bm > mx[3]) mx[3] = bm;
+    }
+    for (int k = 0; k < 4; ++k) {
+        unsigned long long v = mx[k];
+        for (int o = 16; o >= 1; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w > v ? w : v;
+        }
+        if ((threadIdx.x & 31) == 0 && v) atomicMax(&maxbits[k], v);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&status[ST_ERR], ERRBIT_ARG);
+}
+
+__global__ void k_refit_gather(const double *__restrict__ x, const double *__restrict__ m, int64_t N,
+                               const int32_t *pidx, double *px, double *py, double *pz, double *pm) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = pidx[p];
+        px[p] = __dadd_rn(x[3 * o], 0.0);
+        py[p] = __dadd_rn(x[3 * o + 1], 0.0);
+        pz[p] = __dadd_rn(x[3 * o + 2], 0.0);
+        pm[p] = m[o];
+    }
+}
+
+__device__ inline i128 ldcg_i128(const i128 *p) {
+    const long long *q = reinterpret_cast<const long long *>(p);
+    const unsigned long long lo = (unsigned long long)__ldcg(q);
+    const long long hi = __ldcg(q + 1);
+    return (i128)(((u128)(unsigned long long)hi << 64) | (u128)lo);
+}
+__device__ inline int64_t ldcg_i64(const int64_t *p) { return (int64_t)__ldcg(reinterpret_cast<const long long *>(p)); }
+
+// One thread per sink: exact sums and box of the ll-cell from its particles, then every parent
+// (once both children are done) from its children's sums and boxes.  Splits are kept.
+__global__ void k_refit_cells(Ctx c, const int32_t *sinks, int nsinks, const double *px, const double *py,
+                              const double *pz, const double *pm, int32_t *narrive) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsinks) return;
+    int n = sinks[s];
+    const int sh[4] = {62 - c.E[0], 62 - c.E[1], 62 - c.E[2], 62 - c.E[3]};
+    Red r;
+    red_init(r);
+    const int f = c.nfirst[n], cnt = c.ncount[n];
+    bool bad = false;
+    for (int a = f; a < f + cnt; ++a) {
+        const double xs[3] = {px[a], py[a], pz[a]};
+        int64_t P[4], key[3];
+        for (int d = 0; d < 3; ++d) {
+            key[d] = dkey(xs[d]);
+            P[1 + d] = fixed_point(__dmul_rn(pm[a], xs[d]), sh[d]);
+        }
+        P[0] = fixed_point(pm[a], sh[3]);
+        if (P[0] < 1) bad = true;
+        red_add_particle(r, P, key);
+    }
+    if (bad) atomicOr(&c.status[ST_ERR], ERRBIT_FIXED);
+    write_cell(c, n, c.L, f, r);
+    while (n > 1) {
+        const int sib = n ^ 1, P = n >> 1;
+        __threadfence();
+        if (__ldcg(&c.ncount[sib]) > 0) {
+            if (atomicAdd(&narrive[P], 1) == 0) return;
+            __threadfence();
+        }
+        Red q;
+        red_init(q);
+        for (int C = 2 * P; C <= 2 * P + 1; ++C) {
+            const int cc = __ldcg(&c.ncount[C]);
+            if (cc == 0) continue;
+            Red t;
+            for (int k = 0; k < 4; ++k) t.S[k] = ldcg_i128(&c.nS[4 * (int64_t)C + k]);
+            for (int d = 0; d < 3; ++d) {
+                t.lo[d] = ldcg_i64(&c.nbmin[3 * (int64_t)C + d]);
+                t.hi[d] = ldcg_i64(&c.nbmax[3 * (int64_t)C + d]);
+            }
+            t.n = cc;
+            red_merge(q, t);
+        }
+        write_cell(c, P, c.L, c.nfirst[P], q);  // level L: keep the build's split
+        n = P;
     }
 }
 
@@ -1043,7 +1159,8 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
     k_ingest_write<<<grid, 256, 0, st>>>(x, m, N, t->cap_N, t->d_E, t->bx[0], t->by[0], t->bz[0], t->bP[0],
                                          t->bidx[0], partials, t->d_status); note_launch();
     Ctx c = make_ctx(t);
-    k_root_finalize<<<1, 256, 0, st>>>(c, partials, grid, t->big_list[0], t->roots); note_launch();
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_nbig, 0, (kMaxL + 2) * sizeof(int32_t), st));
+    k_root_finalize<<<1, 256, 0, st>>>(c, partials, grid, t->big_list[0], t->roots, t->d_nbig); note_launch();
     RCB_CUDA_TRY(cudaGetLastError());
     stage_end(t, SG_INGEST);
     int rc = read_status(t);
@@ -1051,36 +1168,42 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
     if (t->h_status[ST_ERR] & (ERRBIT_ARG | ERRBIT_FIXED)) return RCB_ERR_ARG;
     stage_begin(t, SG_LEVELS);
 
-    // level passes while large cells remain
+    // level passes while large cells remain.  The number of large cells of every level lives on
+    // the device (d_nbig[level]); kernels read it and do nothing when it is zero, so the host
+    // launches levels in batches with upper-bound grids and synchronises once per batch.
     int nbig = t->h_status[ST_NBIG];
     int level = 0;
-    int cur = 0;
     ChunkPart *parts = reinterpret_cast<ChunkPart *>(t->chunk_part);
+    const int64_t big_cap = N / (kTcta + 1) + 2;
+    constexpr int kBatch = 4;
     while (nbig > 0) {
-        if (level >= t->L) return RCB_ERR_LIMIT;
-        int64_t bound = (N + kChunk - 1) / kChunk + nbig + 1;
-        if (bound > t->cap_chunks) return RCB_ERR_LIMIT;
-        k_chunk_plan<<<1, 1024, 0, st>>>(t->big_list[cur], nbig, t->nfirst, t->ncount, t->cell_chunk0, t->chunks,
-                                         t->d_status); note_launch();
-        int g = (int)std::min<int64_t>(bound, (int64_t)nsm * 8);
-        k_level_reduce<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, t->bx[cur], t->by[cur],
-                                                    t->bz[cur], t->bP[cur], parts); note_launch();
-        RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_NBIG, 0, sizeof(int), st));
-        int gf = (nbig * 32 + 255) / 256;
-        k_level_finalize<<<gf, 256, 0, st>>>(c, level, t->big_list[cur], nbig, t->cell_chunk0,
-                                             t->d_status + ST_NCHUNKS, parts, t->big_list[cur ^ 1], t->roots,
-                                             (level + 1) & 1); note_launch();
-        k_level_scatter<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, parts, t->bx[cur],
-                                                     t->by[cur], t->bz[cur], t->bP[cur], t->bidx[cur], t->bx[cur ^ 1],
-                                                     t->by[cur ^ 1], t->bz[cur ^ 1], t->bP[cur ^ 1],
-                                                     t->bidx[cur ^ 1]); note_launch();
+        int64_t nbig_bound = nbig;
+        for (int b = 0; b < kBatch && level < t->L; ++b, ++level) {
+            const int cur = level & 1;
+            const int64_t bound = (N + kChunk - 1) / kChunk + nbig_bound + 1;
+            if (bound > t->cap_chunks) return RCB_ERR_LIMIT;
+            k_chunk_plan<<<1, 1024, 0, st>>>(t->big_list[cur], t->d_nbig + level, t->nfirst, t->ncount,
+                                             t->cell_chunk0, t->chunks, t->d_status); note_launch();
+            const int g = (int)std::min<int64_t>(bound, (int64_t)nsm * 8);
+            k_level_reduce<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, t->bx[cur],
+                                                        t->by[cur], t->bz[cur], t->bP[cur], parts); note_launch();
+            const int gf = (int)std::max<int64_t>(1, (nbig_bound * 32 + 255) / 256);
+            k_level_finalize<<<gf, 256, 0, st>>>(c, level, t->big_list[cur], t->d_nbig + level, t->cell_chunk0,
+                                                 t->d_status + ST_NCHUNKS, parts, t->big_list[cur ^ 1],
+                                                 t->d_nbig + level + 1, t->roots, (level + 1) & 1); note_launch();
+            k_level_scatter<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, parts, t->bx[cur],
+                                                         t->by[cur], t->bz[cur], t->bP[cur], t->bidx[cur],
+                                                         t->bx[cur ^ 1], t->by[cur ^ 1], t->bz[cur ^ 1],
+                                                         t->bP[cur ^ 1], t->bidx[cur ^ 1]); note_launch();
+            nbig_bound = std::min<int64_t>(2 * nbig_bound, big_cap);
+        }
         RCB_CUDA_TRY(cudaGetLastError());
+        RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status + ST_NWORDS, t->d_nbig + level, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, st));
         rc = read_status(t);
         if (rc) return rc;
         if (t->h_status[ST_ERR] & ERRBIT_STATE) return RCB_ERR_LIMIT;
-        nbig = t->h_status[ST_NBIG];
-        cur ^= 1;
-        ++level;
+        nbig = level < t->L ? t->h_status[ST_NWORDS] : 0;
     }
     stage_end(t, SG_LEVELS);
     int nroots = t->h_status[ST_NROOTS];
@@ -1158,6 +1281,7 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
         pc.mq32a = t->mq32a;
         pc.mq32b = t->mq32b;
         pc.ncomdf = t->ncomdf;
+    pc.nfar = t->nfar;
         int g = (int)std::min<int64_t>((t->nn + 255) / 256, (int64_t)nsm * 8);
         k_pack_nodes<<<g, 256, 0, st>>>(pc, t->nn); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());
@@ -1167,10 +1291,62 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
 }
 
 int refit_tree(rcb_tree *t, const double *x, const double *m) {
-    (void)t;
-    (void)x;
-    (void)m;
-    return RCB_ERR_STATE;
+    if (t->nsinks <= 0) return RCB_ERR_STATE;
+    cudaStream_t st = t->stream;
+    const int64_t N = t->N;
+    const int nsm = sm_count();
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), st));
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_maxbits, 0, 4 * sizeof(unsigned long long), st));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, (int64_t)nsm * 8));
+    k_refit_scan<<<grid, 256, 0, st>>>(x, m, N, t->d_status, t->d_maxbits); note_launch();
+    k_exponents<<<1, 32, 0, st>>>(t->d_maxbits, t->d_E); note_launch();
+    k_refit_gather<<<grid, 256, 0, st>>>(x, m, N, t->pidx, t->px, t->py, t->pz, t->pm); note_launch();
+    RCB_CUDA_TRY(cudaMemsetAsync(t->narrive, 0, t->nn * sizeof(int32_t), st));
+    Ctx c = make_ctx(t);
+    k_refit_cells<<<(t->nsinks + 127) / 128, 128, 0, st>>>(c, t->sinks, t->nsinks, t->px, t->py, t->pz, t->pm,
+                                                          t->narrive); note_launch();
+    RCB_CUDA_TRY(cudaMemsetAsync(t->narrive, 0, t->nn * sizeof(int32_t), st));
+    LeafCtx lc;
+    lc.nfirst = t->nfirst;
+    lc.ncount = t->ncount;
+    lc.nmass = t->nmass;
+    lc.ncom = t->ncom;
+    lc.nrg = t->nrg;
+    lc.nH = t->nH;
+    lc.nhint = t->nhint;
+    lc.nhnode = t->nhnode;
+    lc.nQ = t->nQ;
+    lc.narrive = t->narrive;
+    lc.px = t->px;
+    lc.py = t->py;
+    lc.pz = t->pz;
+    lc.pm = t->pm;
+    lc.ph = t->ph;
+    lc.p32 = t->p32;
+    lc.h32 = t->h32;
+    k_leaves_up<<<(t->nsinks + 127) / 128, 128, 0, st>>>(lc, t->sinks, t->nsinks); note_launch();
+    PackCtx pc;
+    pc.ncount = t->ncount;
+    pc.nmass = t->nmass;
+    pc.ncom = t->ncom;
+    pc.nrg = t->nrg;
+    pc.nH = t->nH;
+    pc.nhint = t->nhint;
+    pc.nQ = t->nQ;
+    pc.w32a = t->w32a;
+    pc.w32b = t->w32b;
+    pc.mq32a = t->mq32a;
+    pc.mq32b = t->mq32b;
+    pc.ncomdf = t->ncomdf;
+    pc.nfar = t->nfar;
+    const int g = (int)std::min<int64_t>((t->nn + 255) / 256, (int64_t)nsm * 8);
+    k_pack_nodes<<<g, 256, 0, st>>>(pc, t->nn); note_launch();
+    RCB_CUDA_TRY(cudaGetLastError());
+    const int rc = read_status(t);
+    if (rc) return rc;
+    if (t->h_status[ST_ERR] & (ERRBIT_ARG | ERRBIT_FIXED)) return RCB_ERR_ARG;
+    t->nb_valid = 0;  // neighbour counts depend on the positions (candidate lists stay frozen)
+    return RCB_OK;
 }
 
 }  // namespace rcb

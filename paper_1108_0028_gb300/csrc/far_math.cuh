@@ -10,97 +10,127 @@
 
 namespace rcb {
 
-// symmetric slot of an index pair / triple (orders 2 and 3, lexicographic sorted tuples)
-__host__ __device__ constexpr int s2(int i, int j) {
-    return i > j ? s2(j, i) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
-}
-__host__ __device__ constexpr int sort3_slot(int a, int b, int c) {
-    // a <= b <= c
-    return a == 0 ? (b == 0 ? c : (b == 1 ? 2 + c : 5)) : (a == 1 ? (b == 1 ? 5 + c : 8) : 9);
-}
-__host__ __device__ constexpr int s3(int i, int j, int k) {
-    return (i <= j && j <= k)   ? sort3_slot(i, j, k)
-           : (i <= k && k <= j) ? sort3_slot(i, k, j)
-           : (j <= i && i <= k) ? sort3_slot(j, i, k)
-           : (j <= k && k <= i) ? sort3_slot(j, k, i)
-           : (k <= i && i <= j) ? sort3_slot(k, i, j)
-                                : sort3_slot(k, j, i);
+// Coefficients of one far source, accumulated into C.  x = r_A - r_B, g = 1/|x|, v = Q x,
+// s = x.v, and
+//   C0     = -M g - s g^5 / 2
+//   C1_i   = a x_i - g^5 v_i                                       a = M g^3 + 5/2 s g^7
+//   C2_ij  = b x_i x_j + a d_ij - g^5 Q_ij + 5 g^7 (v_i x_j + v_j x_i)
+//                                                                  b = -3 M g^5 - 35/2 s g^9
+//   C3_ijk = c x_i x_j x_k + b (d_ij x_k + d_ik x_j + d_jk x_i)
+//            + 5 g^7 (Q_ij x_k + Q_ik x_j + Q_jk x_i + v_i d_jk + v_j d_ik + v_k d_ij)
+//            - 35 g^9 (v_i x_j x_k + v_j x_i x_k + v_k x_i x_j)      c = 15 M g^7 + 315/2 s g^11
+// Slots: C[0]; C[1..3] = x, y, z; C[4..9] = xx, xy, xz, yy, yz, zz; C[10..19] = xxx, xxy, xxz,
+// xyy, xyz, xzz, yyy, yyz, yzz, zzz.  Every slot is written out so that all indices are
+// compile-time constants.
+template <typename T>
+__device__ inline T c3_slot(T c, T b, T f7, T f9, T xi, T xj, T xk, T Qij, T Qik, T Qjk, T vi, T vj, T vk, T dsum,
+                            T vsum) {
+    return c * xi * xj * xk + f7 * (Qij * xk + Qik * xj + Qjk * xi) - f9 * (vi * xj * xk + vj * xi * xk + vk * xi * xj) +
+           b * dsum + f7 * vsum;
 }
 
-// Coefficients of one far source (see the file header); C is accumulated into.
 template <typename T>
 __device__ inline void far_source(const T x[3], T M, const T Q6[6], T C[20]) {
-    const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    const T x0 = x[0], x1 = x[1], x2 = x[2];
+    const T r2 = x0 * x0 + x1 * x1 + x2 * x2;
     const T g = rsqrt(r2);
     const T g2 = g * g, g3 = g * g2, g5 = g3 * g2, g7 = g5 * g2, g9 = g7 * g2, g11 = g9 * g2;
-    T Q[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Q[i][j] = Q6[s2(i, j)];
-    T v[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = Q[i][0] * x[0] + Q[i][1] * x[1] + Q[i][2] * x[2];
-    const T s = x[0] * v[0] + x[1] * v[1] + x[2] * v[2];
+    const T Qxx = Q6[0], Qxy = Q6[1], Qxz = Q6[2], Qyy = Q6[3], Qyz = Q6[4], Qzz = Q6[5];
+    const T v0 = Qxx * x0 + Qxy * x1 + Qxz * x2;
+    const T v1 = Qxy * x0 + Qyy * x1 + Qyz * x2;
+    const T v2 = Qxz * x0 + Qyz * x1 + Qzz * x2;
+    const T s = x0 * v0 + x1 * v1 + x2 * v2;
     const T a = M * g3 + T(2.5) * s * g7;
     const T b = T(-3) * M * g5 - T(17.5) * s * g9;
     const T c = T(15) * M * g7 + T(157.5) * s * g11;
     const T f7 = T(5) * g7, f9 = T(35) * g9;
+    const T zero = T(0);
     C[0] += -M * g - T(0.5) * s * g5;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) C[1 + i] += a * x[i] - g5 * v[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = i; j < 3; ++j) {
-            T t = b * x[i] * x[j] - g5 * Q[i][j] + f7 * (v[i] * x[j] + v[j] * x[i]);
-            if (i == j) t += a;
-            C[4 + s2(i, j)] += t;
-        }
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = i; j < 3; ++j)
-#pragma unroll
-            for (int k = j; k < 3; ++k) {
-                T t = c * x[i] * x[j] * x[k] + f7 * (Q[i][j] * x[k] + Q[i][k] * x[j] + Q[j][k] * x[i]) -
-                      f9 * (v[i] * x[j] * x[k] + v[j] * x[i] * x[k] + v[k] * x[i] * x[j]);
-                T dsum = T(0), vsum = T(0);
-                if (i == j) { dsum += x[k]; vsum += v[k]; }
-                if (i == k) { dsum += x[j]; vsum += v[j]; }
-                if (j == k) { dsum += x[i]; vsum += v[i]; }
-                t += b * dsum + f7 * vsum;
-                C[10 + s3(i, j, k)] += t;
-            }
+    C[1] += a * x0 - g5 * v0;
+    C[2] += a * x1 - g5 * v1;
+    C[3] += a * x2 - g5 * v2;
+    C[4] += b * x0 * x0 - g5 * Qxx + f7 * (v0 * x0 + v0 * x0) + a;
+    C[5] += b * x0 * x1 - g5 * Qxy + f7 * (v0 * x1 + v1 * x0);
+    C[6] += b * x0 * x2 - g5 * Qxz + f7 * (v0 * x2 + v2 * x0);
+    C[7] += b * x1 * x1 - g5 * Qyy + f7 * (v1 * x1 + v1 * x1) + a;
+    C[8] += b * x1 * x2 - g5 * Qyz + f7 * (v1 * x2 + v2 * x1);
+    C[9] += b * x2 * x2 - g5 * Qzz + f7 * (v2 * x2 + v2 * x2) + a;
+    const T t3 = T(3);
+    C[10] += c3_slot(c, b, f7, f9, x0, x0, x0, Qxx, Qxx, Qxx, v0, v0, v0, t3 * x0, t3 * v0);
+    C[11] += c3_slot(c, b, f7, f9, x0, x0, x1, Qxx, Qxy, Qxy, v0, v0, v1, x1, v1);
+    C[12] += c3_slot(c, b, f7, f9, x0, x0, x2, Qxx, Qxz, Qxz, v0, v0, v2, x2, v2);
+    C[13] += c3_slot(c, b, f7, f9, x0, x1, x1, Qxy, Qxy, Qyy, v0, v1, v1, x0, v0);
+    C[14] += c3_slot(c, b, f7, f9, x0, x1, x2, Qxy, Qxz, Qyz, v0, v1, v2, zero, zero);
+    C[15] += c3_slot(c, b, f7, f9, x0, x2, x2, Qxz, Qxz, Qzz, v0, v2, v2, x0, v0);
+    C[16] += c3_slot(c, b, f7, f9, x1, x1, x1, Qyy, Qyy, Qyy, v1, v1, v1, t3 * x1, t3 * v1);
+    C[17] += c3_slot(c, b, f7, f9, x1, x1, x2, Qyy, Qyz, Qyz, v1, v1, v2, x2, v2);
+    C[18] += c3_slot(c, b, f7, f9, x1, x2, x2, Qyz, Qyz, Qzz, v1, v2, v2, x1, v1);
+    C[19] += c3_slot(c, b, f7, f9, x2, x2, x2, Qzz, Qzz, Qzz, v2, v2, v2, t3 * x2, t3 * v2);
+}
+
+// Gradient and Hessian of the sink's third-order Taylor polynomial P at offset d (Eq. 6).
+template <typename T>
+__device__ inline void taylor_grad_hess(const T C[20], T d0, T d1, T d2, T g[3], T H[6]) {
+    const T M00 = C[4], M01 = C[5], M02 = C[6], M11 = C[7], M12 = C[8], M22 = C[9];
+    const T T000 = C[10], T001 = C[11], T002 = C[12], T011 = C[13], T012 = C[14], T022 = C[15], T111 = C[16],
+            T112 = C[17], T122 = C[18], T222 = C[19];
+    H[0] = M00 + T000 * d0 + T001 * d1 + T002 * d2;
+    H[1] = M01 + T001 * d0 + T011 * d1 + T012 * d2;
+    H[2] = M02 + T002 * d0 + T012 * d1 + T022 * d2;
+    H[3] = M11 + T011 * d0 + T111 * d1 + T112 * d2;
+    H[4] = M12 + T012 * d0 + T112 * d1 + T122 * d2;
+    H[5] = M22 + T022 * d0 + T122 * d1 + T222 * d2;
+    // grad_i = C1_i + M_ij d_j + 1/2 T_ijk d_j d_k = C1_i + 1/2 (M_ij + H_ij) d_j
+    const T h = T(0.5);
+    g[0] = C[1] + h * ((M00 + H[0]) * d0 + (M01 + H[1]) * d1 + (M02 + H[2]) * d2);
+    g[1] = C[2] + h * ((M01 + H[1]) * d0 + (M11 + H[3]) * d1 + (M12 + H[4]) * d2);
+    g[2] = C[3] + h * ((M02 + H[2]) * d0 + (M12 + H[4]) * d1 + (M22 + H[5]) * d2);
 }
 
 // Third-order Taylor polynomial of the sink (Eq. 6): phi and a = -grad phi at offset d.
 template <typename T>
 __device__ inline void taylor_eval(const T C[20], const T d[3], T &phi, T acc[3]) {
-    T g[3];
-    T p = C[0];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        g[i] = C[1 + i];
-        p += C[1 + i] * d[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const T c2 = C[4 + s2(i, j)];
-            g[i] += c2 * d[j];
-            p += T(0.5) * c2 * d[i] * d[j];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const T c3 = C[10 + s3(i, j, k)];
-                g[i] += T(0.5) * c3 * d[j] * d[k];
-                p += c3 * d[i] * d[j] * d[k] * T(1.0 / 6.0);
-            }
-        }
-    phi = p;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) acc[i] = -g[i];
+    const T d0 = d[0], d1 = d[1], d2 = d[2];
+    T g[3], H[6];
+    taylor_grad_hess(C, d0, d1, d2, g, H);
+    // Phi = C0 + d.(C1 + 1/2 M d + 1/6 T d d) = C0 + d.(C1 + (g - C1) / ... ) written out:
+    const T q2 = T(0.5) * (C[4] * d0 * d0 + C[7] * d1 * d1 + C[9] * d2 * d2) + C[5] * d0 * d1 + C[6] * d0 * d2 +
+                 C[8] * d1 * d2;
+    const T q3 = (C[10] * d0 * d0 * d0 + C[16] * d1 * d1 * d1 + C[19] * d2 * d2 * d2) * T(1.0 / 6.0) +
+                 T(0.5) * (C[11] * d0 * d0 * d1 + C[12] * d0 * d0 * d2 + C[13] * d0 * d1 * d1 + C[15] * d0 * d2 * d2 +
+                           C[17] * d1 * d1 * d2 + C[18] * d1 * d2 * d2) +
+                 C[14] * d0 * d1 * d2;
+    phi = C[0] + C[1] * d0 + C[2] * d1 + C[3] * d2 + q2 + q3;
+    acc[0] = -g[0];
+    acc[1] = -g[1];
+    acc[2] = -g[2];
+}
+
+// dL/dC of one particle for a = -grad P(d), Phi = P(d), given v = dL/da and w = dL/dPhi
+// (accumulated into cb).
+template <typename T>
+__device__ inline void taylor_cbar(T d0, T d1, T d2, T v0, T v1, T v2, T w, T cb[20]) {
+    const T h = T(0.5), s6 = T(1.0 / 6.0);
+    cb[0] += w;
+    cb[1] += w * d0 - v0;
+    cb[2] += w * d1 - v1;
+    cb[3] += w * d2 - v2;
+    cb[4] += w * h * d0 * d0 - v0 * d0;
+    cb[5] += w * d0 * d1 - (v0 * d1 + v1 * d0);
+    cb[6] += w * d0 * d2 - (v0 * d2 + v2 * d0);
+    cb[7] += w * h * d1 * d1 - v1 * d1;
+    cb[8] += w * d1 * d2 - (v1 * d2 + v2 * d1);
+    cb[9] += w * h * d2 * d2 - v2 * d2;
+    cb[10] += w * s6 * d0 * d0 * d0 - v0 * h * d0 * d0;
+    cb[11] += w * h * d0 * d0 * d1 - (v0 * d0 * d1 + v1 * h * d0 * d0);
+    cb[12] += w * h * d0 * d0 * d2 - (v0 * d0 * d2 + v2 * h * d0 * d0);
+    cb[13] += w * h * d0 * d1 * d1 - (v0 * h * d1 * d1 + v1 * d0 * d1);
+    cb[14] += w * d0 * d1 * d2 - (v0 * d1 * d2 + v1 * d0 * d2 + v2 * d0 * d1);
+    cb[15] += w * h * d0 * d2 * d2 - (v0 * h * d2 * d2 + v2 * d0 * d2);
+    cb[16] += w * s6 * d1 * d1 * d1 - v1 * h * d1 * d1;
+    cb[17] += w * h * d1 * d1 * d2 - (v1 * d1 * d2 + v2 * h * d1 * d1);
+    cb[18] += w * h * d1 * d2 * d2 - (v1 * h * d2 * d2 + v2 * d1 * d2);
+    cb[19] += w * s6 * d2 * d2 * d2 - v2 * h * d2 * d2;
 }
 
 // Butterfly reduce-scatter of V values (power of two, <= 32) across the warp: afterwards lane l

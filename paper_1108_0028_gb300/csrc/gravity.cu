@@ -49,6 +49,7 @@ struct GCtx {
     const double *ncom, *nmass, *nQ;
     const float2 *ncomdf;
     const float4 *mq32a, *mq32b;
+    const float4 *nfar;
     const double *px, *py, *pz, *pm, *ph;
     const float4 *p32;
     const float *h32;
@@ -56,6 +57,12 @@ struct GCtx {
     double *coef;
     float *coef32;
     double *acc, *pot;
+    // neighbour search fused into the mixed near field
+    int64_t *nb_counts;  // [N] by original index
+    int32_t *nb_rows;    // [N][kNbRowCap] by sorted index
+    int2 *nb_long;
+    int cap_long;
+    int *status;
 };
 
 // ------------------------------------------------------------------------------------------ far
@@ -71,15 +78,33 @@ __global__ void __launch_bounds__(kGWarps * 32) k_far(GCtx c) {
             float C[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) C[i] = 0.f;
-            const float2 a0 = c.ncomdf[3 * (int64_t)A], a1 = c.ncomdf[3 * (int64_t)A + 1], a2 = c.ncomdf[3 * (int64_t)A + 2];
-            for (int k = lane; k < nf; k += 32) {
-                const int B = c.far_list[fb + k];
-                const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1], b2 = c.ncomdf[3 * (int64_t)B + 2];
-                const float x[3] = {(a0.x - b0.x) + (a0.y - b0.y), (a1.x - b1.x) + (a1.y - b1.y),
-                                    (a2.x - b2.x) + (a2.y - b2.y)};
-                const float4 qa = c.mq32a[B], qb = c.mq32b[B];
-                const float Q6[6] = {qa.y, qa.z, qa.w, qb.x, qb.y, qb.z};
-                far_source<float>(x, qa.x, Q6, C);
+            const float4 ah = c.nfar[4 * (int64_t)A], al = c.nfar[4 * (int64_t)A + 1];
+            // software pipeline: the records of the next far node are loaded before the current
+            // node's tensor arithmetic, so the gather latency overlaps the math
+            int k = lane;
+            float4 p0, p1, p2, p3;
+            if (k < nf) {
+                const float4 *r = c.nfar + 4 * (int64_t)c.far_list[fb + k];
+                p0 = r[0];
+                p1 = r[1];
+                p2 = r[2];
+                p3 = r[3];
+            }
+            while (k < nf) {
+                const float4 q0 = p0, q1 = p1, q2 = p2, q3 = p3;
+                const int kn = k + 32;
+                if (kn < nf) {
+                    const float4 *r = c.nfar + 4 * (int64_t)c.far_list[fb + kn];
+                    p0 = r[0];
+                    p1 = r[1];
+                    p2 = r[2];
+                    p3 = r[3];
+                }
+                const float x[3] = {(ah.x - q0.x) + (al.x - q1.x), (ah.y - q0.y) + (al.y - q1.y),
+                                    (ah.z - q0.z) + (al.z - q1.z)};
+                const float Q6[6] = {q1.w, q2.x, q2.y, q2.z, q2.w, q3.x};
+                far_source<float>(x, q0.w, Q6, C);
+                k = kn;
             }
             float E[32];
 #pragma unroll
@@ -186,18 +211,48 @@ __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_
 
 constexpr int kNearWarps = 8;     // warps per block of the mixed near kernel
 constexpr int kNearTile = 512;    // staged sources per warp
-constexpr size_t kNearWarpBytes = kNearTile * (sizeof(float4) + sizeof(float) + sizeof(int32_t)) +
-                                  kGroupMixed * (sizeof(float4) + sizeof(int32_t));
 
-// Stage sources [t0, t0 + kNearTile) of the sink's near cells, one lane per cell: float32
-// offsets from the sink's centre of mass (double-float difference of the two centres of mass
-// plus the particle's float32 offset from its own cell's centre), mass, h, sorted index.
-__device__ int stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, int64_t t0, float4 *src, float *hs,
-                                int32_t *si) {
+// Shared memory of one warp of the mixed near kernel.  With the neighbour search (NB) it also
+// holds each source's sorted index (bitwise complement for sources of non-candidate cells) and
+// each sink particle's float32 neighbour band.
+template <bool NB>
+struct NearSmem {
+    static constexpr size_t bytes =
+        kNearTile * (sizeof(float4) + sizeof(float) + sizeof(uint16_t)) + kGroupMixed * sizeof(float4) +
+        (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * (sizeof(float2) + sizeof(int)) : 0);
+    float4 *src;    // (d_b relative to the sink's centre of mass, m_b)
+    float *hs;      // h_b
+    float4 *snk;    // (d_a, h_a) of the current group
+    uint16_t *perm;
+    int32_t *sidx;  // NB
+    float2 *band;   // NB: per sink particle (2h)^2 -+ B
+    int *run;       // NB: per sink particle, neighbours found so far
+    __device__ NearSmem(unsigned char *p) {
+        src = reinterpret_cast<float4 *>(p);
+        hs = reinterpret_cast<float *>(src + kNearTile);
+        snk = reinterpret_cast<float4 *>(hs + kNearTile);
+        band = reinterpret_cast<float2 *>(snk + kGroupMixed);
+        sidx = reinterpret_cast<int32_t *>(band + (NB ? kGroupMixed : 0));
+        run = reinterpret_cast<int *>(sidx + (NB ? kNearTile : 0));
+        perm = reinterpret_cast<uint16_t *>(run + (NB ? kGroupMixed : 0));
+    }
+};
+
+// Stage sources [t0, t0 + kNearTile) of the sink's near cells: lanes first describe 32 cells
+// (first particle, count, centre-of-mass offset), then take one slot each, find its cell and
+// copy the particle: float32 offset from the sink's centre of mass, mass, h.  The cell offset is
+// the double-float difference of the two centres of mass; with NB it is the float64 difference
+// rounded once (the neighbour bound below is derived for that), the sorted index is kept and
+// wmax gets the tile's largest |dCOM|_1 + |d_b|_1.
+template <bool NB>
+__device__ int stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, int64_t t0, const NearSmem<NB> &sm,
+                                float &wmax) {
     const int lane = threadIdx.x & 31;
     const int64_t base = (int64_t)s * c.cap_near;
     const float2 a0 = c.ncomdf[3 * (int64_t)A], a1 = c.ncomdf[3 * (int64_t)A + 1], a2 = c.ncomdf[3 * (int64_t)A + 2];
+    const double cAx = c.ncom[3 * (int64_t)A], cAy = c.ncom[3 * (int64_t)A + 1], cAz = c.ncom[3 * (int64_t)A + 2];
     int64_t pos = 0;
+    float wl = 0.f;
     for (int k0 = 0; k0 < nlist && pos < t0 + kNearTile; k0 += 32) {
         const int k = k0 + lane;
         int f = 0, n = 0;
@@ -206,42 +261,245 @@ __device__ int stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, 
             const int B = near_entry(c, base, nr, k);
             f = c.nfirst[B];
             n = c.ncount[B];
-            const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1], b2 = c.ncomdf[3 * (int64_t)B + 2];
-            ox = (b0.x - a0.x) + (b0.y - a0.y);
-            oy = (b1.x - a1.x) + (b1.y - a1.y);
-            oz = (b2.x - a2.x) + (b2.y - a2.y);
-        }
-        int incl = n;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int64_t my0 = pos + incl - n;
-        for (int q = 0; q < n; ++q) {
-            const int64_t slot = my0 + q - t0;
-            if (slot >= 0 && slot < kNearTile) {
-                const float4 pb = c.p32[f + q];
-                src[slot] = make_float4(ox + pb.x, oy + pb.y, oz + pb.z, pb.w);
-                hs[slot] = c.h32[f + q];
-                si[slot] = f + q;
+            if (NB) {
+                ox = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B], cAx));
+                oy = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B + 1], cAy));
+                oz = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B + 2], cAz));
+            } else {
+                const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1],
+                             b2 = c.ncomdf[3 * (int64_t)B + 2];
+                ox = (b0.x - a0.x) + (b0.y - a0.y);
+                oy = (b1.x - a1.x) + (b1.y - a1.y);
+                oz = (b2.x - a2.x) + (b2.y - a2.y);
             }
         }
-        pos += __shfl_sync(0xffffffffu, incl, 31);
+        const int excl = warp_excl_scan(n);
+        const int total = __shfl_sync(0xffffffffu, excl + n, 31);
+        const int64_t lo = pos > t0 ? pos : t0;
+        const int64_t hi = pos + total < t0 + kNearTile ? pos + total : t0 + kNearTile;
+        for (int64_t j0 = lo; j0 < hi; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const int rel = (int)(j - pos);
+            const int cl = warp_find_slot(excl, rel);
+            const int fc = __shfl_sync(0xffffffffu, f, cl), ec = __shfl_sync(0xffffffffu, excl, cl);
+            const float cx = __shfl_sync(0xffffffffu, ox, cl), cy = __shfl_sync(0xffffffffu, oy, cl),
+                        cz = __shfl_sync(0xffffffffu, oz, cl);
+            if (j < hi) {
+                const int b = fc + rel - ec;
+                const float4 pb = c.p32[b];
+                sm.src[j - t0] = make_float4(cx + pb.x, cy + pb.y, cz + pb.z, pb.w);
+                sm.hs[j - t0] = c.h32[b];
+                if (NB) {
+                    sm.sidx[j - t0] = k0 + cl < nr ? b : ~b;
+                    wl = fmaxf(wl, (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
+                }
+            }
+        }
+        pos += total;
+    }
+    if (NB) {
+        for (int o = 16; o >= 1; o >>= 1) wl = fmaxf(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+        wmax = wl;
     }
     __syncwarp();
     const int64_t left = pos - t0;
     return (int)(left < kNearTile ? left : kNearTile);
 }
 
+// Order the staged sources for the two pair loops.  With R_A the largest |d_a| and H_A the
+// largest h_a of the sink's particles, a source b with |d_b| > (R_A + X_b)(1 + 2^-10) has
+// r_ab >= |d_b| - |d_a| > X_b for every sink particle a.  X_b = H_A + h_b puts all its pairs on
+// the Newtonian branch of Eq. 10 (q >= 2); with the neighbour search X_b = max(H_A + h_b, 2 H_A)
+// also keeps it out of every sink particle's neighbour sphere (r < 2 h_a).  The 2^-10 margin is
+// far above the float32 rounding of the test, of q and of the neighbour filter.  perm[0, nclose)
+// lists the other sources, perm[nclose, ns) these.
+template <bool NB>
+__device__ int partition_near(const NearSmem<NB> &sm, int ns, float RA, float HA) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int nclose = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        int pc = 0, pf = nclose;
+        for (int q0 = 0; q0 < ns; q0 += 32) {
+            const int j = q0 + lane;
+            bool far = false;
+            if (j < ns) {
+                const float4 v = sm.src[j];
+                const float d2 = fmaf(v.z, v.z, fmaf(v.y, v.y, v.x * v.x));
+                const float hb = sm.hs[j];
+                const float X = NB ? fmaxf(HA + hb, HA + HA) : HA + hb;
+                const float R = (RA + X) * (1.0f + 0x1p-10f);
+                far = d2 > R * R;
+            }
+            const unsigned mc = __ballot_sync(0xffffffffu, j < ns && !far);
+            if (pass == 1) {
+                const unsigned mf = __ballot_sync(0xffffffffu, j < ns && far);
+                if (j < ns) sm.perm[far ? pf + __popc(mf & lt) : pc + __popc(mc & lt)] = (uint16_t)j;
+                pf += __popc(mf);
+            }
+            pc += __popc(mc);
+        }
+        nclose = pc;
+    }
+    __syncwarp();
+    return nclose;
+}
+
+// Neighbour-search state of one group of sink particles (running counts sit in shared memory).
+struct NbGroup {
+    int a0;   // sorted index of the group's first sink particle
+    int nfb;  // float64 decisions taken
+};
+
+// Neighbour test of staged source b (lane) against sink particle i of the group: float32 d^2
+// against the particle's band, float64 inside it; b's original index is appended to a's row.
+template <bool NB>
+__device__ __forceinline__ void near_neighbours_of(const GCtx &c, const NearSmem<NB> &sm, int i, float4 b, int sb,
+                                                unsigned cand, NbGroup &g) {
+    const int lane = threadIdx.x & 31;
+    const float4 sa = sm.snk[i];
+    const float dx = sa.x - b.x, dy = sa.y - b.y, dz = sa.z - b.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const float2 bd = sm.band[i];
+    unsigned bl = __ballot_sync(0xffffffffu, r2 < bd.x) & cand;
+    const unsigned bh = __ballot_sync(0xffffffffu, r2 <= bd.y) & cand;
+    if (bl != bh) {
+        // inside the band: the float64 test decides
+        bool nb = false;
+        if (((bh & ~bl) >> lane) & 1u) {
+            const int a = g.a0 + i;
+            const double s2 = __dmul_rn(2.0, c.ph[a]);
+            nb = dist2_rn(c.px[a], c.py[a], c.pz[a], c.px[sb], c.py[sb], c.pz[sb]) < __dmul_rn(s2, s2);
+            ++g.nfb;
+        }
+        bl |= __ballot_sync(0xffffffffu, nb);
+    }
+    bl &= ~__ballot_sync(0xffffffffu, sb == g.a0 + i);  // not itself
+    const int run = sm.run[i];
+    if ((bl >> lane) & 1u) {
+        const int p = run + __popc(bl & ((1u << lane) - 1u));
+        if (p < kNbRowCap) c.nb_rows[(int64_t)(g.a0 + i) * kNbRowCap + p] = c.pidx[sb];
+    }
+    __syncwarp();
+    if (lane == 0) sm.run[i] = run + __popc(bl);
+    __syncwarp();
+}
+
+// The pair loops of one staged tile for G sink particles (snk[0, G)), folded into the lane's
+// compensated total (rs, rc) of value (lane mod 4 G) = 4 i + q.  With NB the close loop also
+// tests every candidate pair (a, b) for |r_a - r_b| < 2 h_a: float32 d^2 against the band of
+// sink particle i, float64 inside it, and appends b's original index to a's row of slots.
+template <int G, bool NB>
+__device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, int ns, int nclose, float &rs, float &rc,
+                                 NbGroup &g) {
+    const int lane = threadIdx.x & 31;
+    float In[4][G];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < G; ++i) In[q][i] = 0.f;
+    // far sources: every pair outside its kernel support, Newtonian only
+    for (int q0 = nclose; q0 < ns; q0 += 32) {
+        const int j = q0 + lane;
+        // padding lanes: a massless source far away (finite r, zero contribution)
+        const float4 b = j < ns ? sm.src[sm.perm[j]] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const float4 sa = sm.snk[i];
+            const float dx = sa.x - b.x, dy = sa.y - b.y, dz = sa.z - b.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+            const float w = b.w * (rinv * rinv * rinv);
+            In[0][i] = fmaf(-w, dx, In[0][i]);
+            In[1][i] = fmaf(-w, dy, In[1][i]);
+            In[2][i] = fmaf(-w, dz, In[2][i]);
+            In[3][i] = fmaf(-b.w, rinv, In[3][i]);
+        }
+    }
+    // close sources: the full kernel-softened pair
+    for (int q0 = 0; q0 < nclose; q0 += 32) {
+        const int j = q0 + lane;
+        float4 b = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        float hb = 1.f;
+        int sb = -1;
+        if (j < nclose) {
+            const int pj = sm.perm[j];
+            b = sm.src[pj];
+            hb = sm.hs[pj];
+            if (NB) sb = sm.sidx[pj];
+        }
+        const unsigned cand = NB ? __ballot_sync(0xffffffffu, sb >= 0) : 0u;  // candidate-cell sources
+        unsigned pend = 0;  // sink particles with a possible neighbour in this chunk
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            // one branch-free pair (the self pair has r = 0: zero force; its
+            // potential m_a phi(0) is removed in the epilogue)
+            const float4 sa = sm.snk[i];
+            const float dx = sa.x - b.x, dy = sa.y - b.y, dz = sa.z - b.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+            const float r = r2 * rinv;
+            const float hinv = __fdividef(2.0f, sa.w + hb);
+            const float q = r * hinv;
+            const float q2 = q * q;
+            const float rinv3 = rinv * rinv * rinv;
+            // Eq. 10 as S/r and its potential: q < 1, 1 <= q < 2, q >= 2
+            const float h3 = hinv * hinv * hinv;
+            const float s1 = h3 * fmaf(q2, fmaf(0.5f, q, -1.2f), 4.0f / 3.0f);
+            const float p1 = hinv * fmaf(q2, fmaf(q2, fmaf(0.1f, q, -0.3f), 2.0f / 3.0f), -1.4f);
+            const float s2v = fmaf(h3, fmaf(q, fmaf(q, fmaf(-1.0f / 6.0f, q, 1.2f), -3.0f), 8.0f / 3.0f),
+                                   -(1.0f / 15.0f) * rinv3);
+            const float p2v = fmaf(hinv,
+                                   fmaf(q2, fmaf(q, fmaf(q, fmaf(-1.0f / 30.0f, q, 0.3f), -1.0f), 4.0f / 3.0f), -1.6f),
+                                   (1.0f / 15.0f) * rinv);
+            const float sr = q < 1.0f ? s1 : (q < 2.0f ? s2v : rinv3);
+            const float ph = q < 1.0f ? p1 : (q < 2.0f ? p2v : -rinv);
+            const float w = b.w * sr;
+            In[0][i] = fmaf(-w, dx, In[0][i]);
+            In[1][i] = fmaf(-w, dy, In[1][i]);
+            In[2][i] = fmaf(-w, dz, In[2][i]);
+            In[3][i] = fmaf(b.w, ph, In[3][i]);
+            if (NB) {
+                // upper bound only here; the rest of the test runs out of the unrolled loop
+                if (__ballot_sync(0xffffffffu, r2 <= sm.band[i].y) & cand) pend |= 1u << i;
+            }
+        }
+        if (NB) {
+            while (pend) {
+                const int i = __ffs(pend) - 1;
+                pend &= pend - 1;
+                near_neighbours_of<NB>(c, sm, i, b, sb, cand, g);
+            }
+        }
+    }
+    // fold this tile: compensated reduce-scatter across lanes, then into (rs, rc)
+    float Vs[4 * G], Vc[4 * G];
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            Vs[4 * i + q] = In[q][i];
+            Vc[4 * i + q] = 0.f;
+        }
+    reduce_scatter_df<4 * G>(Vs, Vc);
+    float t, e;
+    two_sum(rs, Vs[0], t, e);
+    rs = t;
+    rc = __fadd_rn(__fadd_rn(rc, Vc[0]), e);
+}
+
+// Mixed near field; with NB also the neighbour search of Sec. 2.3 on the same staged sources
+// (counts to nb_counts by original index, rows of kNbRowCap slots to nb_rows, longer rows
+// queued).  The float32 neighbour filter is the one of the neighbour kernels: d^2 against
+// (2h)^2 -+ B, B = 2^-19 ((W + |d_a|_1)^2 + (2h)^2) + 1e-30 with W the tile's largest
+// |dCOM|_1 + |d_b|_1, the float64 test inside the band.
+template <bool NB>
 __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned char *smw = smem_raw + (size_t)w * kNearWarpBytes;
-    float4 *src = reinterpret_cast<float4 *>(smw);
-    float *hs = reinterpret_cast<float *>(src + kNearTile);
-    int32_t *si = reinterpret_cast<int32_t *>(hs + kNearTile);
-    float4 *snk = reinterpret_cast<float4 *>(si + kNearTile);  // (d_a, h_a) of the current group
-    int32_t *sid = reinterpret_cast<int32_t *>(snk + kGroupMixed);
+    const NearSmem<NB> sm(smem_raw + (size_t)w * NearSmem<NB>::bytes);
+    NbGroup g;
+    g.nfb = 0;
     for (int s = blockIdx.x * kNearWarps + w; s < c.nsinks; s += gridDim.x * kNearWarps) {
         const int A = c.sinks[s];
         const int fA = c.nfirst[A], nA = c.ncount[A];
@@ -250,69 +508,67 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
         int64_t S = 0;
         for (int k = lane; k < nlist; k += 32) S += c.ncount[near_entry(c, base, nr, k)];
         for (int o = 16; o >= 1; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
-        int ns_once = -1;  // staged tile count when all sources fit one tile
+        // R_A and H_A of the sink cell (float32 offsets from its centre of mass)
+        float RA, HA;
+        {
+            float R2 = 0.f, H = 0.f;
+            for (int i = lane; i < nA; i += 32) {
+                const float4 pa = c.p32[fA + i];
+                R2 = fmaxf(R2, fmaf(pa.z, pa.z, fmaf(pa.y, pa.y, pa.x * pa.x)));
+                H = fmaxf(H, c.h32[fA + i]);
+            }
+            for (int o = 16; o >= 1; o >>= 1) {
+                R2 = fmaxf(R2, __shfl_xor_sync(0xffffffffu, R2, o));
+                H = fmaxf(H, __shfl_xor_sync(0xffffffffu, H, o));
+            }
+            RA = sqrtf(R2) * (1.0f + 0x1p-10f);
+            HA = H;
+        }
+        int once_ns = -1, once_nc = 0;  // staged tile when all sources fit one tile
+        float wmax = 0.f;
         for (int a0 = 0; a0 < nA; a0 += kGroupMixed) {
             const int na = min(kGroupMixed, nA - a0);
             if (lane < kGroupMixed) {
                 const int i = min(lane, na - 1);
                 const float4 pa = c.p32[fA + a0 + i];
-                snk[lane] = make_float4(pa.x, pa.y, pa.z, c.h32[fA + a0 + i]);
-                sid[lane] = lane < na ? fA + a0 + i : -1;
+                sm.snk[lane] = make_float4(pa.x, pa.y, pa.z, c.h32[fA + a0 + i]);
+            }
+            if (NB) {
+                g.a0 = fA + a0;
+                if (lane < kGroupMixed) sm.run[lane] = 0;
             }
             __syncwarp();
-            float rs = 0.f, rc = 0.f;  // compensated total of value `lane` (= 4 i + q)
+            float rs = 0.f, rc = 0.f;  // compensated total of value lane mod 4 G (= 4 i + q)
             for (int64_t t0 = 0; t0 < S; t0 += kNearTile) {
-                int ns = ns_once;
+                int ns = once_ns, nclose = once_nc;
                 if (ns < 0) {
-                    ns = stage_near_mixed(c, s, A, nlist, nr, t0, src, hs, si);
-                    if (S <= kNearTile) ns_once = ns;
-                }
-                float In[4][kGroupMixed];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int i = 0; i < kGroupMixed; ++i) In[q][i] = 0.f;
-                for (int q0 = 0; q0 < ns; q0 += 32) {
-                    const int j = q0 + lane;
-                    float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-                    float hb = 1.f;
-                    int bid = -2;
-                    if (j < ns) {
-                        b = src[j];
-                        hb = hs[j];
-                        bid = si[j];
+                    ns = stage_near_mixed<NB>(c, s, A, nlist, nr, t0, sm, wmax);
+                    nclose = partition_near<NB>(sm, ns, RA, HA);
+                    if (S <= kNearTile) {
+                        once_ns = ns;
+                        once_nc = nclose;
                     }
-#pragma unroll
-                    for (int i = 0; i < kGroupMixed; ++i) {
-                        if (i < na) {
-                            const float4 sa = snk[i];
-                            const float mb = bid == sid[i] ? 0.f : b.w;
-                            float ax, ay, az, ph;
-                            pair_force<float>(sa.x - b.x, sa.y - b.y, sa.z - b.z, sa.w + hb, mb, ax, ay, az, ph);
-                            In[0][i] += ax;
-                            In[1][i] += ay;
-                            In[2][i] += az;
-                            In[3][i] += ph;
+                }
+                if (NB) {
+                    // neighbour band of each sink particle for this tile (-1: padding slot)
+                    if (lane < kGroupMixed) {
+                        float2 bd = make_float2(-1.f, -1.f);
+                        if (lane < na) {
+                            const float4 sa = sm.snk[lane];
+                            const float h2f = 2.0f * sa.w;  // = float32(2 h) exactly
+                            const float h2 = h2f * h2f;
+                            const float F = wmax + (fabsf(sa.x) + fabsf(sa.y) + fabsf(sa.z));
+                            const float B = fmaf(F, F, h2) * 0x1p-19f + 1e-30f;
+                            bd = make_float2(h2 - B, h2 + B);
                         }
+                        sm.band[lane] = bd;
                     }
+                    __syncwarp();
                 }
-                // fold this tile: compensated reduce-scatter across lanes, then into (rs, rc)
-                float Vs[32], Vc[32];
-#pragma unroll
-                for (int i = 0; i < kGroupMixed; ++i)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        Vs[4 * i + q] = In[q][i];
-                        Vc[4 * i + q] = 0.f;
-                    }
-                reduce_scatter_df<32>(Vs, Vc);
-                float t, e;
-                two_sum(rs, Vs[0], t, e);
-                rs = t;
-                rc = __fadd_rn(__fadd_rn(rc, Vc[0]), e);
+                near_tile<kGroupMixed, NB>(c, sm, ns, nclose, rs, rc, g);
                 __syncwarp();
             }
-            const double tot = __dadd_rn((double)rs, (double)rc);  // lane l: particle l/4, quantity l%4
+            const double tot = __dadd_rn((double)rs, (double)rc);  // lane l < 4 na: particle l/4, quantity l%4
             const double q0v = __shfl_sync(0xffffffffu, tot, (4 * lane) & 31);
             const double q1v = __shfl_sync(0xffffffffu, tot, (4 * lane + 1) & 31);
             const double q2v = __shfl_sync(0xffffffffu, tot, (4 * lane + 2) & 31);
@@ -321,6 +577,10 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
                 const int a = fA + a0 + lane;
                 const float4 pa = c.p32[a];
                 const float d[3] = {pa.x, pa.y, pa.z};
+                // the tile loop included the pair of a with itself: zero force, potential
+                // m_a phi(0) = m_a (-1.4) 2 / (h_a + h_a) computed exactly as the loop did
+                const float ha = c.h32[a];
+                const float self_pot = pa.w * (__fdividef(2.0f, ha + ha) * -1.4f);
                 float Cf[20];
 #pragma unroll
                 for (int i = 0; i < 20; ++i) Cf[i] = c.coef32[(int64_t)s * 20 + i];
@@ -330,10 +590,24 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
                 c.acc[3 * (int64_t)o] = q0v + (double)af[0];
                 c.acc[3 * (int64_t)o + 1] = q1v + (double)af[1];
                 c.acc[3 * (int64_t)o + 2] = q2v + (double)af[2];
-                if (c.pot) c.pot[o] = q3v + (double)phf;
+                if (c.pot) c.pot[o] = q3v + (double)phf - (double)self_pot;
+            }
+            if (NB && lane < na) {
+                const int a = fA + a0 + lane;
+                const int n = sm.run[lane];
+                c.nb_counts[c.pidx[a]] = n;
+                if (n > kNbRowCap) {
+                    const int q = atomicAdd(&c.status[ST_LONGROWS], 1);
+                    if (q < c.cap_long) c.nb_long[q] = make_int2(a, s);
+                }
             }
             __syncwarp();
         }
+    }
+    if (NB) {
+        int n = g.nfb;
+        for (int o = 16; o >= 1; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+        if (lane == 0 && n) atomicAdd(&c.status[ST_NBFALLBACK], n);
     }
 }
 
@@ -459,9 +733,11 @@ int far_coefficients_fp64(rcb_tree *t) {
     return RCB_OK;
 }
 
-int gravity(rcb_tree *t, double *acc, double *pot) {
-    cudaStream_t st = t->stream;
+namespace {
+
+GCtx make_gctx(rcb_tree *t, double *acc, double *pot) {
     GCtx c;
+    std::memset(&c, 0, sizeof(c));
     c.nsinks = t->nsinks;
     c.sinks = t->sinks;
     c.near_list = t->near_list;
@@ -479,6 +755,7 @@ int gravity(rcb_tree *t, double *acc, double *pot) {
     c.ncomdf = t->ncomdf;
     c.mq32a = t->mq32a;
     c.mq32b = t->mq32b;
+    c.nfar = t->nfar;
     c.px = t->px;
     c.py = t->py;
     c.pz = t->pz;
@@ -491,6 +768,30 @@ int gravity(rcb_tree *t, double *acc, double *pot) {
     c.coef32 = t->coef32;
     c.acc = acc;
     c.pot = pot;
+    c.nb_counts = t->nb_count;
+    c.nb_rows = t->nb_rows;
+    c.nb_long = t->nb_long;
+    c.cap_long = (int)t->N;
+    c.status = t->d_status;
+    return c;
+}
+
+template <bool NB>
+int launch_near_mixed(rcb_tree *t, const GCtx &c) {
+    const int nsm = sm_count_g();
+    const size_t smem = (size_t)kNearWarps * NearSmem<NB>::bytes;
+    RCB_CUDA_TRY(cudaFuncSetAttribute(k_near_mixed<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nb = std::max(1, std::min((t->nsinks + kNearWarps - 1) / kNearWarps, nsm * 2 * 16));
+    k_near_mixed<NB><<<nb, kNearWarps * 32, smem, t->stream>>>(c); note_launch();
+    RCB_CUDA_TRY(cudaGetLastError());
+    return RCB_OK;
+}
+
+// Far field and near field; with NB (mixed form only) the near kernel also counts the
+// neighbours and writes their slot rows.
+int gravity_impl(rcb_tree *t, double *acc, double *pot, bool nb) {
+    cudaStream_t st = t->stream;
+    const GCtx c = make_gctx(t, acc, pot);
     if (t->nsinks == 0) return RCB_OK;
     const int nsm = sm_count_g();
     const int blocks = std::max(1, std::min((t->nsinks + kGWarps - 1) / kGWarps, nsm * 32));
@@ -498,12 +799,10 @@ int gravity(rcb_tree *t, double *acc, double *pot) {
     if (mixed) {
         stage_begin(t, SG_FAR);
         k_far<true><<<blocks, kGWarps * 32, 0, st>>>(c); note_launch();
-        const size_t smem = (size_t)kNearWarps * kNearWarpBytes;
-        RCB_CUDA_TRY(cudaFuncSetAttribute(k_near_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         stage_end(t, SG_FAR);
         stage_begin(t, SG_NEAR);
-        const int nb = std::max(1, std::min((t->nsinks + kNearWarps - 1) / kNearWarps, nsm * 2 * 16));
-        k_near_mixed<<<nb, kNearWarps * 32, smem, st>>>(c); note_launch();
+        const int rc = nb ? launch_near_mixed<true>(t, c) : launch_near_mixed<false>(t, c);
+        if (rc) return rc;
     } else {
         stage_begin(t, SG_FAR);
         k_far<false><<<blocks, kGWarps * 32, 0, st>>>(c); note_launch();
@@ -516,6 +815,30 @@ int gravity(rcb_tree *t, double *acc, double *pot) {
     stage_end(t, SG_NEAR);
     RCB_CUDA_TRY(cudaGetLastError());
     return RCB_OK;
+}
+
+}  // namespace
+
+int gravity(rcb_tree *t, double *acc, double *pot) { return gravity_impl(t, acc, pot, false); }
+
+int gravity_neighbours(rcb_tree *t, double *acc, double *pot) {
+    if (t->params.precision != RCB_MIXED) {
+        // FP64 form: the two passes run separately
+        const int rc = gravity_impl(t, acc, pot, false);
+        if (rc) return rc;
+        return count_neighbours(t);
+    }
+    if (t->nb_valid) return gravity_impl(t, acc, pot, false);  // counts and rows are current
+    int rc = ensure_nb_rows(t);
+    if (rc) return rc;
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_NBFALLBACK, 0, 2 * sizeof(int), t->stream));
+    rc = gravity_impl(t, acc, pot, true);
+    if (rc) return rc;
+    stage_begin(t, SG_NB_COUNT);
+    rc = scan_neighbour_counts(t);
+    if (rc) return rc;
+    stage_end(t, SG_NB_COUNT);
+    return fetch_neighbour_total(t);
 }
 
 }  // namespace rcb

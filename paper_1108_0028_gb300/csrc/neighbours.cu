@@ -2,28 +2,27 @@
 // the particles b != a with |r_a - r_b| < 2 h_a, and stored in one flat list with per-particle
 // offsets (Sec. 2.3.2), rows in original order and sorted by original index.
 //
-// sizes  per sink: particles of its candidate cells (S) and the words of its ballot masks
-//        (n_A x ceil(S/32)); a scan places every sink's masks.
-// count  one warp per sink stages the candidate particles in shared memory (one lane per cell)
-//        as float32 offsets from the sink's centre of mass (the cell-centre difference formed
-//        in float64, then each particle's float32 offset from its own cell's centre of mass);
-//        lanes take 32 sources, the warp loops over the sink's particles; each 32-source
-//        ballot is the neighbour mask of that chunk.  Counts go to the particle's original
-//        index; masks to global memory.
-// scan   exclusive int64 scan over original indices gives the CSR offsets.
-// fill   per sink, a prefix table of its candidate cells maps a source number to a particle;
-//        each particle's row is expanded from its masks into shared memory, sorted (bitonic)
-//        and written in one coalesced run.  Rows longer than kRowWarp are written unsorted and
-//        sorted afterwards by one block each.
-// The float32 test d^2 - (2h)^2 carries the bound B = 2^-19 F, F = (|dCOM|_1 + |d_b|_1 +
-// |d_a|_1)^2 + (2h)^2: the three input roundings, the two float additions of the offsets, the
-// squares, sums and final subtraction stay below 10 u F (u = 2^-24), so B covers them three
-// times; the additive 1e-30 covers flushed subnormals.  Inside the band the test is repeated in
-// float64 on the original positions, rounded after every operation, which is the definition;
-// the lists are therefore exact.
+// pass     one warp per sink stages its candidate particles in shared memory (one lane per cell)
+//          as float32 offsets from the sink's centre of mass (the cell-centre difference formed
+//          in float64, then each particle's float32 offset from its own cell's centre of mass).
+//          Eight sink particles sit in registers; lanes take 32 sources at a time and every pair
+//          test is one bit of a warp ballot.  A particle's count goes to its original index and
+//          its neighbours' original indices to a row of kRowCap slots; longer rows are queued.
+// scan     exclusive int64 scan over original indices gives the CSR offsets.
+// compact  one warp per particle sorts its slot row (bitonic network of shuffles) and writes it
+//          at its offset.
+// long     queued rows are recomputed straight into place, one warp each, and sorted by one
+//          block each.
+// The float32 test compares d^2 with (2h)^2 -+ B, B = 2^-19 F, F = (W + |d_a|_1)^2 + (2h)^2 with W
+// the tile's largest |dCOM|_1 + |d_b|_1: the three input roundings, the two float additions of
+// the offsets, the squares and sums, and the roundings of (2h)^2 and of (2h)^2 -+ B stay below
+// 13 u F (u = 2^-24), so B covers them more than twice; the additive 1e-30 covers flushed
+// subnormals.  Inside the band the test is repeated in float64 on the original positions,
+// rounded after every operation, which is the definition; the lists are therefore exact.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "rcb_internal.cuh"
 
@@ -31,9 +30,11 @@ namespace rcb {
 namespace {
 
 constexpr int kNbWarps = 8;
-constexpr int kNbTile = 512;      // staged sources per warp (count pass)
-constexpr int kMaxSinkPart = 64;  // sink particles kept in shared memory per pass
-constexpr int kRowWarp = 1024;    // longest row sorted by one warp
+constexpr int kNbTile = 512;      // staged sources per warp
+constexpr int kNbGroup = 8;       // sink particles held in registers
+constexpr int kMaxSinkPart = 64;  // sink particles whose running counts sit in shared memory
+constexpr int kRowCap = kNbRowCap;  // slots of a particle's row before the compaction
+constexpr unsigned kFull = 0xffffffffu;
 
 struct NbCtx {
     int nsinks;
@@ -44,51 +45,66 @@ struct NbCtx {
     const double *px, *py, *pz, *ph;
     const int32_t *pidx;
     const float4 *p32;
-    int64_t *counts;          // [N] by original index
-    const int64_t *offsets;   // [N+1]
+    const float *h32;
+    int64_t *counts;         // [N] by original index
+    const int64_t *offsets;  // [N+1]
     int32_t *idx;
-    int *status;
-    const int64_t *mask_off;  // [nsinks + 1] word offsets of each sink's masks (or null)
-    uint32_t *masks;
-    int32_t *long_rows;
+    int32_t *rows;   // [N][kRowCap] by sorted index
+    int2 *long_rows;  // (sorted particle, sink) of rows longer than kRowCap
     int cap_long;
+    int *status;
 };
 
 struct NbSmem {
-    float4 src[kNbWarps][kNbTile];        // (x, y, z relative to COM_A, |dCOM|_1 + |d_b|_1)
-    int32_t sidx[kNbWarps][kNbTile];      // sorted index of the source
-    float4 snk[kNbWarps][kMaxSinkPart];   // (d_a, |d_a|_1)
-    float h2[kNbWarps][kMaxSinkPart];     // (2 h_a)^2 in float32
-    int cnt[kNbWarps][kMaxSinkPart];
+    float4 src[kNbWarps][kNbTile];    // (d_b relative to COM_A, |dCOM|_1 + |d_b|_1)
+    int32_t sidx[kNbWarps][kNbTile];  // sorted index of the source
+    int32_t oidx[kNbWarps][kNbTile];  // original index of the source
+    int run[kNbWarps][kMaxSinkPart];  // neighbours found so far per sink particle
 };
 
-__device__ inline int64_t sources_of(const NbCtx &c, int s, int nr) {
-    const int lane = threadIdx.x & 31;
-    int64_t S = 0;
-    for (int k = lane; k < nr; k += 32) S += c.ncount[c.near_list[(int64_t)s * c.cap_near + k]];
-    for (int o = 16; o >= 1; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
-    return S;
-}
+// Candidate sources of sink s: their number and the position of the sink's own cell among them
+// (-1 when the cell is not among its own candidates, which needs h_int = 0).
+struct SinkLayout {
+    int64_t S, posA;
+};
 
-__global__ void k_nb_sizes(NbCtx c, int64_t *words) {
+__device__ SinkLayout sink_layout(const NbCtx &c, int s, int A, int nr) {
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int s = gw; s < c.nsinks; s += nw) {
-        const int64_t S = sources_of(c, s, c.near_nr[s]);
-        if (lane == 0) words[s] = (int64_t)c.ncount[c.sinks[s]] * ((S + 31) / 32);
+    const int64_t base = (int64_t)s * c.cap_near;
+    int64_t pos = 0, posA = -1;
+    for (int k0 = 0; k0 < nr; k0 += 32) {
+        const int k = k0 + lane;
+        int n = 0;
+        bool me = false;
+        if (k < nr) {
+            const int B = c.near_list[base + k];
+            n = c.ncount[B];
+            me = B == A;
+        }
+        const int excl = warp_excl_scan(n);
+        const unsigned mm = __ballot_sync(kFull, me);
+        const int before = __shfl_sync(kFull, excl, mm ? __ffs(mm) - 1 : 0);
+        if (mm) posA = pos + before;
+        pos += __shfl_sync(kFull, excl + n, 31);
     }
+    return SinkLayout{pos, posA};
 }
 
-// Stage sources [t0, t0 + kNbTile): one lane per candidate cell copies that cell's particles.
-__device__ int stage_tile(const NbCtx &c, int s, int A, int nr, int64_t t0, float4 *src, int32_t *sidx) {
+// Stage sources [t0, t0 + kNbTile): lanes first describe 32 candidate cells (first particle,
+// count, centre-of-mass offset), then take one slot each, find its cell and copy the particle.
+// Returns the staged count; wmax gets the largest w = |dCOM|_1 + |d_b|_1 of the tile.
+template <bool ORIG>
+__device__ int stage_tile(const NbCtx &c, int s, int A, int nr, int64_t t0, float4 *src, int32_t *sidx,
+                          int32_t *oidx, float &wmax) {
     const int lane = threadIdx.x & 31;
     const int64_t base = (int64_t)s * c.cap_near;
     const double cAx = c.ncom[3 * (int64_t)A], cAy = c.ncom[3 * (int64_t)A + 1], cAz = c.ncom[3 * (int64_t)A + 2];
     int64_t pos = 0;
+    float wl = 0.f;
     for (int k0 = 0; k0 < nr && pos < t0 + kNbTile; k0 += 32) {
         const int k = k0 + lane;
         int f = 0, n = 0;
-        float dx = 0.f, dy = 0.f, dz = 0.f, sd = 0.f;
+        float dx = 0.f, dy = 0.f, dz = 0.f;
         if (k < nr) {
             const int B = c.near_list[base + k];
             f = c.nfirst[B];
@@ -96,44 +112,112 @@ __device__ int stage_tile(const NbCtx &c, int s, int A, int nr, int64_t t0, floa
             dx = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B], cAx));
             dy = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B + 1], cAy));
             dz = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B + 2], cAz));
-            sd = fabsf(dx) + fabsf(dy) + fabsf(dz);
         }
-        int incl = n;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int64_t my0 = pos + incl - n;
-        for (int q = 0; q < n; ++q) {
-            const int64_t slot = my0 + q - t0;
-            if (slot >= 0 && slot < kNbTile) {
-                const float4 pb = c.p32[f + q];
-                src[slot] = make_float4(dx + pb.x, dy + pb.y, dz + pb.z, sd + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
-                sidx[slot] = f + q;
+        const int excl = warp_excl_scan(n);
+        const int total = __shfl_sync(kFull, excl + n, 31);
+        const int64_t lo = pos > t0 ? pos : t0;
+        const int64_t hi = pos + total < t0 + kNbTile ? pos + total : t0 + kNbTile;
+        for (int64_t j0 = lo; j0 < hi; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const int rel = (int)(j - pos);
+            const int cl = warp_find_slot(excl, rel);
+            const int fc = __shfl_sync(kFull, f, cl), ec = __shfl_sync(kFull, excl, cl);
+            const float cx = __shfl_sync(kFull, dx, cl), cy = __shfl_sync(kFull, dy, cl), cz = __shfl_sync(kFull, dz, cl);
+            if (j < hi) {
+                const int b = fc + rel - ec;
+                const float4 pb = c.p32[b];
+                const float wv = (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z);
+                src[j - t0] = make_float4(cx + pb.x, cy + pb.y, cz + pb.z, wv);
+                sidx[j - t0] = b;
+                if (ORIG) oidx[j - t0] = c.pidx[b];
+                wl = fmaxf(wl, wv);
             }
         }
-        pos += __shfl_sync(0xffffffffu, incl, 31);
+        pos += total;
     }
+    for (int o = 16; o >= 1; o >>= 1) wl = fmaxf(wl, __shfl_xor_sync(kFull, wl, o));
+    wmax = wl;
     __syncwarp();
     const int64_t left = pos - t0;
     return (int)(left < kNbTile ? left : kNbTile);
 }
 
-__device__ inline bool is_neighbour(const NbCtx &c, float4 sa, float h2, int a, float4 sb, int b, int &nfb) {
-    if (a == b) return false;
-    const float dx = sb.x - sa.x, dy = sb.y - sa.y, dz = sb.z - sa.z;
-    const float f = dx * dx + dy * dy + dz * dz - h2;
-    const float Fm = sb.w + sa.w;
-    const float B = (Fm * Fm + h2) * 0x1p-19f + 1e-30f;
-    if (f < -B) return true;
-    if (f > B) return false;
-    ++nfb;
-    const double s2 = __dmul_rn(2.0, c.ph[a]);
-    return dist2_rn(c.px[a], c.py[a], c.pz[a], c.px[b], c.py[b], c.pz[b]) < __dmul_rn(s2, s2);
+// Tests the staged sources [0, ns) against the sink particles a0 + i, i < na (sorted indices).
+// Bit selfq_i = self0 + i (tile-relative slot of a0 + i itself) is cleared.  runs[i] holds the
+// neighbours found so far; with EMIT, a neighbour's original index goes to
+// out[i * stride + run] while run < lim.
+template <bool EMIT>
+__device__ void test_group(const NbCtx &c, const float4 *src, const int32_t *sidx, const int32_t *oidx, int ns,
+                           float wmax, int a0, int na, int64_t self0, int *runs, int32_t *out, int64_t stride,
+                           int64_t lim, int &nfb) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    float sx[kNbGroup], sy[kNbGroup], sz[kNbGroup], lo[kNbGroup], hi[kNbGroup];
+    int run[kNbGroup], selfq[kNbGroup];
+#pragma unroll
+    for (int i = 0; i < kNbGroup; ++i) {
+        const int a = a0 + (i < na ? i : 0);
+        const float4 pa = c.p32[a];
+        const float h2f = 2.0f * c.h32[a];  // = float32(2 h) exactly
+        const float h2 = h2f * h2f;
+        const float F = wmax + (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z));
+        const float B = fmaf(F, F, h2) * 0x1p-19f + 1e-30f;
+        sx[i] = pa.x;
+        sy[i] = pa.y;
+        sz[i] = pa.z;
+        lo[i] = h2 - B;
+        hi[i] = h2 + B;
+        run[i] = i < na ? runs[i] : 0;
+        const int64_t q = self0 + i;
+        selfq[i] = (q >= 0 && q < ns) ? (int)q : -1;
+    }
+    for (int q0 = 0; q0 < ns; q0 += 32) {
+        const int j = q0 + lane;
+        const bool valid = j < ns;
+        const unsigned vm = __ballot_sync(kFull, valid);
+        // padding lanes: a source far away (finite d^2, never below the bound)
+        const float4 b = valid ? src[j] : make_float4(3e18f, 3e18f, 3e18f, 0.f);
+#pragma unroll
+        for (int i = 0; i < kNbGroup; ++i) {
+            if (i < na) {
+                const float dx = b.x - sx[i], dy = b.y - sy[i], dz = b.z - sz[i];
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                unsigned bh = __ballot_sync(kFull, r2 <= hi[i]);
+                if (bh) {  // some lane may hold a neighbour (most chunks have none)
+                    bh &= vm;
+                    unsigned bl = __ballot_sync(kFull, r2 < lo[i]) & vm;
+                    if (bl != bh) {
+                        // inside the band: the float64 test decides
+                        const unsigned amb = bh & ~bl;
+                        bool nb = false;
+                        if ((amb >> lane) & 1u) {
+                            const int a = a0 + i, bs = sidx[j];
+                            const double s2 = __dmul_rn(2.0, c.ph[a]);
+                            nb = dist2_rn(c.px[a], c.py[a], c.pz[a], c.px[bs], c.py[bs], c.pz[bs]) < __dmul_rn(s2, s2);
+                            ++nfb;
+                        }
+                        bl |= __ballot_sync(kFull, nb);
+                    }
+                    const int d = selfq[i] - q0;
+                    if ((unsigned)d < 32u) bl &= ~(1u << d);
+                    if (EMIT && ((bl >> lane) & 1u)) {
+                        const int64_t p = (int64_t)run[i] + __popc(bl & lt);
+                        if (p < lim) out[i * stride + p] = oidx[j];
+                    }
+                    run[i] += __popc(bl);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kNbGroup; ++i)
+        if (i < na && lane == 0) runs[i] = run[i];
+    __syncwarp();
 }
 
-// Count pass (and, when masks are given, the per-chunk neighbour masks).
-__global__ void __launch_bounds__(kNbWarps * 32) k_nb_count(NbCtx c) {
+// Count pass; with EMIT also the slot rows and the queue of long rows.
+template <bool EMIT>
+__global__ void __launch_bounds__(kNbWarps * 32) k_nb_pass(NbCtx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     NbSmem &sm = *reinterpret_cast<NbSmem *>(smem_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -142,177 +226,137 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_nb_count(NbCtx c) {
         const int A = c.sinks[s];
         const int fA = c.nfirst[A], nA = c.ncount[A];
         const int nr = c.near_nr[s];
-        const int64_t S = sources_of(c, s, nr);
-        const int nch = (int)((S + 31) / 32);
-        uint32_t *mrow = c.masks ? c.masks + c.mask_off[s] : nullptr;
-        for (int a0 = 0; a0 < nA; a0 += kMaxSinkPart) {
-            const int na = min(kMaxSinkPart, nA - a0);
-            for (int i = lane; i < na; i += 32) {
-                const int a = fA + a0 + i;
-                const float4 pa = c.p32[a];
-                const float h2 = __double2float_rn(__dmul_rn(2.0, c.ph[a]));
-                sm.snk[w][i] = make_float4(pa.x, pa.y, pa.z, fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z));
-                sm.h2[w][i] = h2 * h2;
-                sm.cnt[w][i] = 0;
-            }
+        const SinkLayout L = sink_layout(c, s, A, nr);
+        for (int p0 = 0; p0 < nA; p0 += kMaxSinkPart) {
+            const int np = min(kMaxSinkPart, nA - p0);
+            for (int i = lane; i < np; i += 32) sm.run[w][i] = 0;
             __syncwarp();
-            for (int64_t t0 = 0; t0 < S; t0 += kNbTile) {
-                const int ns = stage_tile(c, s, A, nr, t0, sm.src[w], sm.sidx[w]);
-                const int c0 = (int)(t0 / 32);
-                for (int i = 0; i < na; ++i) {
-                    const int a = fA + a0 + i;
-                    const float4 sa = sm.snk[w][i];
-                    const float h2 = sm.h2[w][i];
-                    int run = 0;
-                    uint32_t mine = 0;
-                    for (int q0 = 0; q0 < ns; q0 += 32) {
-                        const int q = q0 + lane;
-                        bool nb = false;
-                        if (q < ns) nb = is_neighbour(c, sa, h2, a, sm.src[w][q], sm.sidx[w][q], nfb);
-                        const unsigned bal = __ballot_sync(0xffffffffu, nb);
-                        run += __popc(bal);
-                        if (lane == (q0 >> 5)) mine = bal;
-                    }
-                    if (mrow) {
-                        const int nct = (ns + 31) >> 5;  // chunks of this tile (<= 16)
-                        if (lane < nct) mrow[(int64_t)(a0 + i) * nch + c0 + lane] = mine;
-                    }
-                    if (lane == 0) sm.cnt[w][i] += run;
-                    __syncwarp();
+            for (int64_t t0 = 0; t0 < L.S; t0 += kNbTile) {
+                float wmax;
+                const int ns = stage_tile<EMIT>(c, s, A, nr, t0, sm.src[w], sm.sidx[w], sm.oidx[w], wmax);
+                for (int g = 0; g < np; g += kNbGroup) {
+                    const int a0 = fA + p0 + g;
+                    const int64_t self0 = L.posA < 0 ? INT64_MIN / 2 : L.posA + p0 + g - t0;
+                    test_group<EMIT>(c, sm.src[w], sm.sidx[w], sm.oidx[w], ns, wmax, a0, min(kNbGroup, np - g), self0,
+                                     sm.run[w] + g, EMIT ? c.rows + (int64_t)a0 * kRowCap : nullptr, kRowCap, kRowCap,
+                                     nfb);
+                }
+                __syncwarp();
+            }
+            for (int i = lane; i < np; i += 32) {
+                const int a = fA + p0 + i;
+                const int n = sm.run[w][i];
+                c.counts[c.pidx[a]] = n;
+                if (EMIT && n > kRowCap) {
+                    const int q = atomicAdd(&c.status[ST_LONGROWS], 1);
+                    if (q < c.cap_long) c.long_rows[q] = make_int2(a, s);
                 }
             }
-            for (int i = lane; i < na; i += 32) c.counts[c.pidx[fA + a0 + i]] = sm.cnt[w][i];
             __syncwarp();
         }
     }
-    for (int o = 16; o >= 1; o >>= 1) nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
+    for (int o = 16; o >= 1; o >>= 1) nfb += __shfl_xor_sync(kFull, nfb, o);
     if (lane == 0 && nfb) atomicAdd(&c.status[ST_NBFALLBACK], nfb);
 }
 
-// Fill pass: expand the masks into rows, sort each row, write it.  Shared memory per warp: the
-// prefix table of the sink's candidate cells (first source number, first particle) and one row.
-__global__ void __launch_bounds__(kNbWarps * 32) k_nb_fill(NbCtx c, int table_cap) {
+// Rows longer than kRowCap: one warp per row recomputes it straight into its place.
+__global__ void __launch_bounds__(kNbWarps * 32) k_nb_long(NbCtx c, int nlong) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    NbSmem &sm = *reinterpret_cast<NbSmem *>(smem_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int32_t *tab = reinterpret_cast<int32_t *>(smem_raw) + (size_t)w * (2 * table_cap + kRowWarp);
-    int32_t *tpos = tab, *tfirst = tab + table_cap;
-    int32_t *row = tab + 2 * table_cap;
-    for (int s = blockIdx.x * (blockDim.x >> 5) + w; s < c.nsinks; s += gridDim.x * (blockDim.x >> 5)) {
+    int nfb = 0;
+    for (int q = blockIdx.x * kNbWarps + w; q < nlong; q += gridDim.x * kNbWarps) {
+        const int2 e = c.long_rows[q];
+        const int a = e.x, s = e.y;
         const int A = c.sinks[s];
-        const int fA = c.nfirst[A], nA = c.ncount[A];
-        const int nr = c.near_nr[s];
-        const int64_t base = (int64_t)s * c.cap_near;
-        int pos = 0;
-        for (int k0 = 0; k0 < nr; k0 += 32) {
-            const int k = k0 + lane;
-            int n = 0, f = 0;
-            if (k < nr) {
-                const int B = c.near_list[base + k];
-                n = c.ncount[B];
-                f = c.nfirst[B];
-            }
-            int incl = n;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            if (k < nr) {
-                tpos[k] = pos + incl - n;
-                tfirst[k] = f;
-            }
-            pos += __shfl_sync(0xffffffffu, incl, 31);
-        }
+        const int fA = c.nfirst[A], nr = c.near_nr[s];
+        const SinkLayout L = sink_layout(c, s, A, nr);
+        const int64_t o = c.offsets[c.pidx[a]];
+        if (lane == 0) sm.run[w][0] = 0;
         __syncwarp();
-        const int S = pos;
-        const int nch = (S + 31) / 32;
-        const uint32_t *mrow = c.masks + c.mask_off[s];
-        for (int i = 0; i < nA; ++i) {
-            const int a = fA + i;
-            const int64_t o = c.offsets[c.pidx[a]];
-            const int n = (int)(c.offsets[c.pidx[a] + 1] - o);
-            if (n == 0) continue;
-            const bool fits = n <= kRowWarp;
-            int run = 0;
-            for (int ch0 = 0; ch0 < nch; ch0 += 32) {
-                const int ch = ch0 + lane;
-                uint32_t m = ch < nch ? mrow[(int64_t)i * nch + ch] : 0u;
-                const int pc = __popc(m);
-                int incl = pc;
-                for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, incl, o2);
-                    if (lane >= o2) incl += t;
-                }
-                int p = run + incl - pc;
-                while (m) {
-                    const int bit = __ffs(m) - 1;
-                    m &= m - 1;
-                    const int j = ch * 32 + bit;  // source number
-                    int lo = 0, hi = nr - 1;      // last cell with tpos <= j
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (tpos[mid] <= j) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    const int32_t orig = c.pidx[tfirst[lo] + (j - tpos[lo])];
-                    if (fits) row[p] = orig;
-                    else c.idx[o + p] = orig;
-                    ++p;
-                }
-                run += __shfl_sync(0xffffffffu, incl, 31);
-            }
-            __syncwarp();
-            if (!fits) {
-                if (lane == 0) {
-                    const int slot = atomicAdd(&c.status[ST_LONGROWS], 1);
-                    if (slot < c.cap_long) c.long_rows[slot] = c.pidx[a];
-                }
-                continue;
-            }
-            int p2 = 1;
-            while (p2 < n) p2 <<= 1;
-            for (int q = n + lane; q < p2; q += 32) row[q] = INT32_MAX;
-            __syncwarp();
-            // bitonic network with every comparator ascending: a flip stage (i vs i ^ (k-1)) then
-            // half-cleaners (i vs i ^ j); padding at the end never has to move
-            for (int k = 2; k <= p2; k <<= 1) {
-                for (int q = lane; q < p2; q += 32) {
-                    const int l = q ^ (k - 1);
-                    if (l > q) {
-                        const int32_t x = row[q], y = row[l];
-                        if (x > y) {
-                            row[q] = y;
-                            row[l] = x;
-                        }
-                    }
-                }
-                __syncwarp();
-                for (int j = k >> 2; j > 0; j >>= 1) {
-                    for (int q = lane; q < p2; q += 32) {
-                        const int l = q ^ j;
-                        if (l > q) {
-                            const int32_t x = row[q], y = row[l];
-                            if (x > y) {
-                                row[q] = y;
-                                row[l] = x;
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
-            for (int q = lane; q < n; q += 32) c.idx[o + q] = row[q];
+        for (int64_t t0 = 0; t0 < L.S; t0 += kNbTile) {
+            float wmax;
+            const int ns = stage_tile<true>(c, s, A, nr, t0, sm.src[w], sm.sidx[w], sm.oidx[w], wmax);
+            const int64_t self0 = L.posA < 0 ? INT64_MIN / 2 : L.posA + (a - fA) - t0;
+            test_group<true>(c, sm.src[w], sm.sidx[w], sm.oidx[w], ns, wmax, a, 1, self0, sm.run[w], c.idx + o, 0,
+                             INT64_MAX, nfb);
             __syncwarp();
         }
     }
 }
 
-// Rows longer than one warp's buffer: one block per row, the same network in global memory;
-// positions >= n are +infinity and never compared.
-__global__ void k_sort_long(const int64_t *offsets, int32_t *idx, const int32_t *long_rows, const int *nlong_ptr,
-                            int cap_long) {
-    const int nlong = min(*nlong_ptr, cap_long);
+// Sort 32 R keys, R per lane (element e = 32 r + lane), ascending in the same layout: a bitonic
+// network whose comparators at distance >= 32 stay inside a lane and the others are shuffles.
+template <int R>
+__device__ inline void warp_sort(int32_t (&v)[R]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int p = r ^ (j >> 5);
+                    if (p > r) {
+                        const bool up = ((r * 32 + lane) & k) == 0;
+                        const int32_t x = v[r], y = v[p];
+                        v[r] = up ? min(x, y) : max(x, y);
+                        v[p] = up ? max(x, y) : min(x, y);
+                    }
+                }
+            } else {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int32_t y = __shfl_xor_sync(kFull, v[r], j);
+                    const bool up = ((r * 32 + lane) & k) == 0;
+                    v[r] = (lower == up) ? min(v[r], y) : max(v[r], y);
+                }
+            }
+        }
+    }
+}
+
+template <int R>
+__device__ inline void sort_row(const int32_t *row, int n, int32_t *dst) {
+    const int lane = threadIdx.x & 31;
+    int32_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = r * 32 + lane < n ? row[r * 32 + lane] : INT32_MAX;
+    warp_sort<R>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (r * 32 + lane < n) dst[r * 32 + lane] = v[r];
+}
+
+// One warp per particle (sorted index a): sort its slot row and write it at its offset.
+__global__ void __launch_bounds__(256) k_nb_compact(const int32_t *rows, const int32_t *pidx, const int64_t *offsets,
+                                                    int32_t *idx, int64_t N) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < N; a += nw) {
+        const int r = pidx[a];
+        const int64_t o = offsets[r];
+        const int n = (int)(offsets[r + 1] - o);
+        if (n > kRowCap) continue;  // written by k_nb_long
+        const int32_t *row = rows + a * kRowCap;
+        if (n <= 32)
+            sort_row<1>(row, n, idx + o);
+        else if (n <= 64)
+            sort_row<2>(row, n, idx + o);
+        else
+            sort_row<4>(row, n, idx + o);
+    }
+}
+
+// Long rows: one block per row, a bitonic network in global memory with every comparator
+// ascending (a flip stage, then half-cleaners); positions >= n count as +infinity and are never
+// touched.
+__global__ void k_sort_long(const int64_t *offsets, int32_t *idx, const int2 *long_rows, const int32_t *pidx,
+                            int nlong) {
     for (int q = blockIdx.x; q < nlong; q += gridDim.x) {
-        const int64_t r = long_rows[q];
+        const int64_t r = pidx[long_rows[q].x];
         const int64_t o = offsets[r];
         const int64_t n = offsets[r + 1] - o;
         int64_t p2 = 1;
@@ -373,23 +417,24 @@ NbCtx make_nbctx(rcb_tree *t) {
     c.ph = t->ph;
     c.pidx = t->pidx;
     c.p32 = t->p32;
+    c.h32 = t->h32;
     c.counts = t->nb_count;
     c.offsets = nullptr;
     c.idx = nullptr;
-    c.status = t->d_status;
-    c.mask_off = nullptr;
-    c.masks = nullptr;
+    c.rows = nullptr;
     c.long_rows = t->nb_long;
     c.cap_long = (int)t->N;
+    c.status = t->d_status;
     return c;
 }
 
-int launch_count(rcb_tree *t, const NbCtx &c) {
+template <bool EMIT>
+int launch_pass(rcb_tree *t, const NbCtx &c) {
     const int nsm = sm_count_nb();
     const size_t smem = sizeof(NbSmem);
     const int blocks = std::max(1, std::min((t->nsinks + kNbWarps - 1) / kNbWarps, nsm * 8));
-    RCB_CUDA_TRY(cudaFuncSetAttribute(k_nb_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_nb_count<<<blocks, kNbWarps * 32, smem, t->stream>>>(c); note_launch();
+    RCB_CUDA_TRY(cudaFuncSetAttribute(k_nb_pass<EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_nb_pass<EMIT><<<blocks, kNbWarps * 32, smem, t->stream>>>(c); note_launch();
     RCB_CUDA_TRY(cudaGetLastError());
     return RCB_OK;
 }
@@ -400,46 +445,58 @@ int neighbour_counts(rcb_tree *t, int64_t *counts, int *status) {
     NbCtx c = make_nbctx(t);
     c.counts = counts;
     c.status = status;
-    return launch_count(t, c);
+    return launch_pass<false>(t, c);
+}
+
+int ensure_nb_rows(rcb_tree *t) {
+    if (t->cap_rows >= t->N) return RCB_OK;
+    dev_free(t, t->nb_rows);
+    t->nb_rows = (int32_t *)dev_alloc(t, (size_t)t->N * kRowCap * sizeof(int32_t));
+    if (!t->nb_rows) {
+        t->cap_rows = 0;
+        return RCB_ERR_ALLOC;
+    }
+    t->cap_rows = t->N;
+    return RCB_OK;
+}
+
+int scan_neighbour_counts(rcb_tree *t) {
+    return scan_i64(t->nb_count, t->nb_count, t->N, t->nb_count + t->N, t->scan_tmp, t->stream);
+}
+
+int fetch_neighbour_total(rcb_tree *t) {
+    cudaStream_t st = t->stream;
+    RCB_CUDA_TRY(cudaMemcpyAsync(&t->nb_total, t->nb_count + t->N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status + ST_NBFALLBACK, t->d_status + ST_NBFALLBACK, 2 * sizeof(int),
+                                 cudaMemcpyDeviceToHost, st));
+    RCB_CUDA_TRY(cudaStreamSynchronize(st));
+    t->nb_nlong = std::min(t->h_status[ST_LONGROWS], (int)t->N);
+    t->nb_valid = 1;
+    return RCB_OK;
+}
+
+int count_neighbours(rcb_tree *t) {
+    if (t->nb_valid) return RCB_OK;
+    NbCtx c = make_nbctx(t);
+    stage_begin(t, SG_NB_COUNT);
+    int rc = ensure_nb_rows(t);
+    if (rc) return rc;
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_NBFALLBACK, 0, 2 * sizeof(int), t->stream));
+    c.rows = t->nb_rows;
+    rc = launch_pass<true>(t, c);
+    if (rc) return rc;
+    rc = scan_neighbour_counts(t);
+    if (rc) return rc;
+    stage_end(t, SG_NB_COUNT);
+    return fetch_neighbour_total(t);
 }
 
 int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *needed) {
     cudaStream_t st = t->stream;
     NbCtx c = make_nbctx(t);
     const int nsm = sm_count_nb();
-    RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_NBFALLBACK, 0, 2 * sizeof(int), st));
-    if (!t->nb_valid) {
-        stage_begin(t, SG_NB_COUNT);
-        // per-sink mask sizes and offsets; (re)allocate the mask buffer when it is too small
-        int64_t *words = t->nb_count;  // scratch until the count pass overwrites it
-        const int gw = std::max(1, std::min((t->nsinks + 7) / 8, nsm * 16));
-        k_nb_sizes<<<gw, 256, 0, st>>>(c, words); note_launch();
-        int rc = scan_i64(words, t->nb_maskoff, t->nsinks, t->nb_maskoff + t->nsinks, t->scan_tmp, st);
-        if (rc) return rc;
-        int64_t total_words = 0;
-        RCB_CUDA_TRY(cudaMemcpyAsync(&total_words, t->nb_maskoff + t->nsinks, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        RCB_CUDA_TRY(cudaStreamSynchronize(st));
-        if (total_words > t->cap_masks) {
-            dev_free(t, t->nb_masks);
-            const int64_t cap = total_words + total_words / 8 + 1024;
-            t->nb_masks = (uint32_t *)dev_alloc(t, cap * sizeof(uint32_t));
-            if (!t->nb_masks) {
-                t->cap_masks = 0;
-                return RCB_ERR_ALLOC;
-            }
-            t->cap_masks = cap;
-        }
-        c.mask_off = t->nb_maskoff;
-        c.masks = t->nb_masks;
-        rc = launch_count(t, c);
-        if (rc) return rc;
-        rc = scan_i64(t->nb_count, t->nb_count, t->N, t->nb_count + t->N, t->scan_tmp, st);
-        if (rc) return rc;
-        stage_end(t, SG_NB_COUNT);
-        RCB_CUDA_TRY(cudaMemcpyAsync(&t->nb_total, t->nb_count + t->N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        RCB_CUDA_TRY(cudaStreamSynchronize(st));
-        t->nb_valid = 1;
-    }
+    int rc = count_neighbours(t);
+    if (rc) return rc;
     RCB_CUDA_TRY(cudaMemcpyAsync(offsets, t->nb_count, (t->N + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     *needed = t->nb_total;
     if (!idx) {
@@ -452,22 +509,19 @@ int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, in
     }
     c.offsets = offsets;
     c.idx = idx;
-    c.mask_off = t->nb_maskoff;
-    c.masks = t->nb_masks;
+    c.rows = t->nb_rows;
     stage_begin(t, SG_NB_FILL);
-    // warps per block such that every warp's cell table (cap_near cells) and row fit
-    const size_t per_warp = (2 * (size_t)t->cap_near + kRowWarp) * sizeof(int32_t);
-    int warps = kNbWarps;
-    while (warps > 1 && per_warp * warps > 200 * 1024) warps >>= 1;
-    if (per_warp * warps > 227 * 1024) return RCB_ERR_LIMIT;
-    const size_t smem = per_warp * warps;
-    RCB_CUDA_TRY(cudaFuncSetAttribute(k_nb_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int blocks = std::max(1, std::min((t->nsinks + warps - 1) / warps, nsm * 8));
-    k_nb_fill<<<blocks, warps * 32, smem, st>>>(c, t->cap_near); note_launch();
+    k_nb_compact<<<std::max(1, nsm * 16), 256, 0, st>>>(t->nb_rows, t->pidx, offsets, idx, t->N); note_launch();
     stage_end(t, SG_NB_FILL);
     stage_begin(t, SG_NB_SORT);
-    k_sort_long<<<std::max(1, nsm * 2), 1024, 0, st>>>(offsets, idx, t->nb_long, t->d_status + ST_LONGROWS,
-                                                        (int)t->N); note_launch();
+    if (t->nb_nlong > 0) {
+        const size_t smem = sizeof(NbSmem);
+        RCB_CUDA_TRY(cudaFuncSetAttribute(k_nb_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int blocks = std::max(1, std::min((t->nb_nlong + kNbWarps - 1) / kNbWarps, nsm * 8));
+        k_nb_long<<<blocks, kNbWarps * 32, smem, st>>>(c, t->nb_nlong); note_launch();
+        k_sort_long<<<std::max(1, std::min(t->nb_nlong, nsm * 2)), 1024, 0, st>>>(offsets, idx, t->nb_long, t->pidx,
+                                                                                 t->nb_nlong); note_launch();
+    }
     stage_end(t, SG_NB_SORT);
     RCB_CUDA_TRY(cudaGetLastError());
     RCB_CUDA_TRY(cudaStreamSynchronize(st));

@@ -68,6 +68,7 @@ template <typename F>
 void for_each_array(rcb_tree *t, F f) {
     f((void **)&t->d_status);
     f((void **)&t->d_E);
+    f((void **)&t->d_nbig);
     f((void **)&t->d_maxbits);
     f((void **)&t->d_pairs);
     for (int b = 0; b < 2; ++b) {
@@ -83,11 +84,11 @@ void for_each_array(rcb_tree *t, F f) {
                   (void **)&t->naxis, (void **)&t->nsplit, (void **)&t->nsplitkey, (void **)&t->nS,
                   (void **)&t->nbmin, (void **)&t->nbmax, (void **)&t->nmass, (void **)&t->ncom, (void **)&t->nrg,
                   (void **)&t->nH, (void **)&t->nhint, (void **)&t->nhnode, (void **)&t->nQ, (void **)&t->w32a,
-                  (void **)&t->w32b, (void **)&t->mq32a, (void **)&t->mq32b, (void **)&t->ncomdf,
+                  (void **)&t->w32b, (void **)&t->mq32a, (void **)&t->mq32b, (void **)&t->ncomdf, (void **)&t->nfar,
                   (void **)&t->narrive, (void **)&t->roots, (void **)&t->chunks, (void **)&t->cell_chunk0,
                   (void **)&t->chunk_part, (void **)&t->sinks, (void **)&t->sink_of_leaf, (void **)&t->near_nr,
                   (void **)&t->near_nn, (void **)&t->far_n, (void **)&t->near_list, (void **)&t->far_list,
-                  (void **)&t->coef, (void **)&t->coef32, (void **)&t->nb_count, (void **)&t->nb_long, (void **)&t->nb_maskoff, (void **)&t->nb_masks, (void **)&t->scan_tmp, (void **)&t->tnear_off,
+                  (void **)&t->coef, (void **)&t->coef32, (void **)&t->nb_count, (void **)&t->nb_long, (void **)&t->nb_rows, (void **)&t->scan_tmp, (void **)&t->tnear_off,
                   (void **)&t->tnear_sink, (void **)&t->tfar_off, (void **)&t->tfar_sink, (void **)&t->adj};
     for (void **q : p) f(q);
 }
@@ -101,7 +102,7 @@ void release_arrays(rcb_tree *t) {
     t->cap_L = 0;
     t->cap_near = t->cap_far = 0;
     t->cap_lists_near = t->cap_lists_far = 0;
-    t->cap_masks = 0;
+    t->cap_rows = 0;
 }
 
 int allocate_arrays(rcb_tree *t, int64_t N, int L) {
@@ -117,6 +118,7 @@ int allocate_arrays(rcb_tree *t, int64_t N, int L) {
     };
     A((void **)&t->d_status, ST_NWORDS * sizeof(int));
     A((void **)&t->d_E, 4 * sizeof(int));
+    A((void **)&t->d_nbig, (kMaxL + 2) * sizeof(int32_t));
     A((void **)&t->d_maxbits, 4 * sizeof(unsigned long long));
     A((void **)&t->d_pairs, 2 * sizeof(int64_t));
     for (int b = 0; b < 2; ++b) {
@@ -155,6 +157,7 @@ int allocate_arrays(rcb_tree *t, int64_t N, int L) {
     A((void **)&t->mq32a, nn * sizeof(float4));
     A((void **)&t->mq32b, nn * sizeof(float4));
     A((void **)&t->ncomdf, 3 * nn * sizeof(float2));
+    A((void **)&t->nfar, 4 * nn * sizeof(float4));
     A((void **)&t->narrive, nn * sizeof(int32_t));
     A((void **)&t->roots, cap_roots * sizeof(int32_t));
     A((void **)&t->chunks, cap_chunks * sizeof(int4));
@@ -168,8 +171,7 @@ int allocate_arrays(rcb_tree *t, int64_t N, int L) {
     A((void **)&t->coef, 20 * nl * sizeof(double));
     A((void **)&t->coef32, 20 * nl * sizeof(float));
     A((void **)&t->nb_count, (capN + 1) * sizeof(int64_t));
-    A((void **)&t->nb_long, capN * sizeof(int32_t));
-    A((void **)&t->nb_maskoff, (nl + 1) * sizeof(int64_t));
+    A((void **)&t->nb_long, capN * sizeof(int2));
     A((void **)&t->scan_tmp, (size_t)scan_tmp_bytes(std::max<int64_t>(capN + 1, nl)) + 256);
     if (!ok) return RCB_ERR_ALLOC;
     t->cap_N = capN;
@@ -240,7 +242,7 @@ int rcb_build(const double *x, const double *m, const double *h, int64_t N, cons
         t = new (std::nothrow) rcb_tree;
         if (!t) return RCB_ERR_ALLOC;
         std::memset((void *)t, 0, sizeof(rcb_tree));
-        if (cudaMallocHost((void **)&t->h_status, ST_NWORDS * sizeof(int)) != cudaSuccess) {
+        if (cudaMallocHost((void **)&t->h_status, 2 * ST_NWORDS * sizeof(int)) != cudaSuccess) {
             delete t;
             return RCB_ERR_CUDA;
         }
@@ -290,6 +292,15 @@ int rcb_gravity(rcb_tree *tree, double *acc, double *pot, void *stream) {
     if (!tree || !acc) return RCB_ERR_ARG;
     tree->stream = (cudaStream_t)stream;
     return gravity(tree, acc, pot);
+}
+
+int rcb_gravity_neighbours(rcb_tree *tree, double *acc, double *pot, int64_t *offsets, int64_t *needed,
+                           void *stream) {
+    if (!tree || !acc || !offsets || !needed) return RCB_ERR_ARG;
+    tree->stream = (cudaStream_t)stream;
+    int rc = gravity_neighbours(tree, acc, pot);
+    if (rc) return rc;
+    return neighbours(tree, offsets, nullptr, 0, needed);
 }
 
 int rcb_gravity_backward(rcb_tree *tree, const double *g_acc, const double *g_pot, double *g_x, double *g_m,

@@ -12,6 +12,7 @@ namespace rcb {
 typedef __int128 i128;
 typedef unsigned __int128 u128;
 
+constexpr int kNbRowCap = 128;  // slots of a particle's neighbour row before the compaction
 constexpr int kMaxL = 28;           // deepest supported lowest level (node labels < 2^29)
 constexpr int kTcta = 2048;         // largest cell whose subtree one CTA builds in shared memory
 constexpr int kCtaThreads = 512;    // threads of that CTA
@@ -150,6 +151,30 @@ __device__ inline float2 to_df(double v) {
 }
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+// Exclusive prefix sum of v across the warp.
+__device__ inline int warp_excl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    return incl - v;
+}
+
+// With first[k] (held by lane k) non-decreasing and first[0] = 0 <= rel: the largest k with
+// first[k] <= rel, i.e. the run that holds position rel (empty runs are skipped).
+__device__ inline int warp_find_slot(int first, int rel) {
+    int k = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int cand = k + step;
+        const int v = __shfl_sync(0xffffffffu, first, cand & 31);
+        if (cand < 32 && v <= rel) k = cand;
+    }
+    return k;
+}
+
 __device__ inline void two_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);
     float bb = __fsub_rn(s, a);
@@ -184,8 +209,9 @@ struct rcb_tree {
 
     // status
     int *d_status;  // [ST_NWORDS]
-    int *h_status;  // pinned mirror
+    int *h_status;  // pinned mirror ([ST_NWORDS + 16])
     int *d_E;       // [4] fixed-point exponents E_x, E_y, E_z, E_m
+    int32_t *d_nbig;  // [kMaxL + 2] large cells per level of the level passes
     unsigned long long *d_maxbits;  // [4] bit patterns of max |m x_d| and max m
 
     // ping-pong particle records of the build (SoA)
@@ -209,6 +235,7 @@ struct rcb_tree {
     float4 *w32a, *w32b;     // walk packs: (rg, hint), (com, H) in float32
     float4 *mq32a, *mq32b;   // (M, Qxx, Qxy, Qxz), (Qyy, Qyz, Qzz, 0) in float32
     float2 *ncomdf;          // [nn][3] double-float centre of mass
+    float4 *nfar;            // [nn][4] far-field record: (COM hi, M), (COM lo, Qxx), (Qxy, Qxz, Qyy, Qyz), (Qzz)
     int32_t *narrive;        // bottom-up arrival counters
 
     // level passes over large cells
@@ -232,10 +259,10 @@ struct rcb_tree {
     double *coef;    // [nsinks][20] far-field Taylor coefficients
     float *coef32;   // their float32 values (mixed form)
     int64_t *nb_count;
-    int32_t *nb_long;  // [N] rows queued for the block-level sort
-    int64_t *nb_maskoff;  // [nleaves + 1] word offsets of each sink's neighbour masks
-    uint32_t *nb_masks;   // ballot masks of the count pass (grown on demand)
-    int64_t cap_masks;
+    int2 *nb_long;     // [N] (sorted particle, sink) of rows longer than the slot rows
+    int32_t *nb_rows;  // [N][128] neighbour rows before the compaction (allocated on first use)
+    int64_t cap_rows;
+    int nb_nlong;
     void *scan_tmp;
     int64_t cap_scan;
     int64_t nb_total;
@@ -273,8 +300,13 @@ int walk_tree(rcb_tree *t);
 // neighbours.cu
 int neighbour_counts(rcb_tree *t, int64_t *counts, int *status);  // count pass into caller memory
 int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *needed);
+int ensure_nb_rows(rcb_tree *t);          // slot rows of the neighbour pass ([N][kNbRowCap])
+int count_neighbours(rcb_tree *t);        // counts, slot rows and offsets (nb_count) unless valid
+int scan_neighbour_counts(rcb_tree *t);   // nb_count: counts by original index -> offsets
+int fetch_neighbour_total(rcb_tree *t);   // total and long-row count to the host; counts valid
 // gravity.cu
 int gravity(rcb_tree *t, double *acc, double *pot);
+int gravity_neighbours(rcb_tree *t, double *acc, double *pot);  // mixed near field + neighbour counts/rows
 // backward.cu
 int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double *gx, double *gm);
 

@@ -1,11 +1,9 @@
 // Per-sink tree walk (Sec. 2.2, Sec. 2.3.1, Sec. 2.4.1) emitting near and far lists.
 //
-// One warp walks for 32 consecutive sinks (non-empty ll-cells in label order, hence spatial
-// neighbours).  The warp visits nodes in the depth-first order of Sec. 2.2 starting at node 2;
-// at a node, only the lanes whose walk reached it (every ancestor opened by that lane) decide;
-// the warp descends when any lane opens the node and skips the subtree otherwise.  Each lane's
-// decisions -- and therefore its lists -- are exactly those of its own single-sink walk, while
-// control flow stays uniform and node loads are broadcasts.
+// One thread walks for one sink (non-empty ll-cells in label order, so the 32 sinks of a warp
+// are spatial neighbours and share most of the nodes they load).  The walk is the stackless
+// depth-first order of Sec. 2.2 on heap labels, starting at node 2: after a node that is not
+// opened, climb while the node is a right child, then step to the next label.
 //
 // Decisions (in this order, Sec. 2.4.1):
 //   reachable   |r_gA - r_gB|^2 < (h_node(A) + h_node_int(B))^2   -> ll-cell: near + candidate
@@ -46,57 +44,49 @@ struct WalkCtx {
 __device__ inline float sq(float v) { return v * v; }
 
 __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
-    __shared__ uint32_t masks[kWalkWarps][kMaxL + 2];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int gw = blockIdx.x * kWalkWarps + w;
-    const int s = gw * 32 + lane;
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = s < c.nsinks;
-    const uint32_t valid_mask = __ballot_sync(0xffffffffu, valid);
-    if (valid_mask == 0) return;
-    const int A = valid ? c.sinks[s] : c.sinks[0];
-    const float4 a32 = c.w32a[A], b32 = c.w32b[A];
-    const float3 rgA = make_float3(a32.x, a32.y, a32.z);
-    const float3 comA = make_float3(b32.x, b32.y, b32.z);
-    const float hA = __double2float_rn(c.nhnode[A]);
-    const float3 rgAabs = make_float3(fabsf(rgA.x), fabsf(rgA.y), fabsf(rgA.z));
-    const float3 comAabs = make_float3(fabsf(comA.x), fabsf(comA.y), fabsf(comA.z));
-    const int64_t near_base = (int64_t)s * c.cap_near;
-    const int64_t far_base = (int64_t)s * c.cap_far;
     int nr = 0, nnr = 0, nf = 0, nfallback = 0;
-
-    if (lane == 0) masks[w][0] = valid_mask;
-    __syncwarp();
-    int n = 2, lev = 1;
-    int64_t iter = 0;
-    const int64_t max_iter = 2 * c.nn + 8;
     bool limit = false;
-    while (true) {
-        if (++iter > max_iter) {
-            limit = true;
-            break;
-        }
-        const uint32_t act = masks[w][lev - 1];
-        const int cnt = c.ncount[n];
-        bool open = false;
-        if (cnt > 0) {
-            const float4 na = c.w32a[n], nb = c.w32b[n];
-            if ((act >> lane) & 1u) {
-                const bool is_leaf = lev == c.L;
+    if (valid) {
+        const int A = c.sinks[s];
+        const float4 a32 = c.w32a[A], b32 = c.w32b[A];
+        const float3 rgA = make_float3(a32.x, a32.y, a32.z);
+        const float3 comA = make_float3(b32.x, b32.y, b32.z);
+        const float hA = __double2float_rn(c.nhnode[A]);
+        const float3 rgAabs = make_float3(fabsf(rgA.x), fabsf(rgA.y), fabsf(rgA.z));
+        const float3 comAabs = make_float3(fabsf(comA.x), fabsf(comA.y), fabsf(comA.z));
+        const int64_t near_base = (int64_t)s * c.cap_near;
+        const int64_t far_base = (int64_t)s * c.cap_far;
+        const int leaf0 = 1 << c.L;
+        int n = 2;
+        int64_t iter = 0;
+        const int64_t max_iter = 2 * c.nn + 8;
+        while (true) {
+            if (++iter > max_iter) {
+                limit = true;
+                break;
+            }
+            bool open = false;
+            if (c.ncount[n] > 0) {
+                const float4 na = c.w32a[n], nb = c.w32b[n];
+                const bool is_leaf = n >= leaf0;
                 // reachability
-                float dx = rgA.x - na.x, dy = rgA.y - na.y, dz = rgA.z - na.z;
-                float d2 = dx * dx + dy * dy + dz * dz;
-                float rr = hA + na.w;
-                float f = d2 - rr * rr;
-                float F = sq(rgAabs.x + fabsf(na.x)) + sq(rgAabs.y + fabsf(na.y)) + sq(rgAabs.z + fabsf(na.z)) + rr * rr;
-                float B = F * 0x1p-20f + 1e-30f;
+                const float dx = rgA.x - na.x, dy = rgA.y - na.y, dz = rgA.z - na.z;
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                const float rr = hA + na.w;
+                const float f = d2 - rr * rr;
+                const float F = sq(rgAabs.x + fabsf(na.x)) + sq(rgAabs.y + fabsf(na.y)) + sq(rgAabs.z + fabsf(na.z)) + rr * rr;
+                const float B = F * 0x1p-20f + 1e-30f;
                 bool reach;
                 if (f < -B) reach = true;
                 else if (f > B) reach = false;
                 else {
                     ++nfallback;
-                    double e2 = dist2_rn(c.nrg[3 * (int64_t)A], c.nrg[3 * (int64_t)A + 1], c.nrg[3 * (int64_t)A + 2],
-                                         c.nrg[3 * (int64_t)n], c.nrg[3 * (int64_t)n + 1], c.nrg[3 * (int64_t)n + 2]);
-                    double r = __dadd_rn(c.nhnode[A], c.nhint[n]);
+                    const double e2 = dist2_rn(c.nrg[3 * (int64_t)A], c.nrg[3 * (int64_t)A + 1], c.nrg[3 * (int64_t)A + 2],
+                                               c.nrg[3 * (int64_t)n], c.nrg[3 * (int64_t)n + 1], c.nrg[3 * (int64_t)n + 2]);
+                    const double r = __dadd_rn(c.nhnode[A], c.nhint[n]);
                     reach = e2 < __dmul_rn(r, r);
                 }
                 if (reach) {
@@ -107,20 +97,20 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
                         open = true;
                     }
                 } else {
-                    float ex = comA.x - nb.x, ey = comA.y - nb.y, ez = comA.z - nb.z;
-                    float R2 = ex * ex + ey * ey + ez * ez;
-                    float fm = nb.w * nb.w - c.theta2f * R2;
-                    float Fm = nb.w * nb.w +
-                               c.theta2f * (sq(comAabs.x + fabsf(nb.x)) + sq(comAabs.y + fabsf(nb.y)) + sq(comAabs.z + fabsf(nb.z)));
-                    float Bm = Fm * 0x1p-20f + 1e-30f;
+                    const float ex = comA.x - nb.x, ey = comA.y - nb.y, ez = comA.z - nb.z;
+                    const float R2 = ex * ex + ey * ey + ez * ez;
+                    const float fm = nb.w * nb.w - c.theta2f * R2;
+                    const float Fm = nb.w * nb.w +
+                                     c.theta2f * (sq(comAabs.x + fabsf(nb.x)) + sq(comAabs.y + fabsf(nb.y)) + sq(comAabs.z + fabsf(nb.z)));
+                    const float Bm = Fm * 0x1p-20f + 1e-30f;
                     bool mac;
                     if (fm < -Bm) mac = true;
                     else if (fm > Bm) mac = false;
                     else {
                         ++nfallback;
-                        double R2d = dist2_rn(c.ncom[3 * (int64_t)A], c.ncom[3 * (int64_t)A + 1], c.ncom[3 * (int64_t)A + 2],
-                                              c.ncom[3 * (int64_t)n], c.ncom[3 * (int64_t)n + 1], c.ncom[3 * (int64_t)n + 2]);
-                        double H = c.nH[n];
+                        const double R2d = dist2_rn(c.ncom[3 * (int64_t)A], c.ncom[3 * (int64_t)A + 1], c.ncom[3 * (int64_t)A + 2],
+                                                    c.ncom[3 * (int64_t)n], c.ncom[3 * (int64_t)n + 1], c.ncom[3 * (int64_t)n + 2]);
+                        const double H = c.nH[n];
                         mac = __dmul_rn(H, H) < __dmul_rn(c.theta2, R2d);
                     }
                     if (mac) {
@@ -134,39 +124,30 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
                     }
                 }
             }
+            if (open) {
+                n = 2 * n;
+                continue;
+            }
+            while (n & 1) n >>= 1;
+            n += 1;
+            if (n == 1) break;
         }
-        const uint32_t om = __ballot_sync(0xffffffffu, open);
-        if (om) {
-            __syncwarp();
-            if (lane == 0) masks[w][lev] = om;
-            __syncwarp();
-            n = 2 * n;
-            ++lev;
-            continue;
-        }
-        while (n & 1) {
-            n >>= 1;
-            --lev;
-        }
-        n += 1;
-        if (n == 1) break;
-    }
-    if (valid) {
         c.near_nr[s] = nr;
         c.near_nn[s] = nnr;
         c.far_n[s] = nf;
     }
-    int mn = valid ? nr + nnr : 0, mf = valid ? nf : 0;
+    int mn = nr + nnr, mf = nf;
     for (int o = 16; o >= 1; o >>= 1) {
         mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, o));
         mf = max(mf, __shfl_xor_sync(0xffffffffu, mf, o));
         nfallback += __shfl_xor_sync(0xffffffffu, nfallback, o);
     }
+    const bool anylimit = __any_sync(0xffffffffu, limit);
     if (lane == 0) {
         atomicMax(&c.status[ST_MAXNEAR], mn);
         atomicMax(&c.status[ST_MAXFAR], mf);
         if (nfallback) atomicAdd(&c.status[ST_FALLBACK], nfallback);
-        if (limit) atomicOr(&c.status[ST_ERR], ERRBIT_LIMIT);
+        if (anylimit) atomicOr(&c.status[ST_ERR], ERRBIT_LIMIT);
     }
 }
 
@@ -242,8 +223,7 @@ int walk_tree(rcb_tree *t) {
         c.near_nn = t->near_nn;
         c.far_n = t->far_n;
         RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_MAXNEAR, 0, 3 * sizeof(int), st));
-        int warps = (t->nsinks + 31) / 32;
-        int blocks = (warps + kWalkWarps - 1) / kWalkWarps;
+        int blocks = (t->nsinks + kWalkWarps * 32 - 1) / (kWalkWarps * 32);
         if (blocks > 0) k_walk<<<blocks, kWalkWarps * 32, 0, st>>>(c); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());
         RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status, t->d_status, ST_NWORDS * sizeof(int), cudaMemcpyDeviceToHost, st));

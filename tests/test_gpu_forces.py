@@ -79,6 +79,27 @@ def test_neighbours_bit_exact(kind, N, mass, theta, nsample):
         assert np.array_equal(row, want)
 
 
+def test_neighbours_long_rows():
+    # every 37th particle gets 3x its smoothing length: rows of ~27x the usual length (far past
+    # the 64 slots of the in-warp sort) and sinks with several tiles of candidates
+    import paper_1108_0028_gb300 as rcb
+    N = 30000
+    x, m, h = synth.make_particles("sphere", N, synth.seed_for(4, 77), "loguniform10")
+    h = h.copy()
+    h[::37] *= 3.0
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(0.6)
+    ro, ri = ref.neighbours()
+    lengths = np.diff(ro)
+    assert lengths.max() > 512 and np.sum(lengths > 64) > 100 and np.sum((lengths > 32) & (lengths <= 64)) > 100
+    tree = rcb.RCBTree(*_gpu(x, m, h), theta=0.6)
+    go, gi = tree.neighbours()
+    assert np.array_equal(go.cpu().numpy(), ro) and np.array_equal(gi.cpu().numpy(), ri)
+    # a second call reuses the counts and rows and gives the same lists
+    go2, gi2 = tree.neighbours()
+    assert np.array_equal(go2.cpu().numpy(), ro) and np.array_equal(gi2.cpu().numpy(), ri)
+
+
 @pytest.mark.parametrize("kind,N,mass,theta,nsample", CASES)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_gravity_matches_oracle(kind, N, mass, theta, nsample, precision):
@@ -104,6 +125,29 @@ def test_gravity_matches_oracle(kind, N, mass, theta, nsample, precision):
         assert np.sqrt(np.mean(ep * ep)) <= MIXED_RMS
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gravity_wide_smoothing_length_spread(precision):
+    # h spread over a factor ~30 (every 37th particle 3x, every 101st 0.1x): the mixed near field
+    # sorts sources into those inside some kernel support of the sink cell and those certainly
+    # outside every support; both kinds meet here in one tile
+    import paper_1108_0028_gb300 as rcb
+    N = 30000
+    x, m, h = synth.make_particles("sphere", N, synth.seed_for(4, 78), "loguniform10")
+    h = h.copy()
+    h[::37] *= 3.0
+    h[::101] *= 0.1
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(0.6)
+    oa, op = ref.gravity()
+    tree = rcb.RCBTree(*_gpu(x, m, h), theta=0.6, precision=precision)
+    ga, gp = tree.gravity()
+    e = rel_errors(ga.cpu().numpy(), oa)
+    ep = np.abs(gp.cpu().numpy() - op) / np.abs(op)
+    rms_b, p999_b = (FP64_RMS, FP64_P999) if precision == "fp64" else (MIXED_RMS, MIXED_P999)
+    assert np.sqrt(np.mean(e ** 2)) < rms_b and np.quantile(e, 0.999) < p999_b
+    assert np.sqrt(np.mean(ep ** 2)) < rms_b
+
+
 def test_gravity_theta_zero_equals_direct_sum():
     import paper_1108_0028_gb300 as rcb
     x, m, h = synth.make_particles("plummer", 3000, 77, "loguniform10")
@@ -124,3 +168,67 @@ def test_precision_switch_on_one_tree():
     a32, _ = tree.gravity()
     e = rel_errors(a32.cpu().numpy(), a64.cpu().numpy())
     assert 0 < e.max() < 1e-3
+
+
+FUSED_CASES = [
+    ("plummer", 4096, "equal", 0.5, 1.0),
+    ("sphere", 20000, "loguniform10", 0.7, 1.0),
+    ("sphere", 30000, "loguniform10", 0.6, 3.0),   # every 37th h x3: rows past the 128 slots
+    ("cube", 5000, "loguniform10", 0.0, 1.0),      # theta = 0: everything in the near list
+]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("kind,N,mass,theta,hscale", FUSED_CASES)
+def test_gravity_neighbours_fused(kind, N, mass, theta, hscale, precision):
+    # one pass for forces and neighbour lists: the lists are bit-exact (the same exact decisions
+    # as rcb_neighbours), the forces meet the bounds of the form
+    import paper_1108_0028_gb300 as rcb
+    x, m, h = synth.make_particles(kind, N, synth.seed_for(4, 300 + N), mass)
+    h = h.copy()
+    h[::37] *= hscale
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(theta)
+    ro, ri = ref.neighbours()
+    oa, op = ref.gravity()
+    tree = rcb.RCBTree(*_gpu(x, m, h), theta=theta, precision=precision)
+    ga, gp, go, gi = tree.gravity_neighbours()
+    assert np.array_equal(go.cpu().numpy(), ro) and np.array_equal(gi.cpu().numpy(), ri)
+    e = rel_errors(ga.cpu().numpy(), oa)
+    rms_b, p999_b = (FP64_RMS, FP64_P999) if precision == "fp64" else (MIXED_RMS, MIXED_P999)
+    assert np.sqrt(np.mean(e ** 2)) < rms_b and np.quantile(e, 0.999) < p999_b
+    ep = np.abs(gp.cpu().numpy() - op) / np.abs(op)
+    assert np.sqrt(np.mean(ep ** 2)) < rms_b
+    # the plain entry points on the same tree agree: gravity() bit for bit in the FP64 form and to
+    # the bounds in the mixed form (the fused kernel stages its cell offsets differently), and
+    # neighbours() reuses the counted rows
+    pa, _ = tree.gravity()
+    if precision == "fp64":
+        assert np.array_equal(pa.cpu().numpy(), ga.cpu().numpy())
+    else:
+        e2 = rel_errors(pa.cpu().numpy(), ga.cpu().numpy())
+        assert np.sqrt(np.mean(e2 ** 2)) < MIXED_RMS
+    no, ni = tree.neighbours()
+    assert np.array_equal(no.cpu().numpy(), ro) and np.array_equal(ni.cpu().numpy(), ri)
+
+
+def test_gravity_neighbours_after_rebuild_and_refit():
+    # counts are recomputed after a rebuild (new lists) and after a refit (new positions)
+    import paper_1108_0028_gb300 as rcb
+    N = 12000
+    x, m, h = synth.make_particles("sphere", N, synth.seed_for(4, 901), "loguniform10")
+    x2 = synth.jitter(x, 3e-3, synth.seed_for(4, 902))
+    tree = rcb.RCBTree(*_gpu(x, m, h), theta=0.6)
+    tree.gravity_neighbours()
+    tree.rebuild(*_gpu(x2, m, h))
+    ref = oracle.OracleTree(x2, m, h)
+    ref.walk(0.6)
+    ro, ri = ref.neighbours()
+    _, _, go, gi = tree.gravity_neighbours()
+    assert np.array_equal(go.cpu().numpy(), ro) and np.array_equal(gi.cpu().numpy(), ri)
+    x3 = synth.jitter(x2, 1e-4, synth.seed_for(4, 903))
+    tree.refit(*_gpu(x3, m))
+    ref.refit(x3, m)
+    ro, ri = ref.neighbours()
+    _, _, go, gi = tree.gravity_neighbours()
+    assert np.array_equal(go.cpu().numpy(), ro) and np.array_equal(gi.cpu().numpy(), ri)
