@@ -219,22 +219,20 @@ template <bool NB>
 struct NearSmem {
     static constexpr size_t bytes =
         kNearTile * (sizeof(float4) + sizeof(float) + sizeof(uint16_t)) + kGroupMixed * sizeof(float4) +
-        (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * (sizeof(float2) + sizeof(int)) : 0);
+        (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * sizeof(float2) : 0);
     float4 *src;    // (d_b relative to the sink's centre of mass, m_b)
     float *hs;      // h_b
     float4 *snk;    // (d_a, h_a) of the current group
     uint16_t *perm;
     int32_t *sidx;  // NB
     float2 *band;   // NB: per sink particle (2h)^2 -+ B
-    int *run;       // NB: per sink particle, neighbours found so far
     __device__ NearSmem(unsigned char *p) {
         src = reinterpret_cast<float4 *>(p);
         hs = reinterpret_cast<float *>(src + kNearTile);
         snk = reinterpret_cast<float4 *>(hs + kNearTile);
         band = reinterpret_cast<float2 *>(snk + kGroupMixed);
         sidx = reinterpret_cast<int32_t *>(band + (NB ? kGroupMixed : 0));
-        run = reinterpret_cast<int *>(sidx + (NB ? kNearTile : 0));
-        perm = reinterpret_cast<uint16_t *>(run + (NB ? kGroupMixed : 0));
+        perm = reinterpret_cast<uint16_t *>(sidx + (NB ? kNearTile : 0));
     }
 };
 
@@ -345,17 +343,19 @@ __device__ int partition_near(const NearSmem<NB> &sm, int ns, float RA, float HA
     return nclose;
 }
 
-// Neighbour-search state of one group of sink particles (running counts sit in shared memory).
+// Neighbour-search state of one group of sink particles.
 struct NbGroup {
     int a0;   // sorted index of the group's first sink particle
+    int run;  // lane i < G: neighbours of sink particle i found so far
     int nfb;  // float64 decisions taken
 };
 
 // Neighbour test of staged source b (lane) against sink particle i of the group: float32 d^2
-// against the particle's band, float64 inside it; b's original index is appended to a's row.
+// against the particle's band, float64 inside it; b's sorted index is appended to a's row.
+// own: the chunk holds one of the group's own particles.
 template <bool NB>
 __device__ __forceinline__ void near_neighbours_of(const GCtx &c, const NearSmem<NB> &sm, int i, float4 b, int sb,
-                                                unsigned cand, NbGroup &g) {
+                                                   unsigned cand, bool own, NbGroup &g) {
     const int lane = threadIdx.x & 31;
     const float4 sa = sm.snk[i];
     const float dx = sa.x - b.x, dy = sa.y - b.y, dz = sa.z - b.z;
@@ -374,15 +374,13 @@ __device__ __forceinline__ void near_neighbours_of(const GCtx &c, const NearSmem
         }
         bl |= __ballot_sync(0xffffffffu, nb);
     }
-    bl &= ~__ballot_sync(0xffffffffu, sb == g.a0 + i);  // not itself
-    const int run = sm.run[i];
+    if (own) bl &= ~__ballot_sync(0xffffffffu, sb == g.a0 + i);  // not itself
+    const int run = __shfl_sync(0xffffffffu, g.run, i);
     if ((bl >> lane) & 1u) {
         const int p = run + __popc(bl & ((1u << lane) - 1u));
-        if (p < kNbRowCap) c.nb_rows[(int64_t)(g.a0 + i) * kNbRowCap + p] = c.pidx[sb];
+        if (p < kNbRowCap) c.nb_rows[(int64_t)(g.a0 + i) * kNbRowCap + p] = sb;
     }
-    __syncwarp();
-    if (lane == 0) sm.run[i] = run + __popc(bl);
-    __syncwarp();
+    if (lane == i) g.run += __popc(bl);
 }
 
 // The pair loops of one staged tile for G sink particles (snk[0, G)), folded into the lane's
@@ -429,6 +427,7 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, int ns, 
             if (NB) sb = sm.sidx[pj];
         }
         const unsigned cand = NB ? __ballot_sync(0xffffffffu, sb >= 0) : 0u;  // candidate-cell sources
+        const bool own = NB && __any_sync(0xffffffffu, sb >= g.a0 && sb < g.a0 + G);
         unsigned pend = 0;  // sink particles with a possible neighbour in this chunk
 #pragma unroll
         for (int i = 0; i < G; ++i) {
@@ -468,7 +467,7 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, int ns, 
             while (pend) {
                 const int i = __ffs(pend) - 1;
                 pend &= pend - 1;
-                near_neighbours_of<NB>(c, sm, i, b, sb, cand, g);
+                near_neighbours_of<NB>(c, sm, i, b, sb, cand, own, g);
             }
         }
     }
@@ -535,7 +534,7 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             }
             if (NB) {
                 g.a0 = fA + a0;
-                if (lane < kGroupMixed) sm.run[lane] = 0;
+                g.run = 0;
             }
             __syncwarp();
             float rs = 0.f, rc = 0.f;  // compensated total of value lane mod 4 G (= 4 i + q)
@@ -594,7 +593,7 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             }
             if (NB && lane < na) {
                 const int a = fA + a0 + lane;
-                const int n = sm.run[lane];
+                const int n = g.run;
                 c.nb_counts[c.pidx[a]] = n;
                 if (n > kNbRowCap) {
                     const int q = atomicAdd(&c.status[ST_LONGROWS], 1);

@@ -7,10 +7,10 @@
 //          in float64, then each particle's float32 offset from its own cell's centre of mass).
 //          Eight sink particles sit in registers; lanes take 32 sources at a time and every pair
 //          test is one bit of a warp ballot.  A particle's count goes to its original index and
-//          its neighbours' original indices to a row of kRowCap slots; longer rows are queued.
+//          its neighbours' sorted indices to a row of kRowCap slots; longer rows are queued.
 // scan     exclusive int64 scan over original indices gives the CSR offsets.
-// compact  one warp per particle sorts its slot row (bitonic network of shuffles) and writes it
-//          at its offset.
+// compact  one warp per particle maps its slot row to original indices, sorts it (bitonic
+//          network of shuffles) and writes it at its offset.
 // long     queued rows are recomputed straight into place, one warp each, and sorted by one
 //          block each.
 // The float32 test compares d^2 with (2h)^2 -+ B, B = 2^-19 F, F = (W + |d_a|_1)^2 + (2h)^2 with W
@@ -49,7 +49,7 @@ struct NbCtx {
     int64_t *counts;         // [N] by original index
     const int64_t *offsets;  // [N+1]
     int32_t *idx;
-    int32_t *rows;   // [N][kRowCap] by sorted index
+    int32_t *rows;   // [N][kRowCap] by sorted index, entries sorted indices
     int2 *long_rows;  // (sorted particle, sink) of rows longer than kRowCap
     int cap_long;
     int *status;
@@ -144,10 +144,10 @@ __device__ int stage_tile(const NbCtx &c, int s, int A, int nr, int64_t t0, floa
 
 // Tests the staged sources [0, ns) against the sink particles a0 + i, i < na (sorted indices).
 // Bit selfq_i = self0 + i (tile-relative slot of a0 + i itself) is cleared.  runs[i] holds the
-// neighbours found so far; with EMIT, a neighbour's original index goes to
-// out[i * stride + run] while run < lim.
+// neighbours found so far; with EMIT, a neighbour's emit[j] goes to out[i * stride + run] while
+// run < lim.
 template <bool EMIT>
-__device__ void test_group(const NbCtx &c, const float4 *src, const int32_t *sidx, const int32_t *oidx, int ns,
+__device__ void test_group(const NbCtx &c, const float4 *src, const int32_t *sidx, const int32_t *emit, int ns,
                            float wmax, int a0, int na, int64_t self0, int *runs, int32_t *out, int64_t stride,
                            int64_t lim, int &nfb) {
     const int lane = threadIdx.x & 31;
@@ -202,7 +202,7 @@ __device__ void test_group(const NbCtx &c, const float4 *src, const int32_t *sid
                     if ((unsigned)d < 32u) bl &= ~(1u << d);
                     if (EMIT && ((bl >> lane) & 1u)) {
                         const int64_t p = (int64_t)run[i] + __popc(bl & lt);
-                        if (p < lim) out[i * stride + p] = oidx[j];
+                        if (p < lim) out[i * stride + p] = emit[j];
                     }
                     run[i] += __popc(bl);
                 }
@@ -233,11 +233,11 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_nb_pass(NbCtx c) {
             __syncwarp();
             for (int64_t t0 = 0; t0 < L.S; t0 += kNbTile) {
                 float wmax;
-                const int ns = stage_tile<EMIT>(c, s, A, nr, t0, sm.src[w], sm.sidx[w], sm.oidx[w], wmax);
+                const int ns = stage_tile<false>(c, s, A, nr, t0, sm.src[w], sm.sidx[w], sm.oidx[w], wmax);
                 for (int g = 0; g < np; g += kNbGroup) {
                     const int a0 = fA + p0 + g;
                     const int64_t self0 = L.posA < 0 ? INT64_MIN / 2 : L.posA + p0 + g - t0;
-                    test_group<EMIT>(c, sm.src[w], sm.sidx[w], sm.oidx[w], ns, wmax, a0, min(kNbGroup, np - g), self0,
+                    test_group<EMIT>(c, sm.src[w], sm.sidx[w], sm.sidx[w], ns, wmax, a0, min(kNbGroup, np - g), self0,
                                      sm.run[w] + g, EMIT ? c.rows + (int64_t)a0 * kRowCap : nullptr, kRowCap, kRowCap,
                                      nfb);
                 }
@@ -319,18 +319,19 @@ __device__ inline void warp_sort(int32_t (&v)[R]) {
 }
 
 template <int R>
-__device__ inline void sort_row(const int32_t *row, int n, int32_t *dst) {
+__device__ inline void sort_row(const int32_t *row, const int32_t *pidx, int n, int32_t *dst) {
     const int lane = threadIdx.x & 31;
     int32_t v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = r * 32 + lane < n ? row[r * 32 + lane] : INT32_MAX;
+    for (int r = 0; r < R; ++r) v[r] = r * 32 + lane < n ? pidx[row[r * 32 + lane]] : INT32_MAX;
     warp_sort<R>(v);
 #pragma unroll
     for (int r = 0; r < R; ++r)
         if (r * 32 + lane < n) dst[r * 32 + lane] = v[r];
 }
 
-// One warp per particle (sorted index a): sort its slot row and write it at its offset.
+// One warp per particle (sorted index a): map its slot row to original indices, sort it and
+// write it at its offset.
 __global__ void __launch_bounds__(256) k_nb_compact(const int32_t *rows, const int32_t *pidx, const int64_t *offsets,
                                                     int32_t *idx, int64_t N) {
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -342,11 +343,11 @@ __global__ void __launch_bounds__(256) k_nb_compact(const int32_t *rows, const i
         if (n > kRowCap) continue;  // written by k_nb_long
         const int32_t *row = rows + a * kRowCap;
         if (n <= 32)
-            sort_row<1>(row, n, idx + o);
+            sort_row<1>(row, pidx, n, idx + o);
         else if (n <= 64)
-            sort_row<2>(row, n, idx + o);
+            sort_row<2>(row, pidx, n, idx + o);
         else
-            sort_row<4>(row, n, idx + o);
+            sort_row<4>(row, pidx, n, idx + o);
     }
 }
 
