@@ -218,11 +218,13 @@ constexpr int kNearTile = 512;    // staged sources per warp
 template <bool NB>
 struct NearSmem {
     static constexpr size_t bytes =
-        kNearTile * (sizeof(float4) + sizeof(float) + sizeof(uint16_t)) + kGroupMixed * sizeof(float4) +
-        (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * sizeof(float2) : 0);
+        kNearTile * (sizeof(float4) + sizeof(float) + sizeof(uint16_t)) + 2 * kGroupMixed * sizeof(float4) +
+        (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * sizeof(float2) + kGroupMixed / 2 * sizeof(float2) : 0);
     float4 *src;    // (d_b relative to the sink's centre of mass, m_b)
     float *hs;      // h_b
     float4 *snk;    // (d_a, h_a) of the current group
+    float4 *snk2;   // the same by pairs (i, i + 1): (x_i, x_i+1, y_i, y_i+1), (z_i, z_i+1, h_i, h_i+1)
+    float2 *hi2;    // NB: upper band edges by pairs
     uint16_t *perm;
     int32_t *sidx;  // NB
     float2 *band;   // NB: per sink particle (2h)^2 -+ B
@@ -230,8 +232,10 @@ struct NearSmem {
         src = reinterpret_cast<float4 *>(p);
         hs = reinterpret_cast<float *>(src + kNearTile);
         snk = reinterpret_cast<float4 *>(hs + kNearTile);
-        band = reinterpret_cast<float2 *>(snk + kGroupMixed);
-        sidx = reinterpret_cast<int32_t *>(band + (NB ? kGroupMixed : 0));
+        snk2 = snk + kGroupMixed;
+        band = reinterpret_cast<float2 *>(snk2 + kGroupMixed);
+        hi2 = band + (NB ? kGroupMixed : 0);
+        sidx = reinterpret_cast<int32_t *>(hi2 + (NB ? kGroupMixed / 2 : 0));
         perm = reinterpret_cast<uint16_t *>(sidx + (NB ? kNearTile : 0));
     }
 };
@@ -390,31 +394,46 @@ __device__ __forceinline__ void near_neighbours_of(const GCtx &c, const NearSmem
 template <int G, bool NB>
 __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, int ns, int nclose, float &rs, float &rc,
                                  NbGroup &g) {
+    static_assert(G % 2 == 0, "sink particles go by pairs");
     const int lane = threadIdx.x & 31;
-    float In[4][G];
+    // In[q][p]: quantity q (a_x, a_y, a_z, phi) of sink particles 2p and 2p + 1.  Every pair
+    // term below is computed for two sink particles at once with paired float32 instructions
+    // (each half rounds exactly as the scalar operation would).
+    float2 In[4][G / 2];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int i = 0; i < G; ++i) In[q][i] = 0.f;
+        for (int p = 0; p < G / 2; ++p) In[q][p] = make_float2(0.f, 0.f);
     // far sources: every pair outside its kernel support, Newtonian only
     for (int q0 = nclose; q0 < ns; q0 += 32) {
         const int j = q0 + lane;
         // padding lanes: a massless source far away (finite r, zero contribution)
         const float4 b = j < ns ? sm.src[sm.perm[j]] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        const float2 nbx = make_float2(-b.x, -b.x), nby = make_float2(-b.y, -b.y), nbz = make_float2(-b.z, -b.z);
+        const float2 nbm = make_float2(-b.w, -b.w);
 #pragma unroll
-        for (int i = 0; i < G; ++i) {
-            const float4 sa = sm.snk[i];
-            const float dx = sa.x - b.x, dy = sa.y - b.y, dz = sa.z - b.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-            const float w = b.w * (rinv * rinv * rinv);
-            In[0][i] = fmaf(-w, dx, In[0][i]);
-            In[1][i] = fmaf(-w, dy, In[1][i]);
-            In[2][i] = fmaf(-w, dz, In[2][i]);
-            In[3][i] = fmaf(-b.w, rinv, In[3][i]);
+        for (int p = 0; p < G / 2; ++p) {
+            const float4 sxy = sm.snk2[2 * p], szh = sm.snk2[2 * p + 1];
+            const float2 dx = __fadd2_rn(make_float2(sxy.x, sxy.y), nbx);
+            const float2 dy = __fadd2_rn(make_float2(sxy.z, sxy.w), nby);
+            const float2 dz = __fadd2_rn(make_float2(szh.x, szh.y), nbz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 rinv = make_float2(rsqrtf(fmaxf(r2.x, 1e-30f)), rsqrtf(fmaxf(r2.y, 1e-30f)));
+            const float2 nw = __fmul2_rn(nbm, __fmul2_rn(__fmul2_rn(rinv, rinv), rinv));  // -m_b / r^3
+            In[0][p] = __ffma2_rn(nw, dx, In[0][p]);
+            In[1][p] = __ffma2_rn(nw, dy, In[1][p]);
+            In[2][p] = __ffma2_rn(nw, dz, In[2][p]);
+            In[3][p] = __ffma2_rn(nbm, rinv, In[3][p]);
         }
     }
     // close sources: the full kernel-softened pair
+    const float2 k05 = make_float2(0.5f, 0.5f), km12 = make_float2(-1.2f, -1.2f), k43 = make_float2(4.0f / 3.0f, 4.0f / 3.0f);
+    const float2 k01 = make_float2(0.1f, 0.1f), km03 = make_float2(-0.3f, -0.3f), k23 = make_float2(2.0f / 3.0f, 2.0f / 3.0f);
+    const float2 km14 = make_float2(-1.4f, -1.4f), km16 = make_float2(-1.0f / 6.0f, -1.0f / 6.0f);
+    const float2 k12 = make_float2(1.2f, 1.2f), km3 = make_float2(-3.0f, -3.0f), k83 = make_float2(8.0f / 3.0f, 8.0f / 3.0f);
+    const float2 km115 = make_float2(-1.0f / 15.0f, -1.0f / 15.0f), km130 = make_float2(-1.0f / 30.0f, -1.0f / 30.0f);
+    const float2 k03 = make_float2(0.3f, 0.3f), km1 = make_float2(-1.0f, -1.0f), km16b = make_float2(-1.6f, -1.6f);
+    const float2 k115 = make_float2(1.0f / 15.0f, 1.0f / 15.0f);
     for (int q0 = 0; q0 < nclose; q0 += 32) {
         const int j = q0 + lane;
         float4 b = make_float4(1e18f, 1e18f, 1e18f, 0.f);
@@ -429,38 +448,47 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, int ns, 
         const unsigned cand = NB ? __ballot_sync(0xffffffffu, sb >= 0) : 0u;  // candidate-cell sources
         const bool own = NB && __any_sync(0xffffffffu, sb >= g.a0 && sb < g.a0 + G);
         unsigned pend = 0;  // sink particles with a possible neighbour in this chunk
+        const float2 nbx = make_float2(-b.x, -b.x), nby = make_float2(-b.y, -b.y), nbz = make_float2(-b.z, -b.z);
+        const float2 bm = make_float2(b.w, b.w), nbm = make_float2(-b.w, -b.w), hb2 = make_float2(hb, hb);
 #pragma unroll
-        for (int i = 0; i < G; ++i) {
-            // one branch-free pair (the self pair has r = 0: zero force; its
-            // potential m_a phi(0) is removed in the epilogue)
-            const float4 sa = sm.snk[i];
-            const float dx = sa.x - b.x, dy = sa.y - b.y, dz = sa.z - b.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-            const float r = r2 * rinv;
-            const float hinv = __fdividef(2.0f, sa.w + hb);
-            const float q = r * hinv;
-            const float q2 = q * q;
-            const float rinv3 = rinv * rinv * rinv;
+        for (int p = 0; p < G / 2; ++p) {
+            // sink particles 2p and 2p + 1 against this lane's source (the self pair has r = 0:
+            // zero force; its potential m_a phi(0) is removed in the epilogue)
+            const float4 sxy = sm.snk2[2 * p], szh = sm.snk2[2 * p + 1];
+            const float2 dx = __fadd2_rn(make_float2(sxy.x, sxy.y), nbx);
+            const float2 dy = __fadd2_rn(make_float2(sxy.z, sxy.w), nby);
+            const float2 dz = __fadd2_rn(make_float2(szh.x, szh.y), nbz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 rinv = make_float2(rsqrtf(fmaxf(r2.x, 1e-30f)), rsqrtf(fmaxf(r2.y, 1e-30f)));
+            const float2 r = __fmul2_rn(r2, rinv);
+            const float2 hsum = __fadd2_rn(make_float2(szh.z, szh.w), hb2);
+            const float2 hinv = make_float2(__fdividef(2.0f, hsum.x), __fdividef(2.0f, hsum.y));
+            const float2 q = __fmul2_rn(r, hinv);
+            const float2 q2 = __fmul2_rn(q, q);
+            const float2 rinv3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
             // Eq. 10 as S/r and its potential: q < 1, 1 <= q < 2, q >= 2
-            const float h3 = hinv * hinv * hinv;
-            const float s1 = h3 * fmaf(q2, fmaf(0.5f, q, -1.2f), 4.0f / 3.0f);
-            const float p1 = hinv * fmaf(q2, fmaf(q2, fmaf(0.1f, q, -0.3f), 2.0f / 3.0f), -1.4f);
-            const float s2v = fmaf(h3, fmaf(q, fmaf(q, fmaf(-1.0f / 6.0f, q, 1.2f), -3.0f), 8.0f / 3.0f),
-                                   -(1.0f / 15.0f) * rinv3);
-            const float p2v = fmaf(hinv,
-                                   fmaf(q2, fmaf(q, fmaf(q, fmaf(-1.0f / 30.0f, q, 0.3f), -1.0f), 4.0f / 3.0f), -1.6f),
-                                   (1.0f / 15.0f) * rinv);
-            const float sr = q < 1.0f ? s1 : (q < 2.0f ? s2v : rinv3);
-            const float ph = q < 1.0f ? p1 : (q < 2.0f ? p2v : -rinv);
-            const float w = b.w * sr;
-            In[0][i] = fmaf(-w, dx, In[0][i]);
-            In[1][i] = fmaf(-w, dy, In[1][i]);
-            In[2][i] = fmaf(-w, dz, In[2][i]);
-            In[3][i] = fmaf(b.w, ph, In[3][i]);
+            const float2 h3 = __fmul2_rn(__fmul2_rn(hinv, hinv), hinv);
+            const float2 s1 = __fmul2_rn(h3, __ffma2_rn(q2, __ffma2_rn(k05, q, km12), k43));
+            const float2 p1 = __fmul2_rn(hinv, __ffma2_rn(q2, __ffma2_rn(q2, __ffma2_rn(k01, q, km03), k23), km14));
+            const float2 s2v = __ffma2_rn(h3, __ffma2_rn(q, __ffma2_rn(q, __ffma2_rn(km16, q, k12), km3), k83),
+                                          __fmul2_rn(km115, rinv3));
+            const float2 p2v =
+                __ffma2_rn(hinv, __ffma2_rn(q2, __ffma2_rn(q, __ffma2_rn(q, __ffma2_rn(km130, q, k03), km1), k43), km16b),
+                           __fmul2_rn(k115, rinv));
+            const float2 sr = make_float2(q.x < 1.0f ? s1.x : (q.x < 2.0f ? s2v.x : rinv3.x),
+                                          q.y < 1.0f ? s1.y : (q.y < 2.0f ? s2v.y : rinv3.y));
+            const float2 ph = make_float2(q.x < 1.0f ? p1.x : (q.x < 2.0f ? p2v.x : -rinv.x),
+                                          q.y < 1.0f ? p1.y : (q.y < 2.0f ? p2v.y : -rinv.y));
+            const float2 nw = __fmul2_rn(nbm, sr);
+            In[0][p] = __ffma2_rn(nw, dx, In[0][p]);
+            In[1][p] = __ffma2_rn(nw, dy, In[1][p]);
+            In[2][p] = __ffma2_rn(nw, dz, In[2][p]);
+            In[3][p] = __ffma2_rn(bm, ph, In[3][p]);
             if (NB) {
-                // upper bound only here; the rest of the test runs out of the unrolled loop
-                if (__ballot_sync(0xffffffffu, r2 <= sm.band[i].y) & cand) pend |= 1u << i;
+                // upper band edge only here; the rest of the test runs out of the unrolled loop
+                const float2 hi = sm.hi2[p];
+                if (__ballot_sync(0xffffffffu, r2.x <= hi.x) & cand) pend |= 1u << (2 * p);
+                if (__ballot_sync(0xffffffffu, r2.y <= hi.y) & cand) pend |= 2u << (2 * p);
             }
         }
         if (NB) {
@@ -477,7 +505,7 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, int ns, 
     for (int i = 0; i < G; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            Vs[4 * i + q] = In[q][i];
+            Vs[4 * i + q] = (i & 1) ? In[q][i / 2].y : In[q][i / 2].x;
             Vc[4 * i + q] = 0.f;
         }
     reduce_scatter_df<4 * G>(Vs, Vc);
@@ -532,6 +560,11 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
                 const float4 pa = c.p32[fA + a0 + i];
                 sm.snk[lane] = make_float4(pa.x, pa.y, pa.z, c.h32[fA + a0 + i]);
             }
+            __syncwarp();
+            if (lane < kGroupMixed) {
+                const float4 u = sm.snk[lane & ~1], v = sm.snk[lane | 1];
+                sm.snk2[lane] = (lane & 1) ? make_float4(u.z, v.z, u.w, v.w) : make_float4(u.x, v.x, u.y, v.y);
+            }
             if (NB) {
                 g.a0 = fA + a0;
                 g.run = 0;
@@ -562,6 +595,8 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
                         }
                         sm.band[lane] = bd;
                     }
+                    __syncwarp();
+                    if (lane < kGroupMixed / 2) sm.hi2[lane] = make_float2(sm.band[2 * lane].y, sm.band[2 * lane + 1].y);
                     __syncwarp();
                 }
                 near_tile<kGroupMixed, NB>(c, sm, ns, nclose, rs, rc, g);
