@@ -240,29 +240,61 @@ struct NearSmem {
     }
 };
 
-// Stage sources [t0, t0 + kNearTile) of the sink's near cells: lanes first describe 32 cells
-// (first particle, count, centre-of-mass offset), then take one slot each, find its cell and
-// copy the particle: float32 offset from the sink's centre of mass, mass, h.  The cell offset is
-// the double-float difference of the two centres of mass; with NB it is the float64 difference
-// rounded once (the neighbour bound below is derived for that), the sorted index is kept and
-// wmax gets the tile's largest |dCOM|_1 + |d_b|_1.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Staged tile: sources [0, ns) of src/hs (and sidx); perm[0, nclose) lists the close sources,
+// perm[kNearTile - nfar, kNearTile) the far ones (see below).
+struct NearTile {
+    int ns, nclose, nfar;
+    int64_t S;  // all sources of the sink
+};
+
+// Stage sources [t0, t0 + kNearTile) of the sink's near cells.  For 32 cells at a time, lanes
+// first describe the cells (first particle, count, centre-of-mass offset), then take one slot
+// each, find its cell and start an asynchronous copy of the particle's float32 record and h into
+// shared memory; after one wait, a second pass adds the cell offset (float32 offset from the
+// sink's centre of mass) and classifies the source.  The cell offset is the double-float
+// difference of the two centres of mass; with NB it is the float64 difference rounded once (the
+// neighbour bound is derived for that), the sorted index is kept (bitwise complement for
+// sources of non-candidate cells) and wmax gets the tile's largest |dCOM|_1 + |d_b|_1.
+//
+// Classification: with R_A the largest |d_a| and H_A the largest h_a of the sink's particles,
+// a source b with |d_b| > (R_A + X_b)(1 + 2^-10) has r_ab >= |d_b| - |d_a| > X_b for every sink
+// particle a.  X_b = H_A + h_b puts all its pairs on the Newtonian branch of Eq. 10 (q >= 2);
+// with NB, X_b = max(H_A + h_b, 2 H_A) also keeps it out of every sink particle's neighbour
+// sphere (r < 2 h_a).  The 2^-10 margin is far above the float32 rounding of the test, of q and
+// of the neighbour filter.  Such sources fill perm from the back, the others from the front.
 template <bool NB>
-__device__ int stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, int64_t t0, const NearSmem<NB> &sm,
-                                float &wmax) {
+__device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, int64_t t0, const NearSmem<NB> &sm,
+                                     float RA, float HA, float &wmax) {
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)s * c.cap_near;
     const float2 a0 = c.ncomdf[3 * (int64_t)A], a1 = c.ncomdf[3 * (int64_t)A + 1], a2 = c.ncomdf[3 * (int64_t)A + 2];
     const double cAx = c.ncom[3 * (int64_t)A], cAy = c.ncom[3 * (int64_t)A + 1], cAz = c.ncom[3 * (int64_t)A + 2];
     int64_t pos = 0;
     float wl = 0.f;
-    for (int k0 = 0; k0 < nlist && pos < t0 + kNearTile; k0 += 32) {
+    int nclose = 0, nfar = 0;
+    for (int k0 = 0; k0 < nlist; k0 += 32) {
         const int k = k0 + lane;
         int f = 0, n = 0;
         float ox = 0.f, oy = 0.f, oz = 0.f;
+        const bool inside = pos < t0 + kNearTile;  // cells beyond the tile are only counted
         if (k < nlist) {
             const int B = near_entry(c, base, nr, k);
-            f = c.nfirst[B];
             n = c.ncount[B];
+        }
+        if (k < nlist && inside) {
+            const int B = near_entry(c, base, nr, k);
+            f = c.nfirst[B];
             if (NB) {
                 ox = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B], cAx));
                 oy = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B + 1], cAy));
@@ -279,23 +311,45 @@ __device__ int stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, 
         const int total = __shfl_sync(0xffffffffu, excl + n, 31);
         const int64_t lo = pos > t0 ? pos : t0;
         const int64_t hi = pos + total < t0 + kNearTile ? pos + total : t0 + kNearTile;
+        // copies in flight for every slot of these cells
         for (int64_t j0 = lo; j0 < hi; j0 += 32) {
             const int64_t j = j0 + lane;
             const int rel = (int)(j - pos);
-            const int cl = warp_find_slot(excl, rel);
+            const int cl = warp_run_of(excl, n, (int)(j0 - pos));
             const int fc = __shfl_sync(0xffffffffu, f, cl), ec = __shfl_sync(0xffffffffu, excl, cl);
-            const float cx = __shfl_sync(0xffffffffu, ox, cl), cy = __shfl_sync(0xffffffffu, oy, cl),
-                        cz = __shfl_sync(0xffffffffu, oz, cl);
             if (j < hi) {
                 const int b = fc + rel - ec;
-                const float4 pb = c.p32[b];
-                sm.src[j - t0] = make_float4(cx + pb.x, cy + pb.y, cz + pb.z, pb.w);
-                sm.hs[j - t0] = c.h32[b];
-                if (NB) {
-                    sm.sidx[j - t0] = k0 + cl < nr ? b : ~b;
-                    wl = fmaxf(wl, (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
-                }
+                cp_async16(&sm.src[j - t0], &c.p32[b]);
+                cp_async4(&sm.hs[j - t0], &c.h32[b]);
+                if (NB) sm.sidx[j - t0] = k0 + cl < nr ? b : ~b;
             }
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        // cell offsets and classification
+        for (int64_t j0 = lo; j0 < hi; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const int cl = warp_run_of(excl, n, (int)(j0 - pos));
+            const float cx = __shfl_sync(0xffffffffu, ox, cl), cy = __shfl_sync(0xffffffffu, oy, cl),
+                        cz = __shfl_sync(0xffffffffu, oz, cl);
+            const bool act = j < hi;
+            bool far = false;
+            if (act) {
+                const float4 pb = sm.src[j - t0];
+                const float4 v = make_float4(cx + pb.x, cy + pb.y, cz + pb.z, pb.w);
+                sm.src[j - t0] = v;
+                if (NB) wl = fmaxf(wl, (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
+                const float hb = sm.hs[j - t0];
+                const float d2 = fmaf(v.z, v.z, fmaf(v.y, v.y, v.x * v.x));
+                const float X = NB ? fmaxf(HA + hb, HA + HA) : HA + hb;
+                const float R = (RA + X) * (1.0f + 0x1p-10f);
+                far = d2 > R * R;
+            }
+            const unsigned mc = __ballot_sync(0xffffffffu, act && !far), mf = __ballot_sync(0xffffffffu, act && far);
+            if (act)
+                sm.perm[far ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt)] = (uint16_t)(j - t0);
+            nclose += __popc(mc);
+            nfar += __popc(mf);
         }
         pos += total;
     }
@@ -305,46 +359,7 @@ __device__ int stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, 
     }
     __syncwarp();
     const int64_t left = pos - t0;
-    return (int)(left < kNearTile ? left : kNearTile);
-}
-
-// Order the staged sources for the two pair loops.  With R_A the largest |d_a| and H_A the
-// largest h_a of the sink's particles, a source b with |d_b| > (R_A + X_b)(1 + 2^-10) has
-// r_ab >= |d_b| - |d_a| > X_b for every sink particle a.  X_b = H_A + h_b puts all its pairs on
-// the Newtonian branch of Eq. 10 (q >= 2); with the neighbour search X_b = max(H_A + h_b, 2 H_A)
-// also keeps it out of every sink particle's neighbour sphere (r < 2 h_a).  The 2^-10 margin is
-// far above the float32 rounding of the test, of q and of the neighbour filter.  perm[0, nclose)
-// lists the other sources, perm[nclose, ns) these.
-template <bool NB>
-__device__ int partition_near(const NearSmem<NB> &sm, int ns, float RA, float HA) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int nclose = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        int pc = 0, pf = nclose;
-        for (int q0 = 0; q0 < ns; q0 += 32) {
-            const int j = q0 + lane;
-            bool far = false;
-            if (j < ns) {
-                const float4 v = sm.src[j];
-                const float d2 = fmaf(v.z, v.z, fmaf(v.y, v.y, v.x * v.x));
-                const float hb = sm.hs[j];
-                const float X = NB ? fmaxf(HA + hb, HA + HA) : HA + hb;
-                const float R = (RA + X) * (1.0f + 0x1p-10f);
-                far = d2 > R * R;
-            }
-            const unsigned mc = __ballot_sync(0xffffffffu, j < ns && !far);
-            if (pass == 1) {
-                const unsigned mf = __ballot_sync(0xffffffffu, j < ns && far);
-                if (j < ns) sm.perm[far ? pf + __popc(mf & lt) : pc + __popc(mc & lt)] = (uint16_t)j;
-                pf += __popc(mf);
-            }
-            pc += __popc(mc);
-        }
-        nclose = pc;
-    }
-    __syncwarp();
-    return nclose;
+    return NearTile{(int)(left < kNearTile ? left : kNearTile), nclose, nfar, pos};
 }
 
 // Neighbour-search state of one group of sink particles.
@@ -392,8 +407,9 @@ __device__ __forceinline__ void near_neighbours_of(const GCtx &c, const NearSmem
 // tests every candidate pair (a, b) for |r_a - r_b| < 2 h_a: float32 d^2 against the band of
 // sink particle i, float64 inside it, and appends b's original index to a's row of slots.
 template <int G, bool NB>
-__device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, int ns, int nclose, float &rs, float &rc,
+__device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const NearTile &tl, float &rs, float &rc,
                                  NbGroup &g) {
+    const int nclose = tl.nclose;
     static_assert(G % 2 == 0, "sink particles go by pairs");
     const int lane = threadIdx.x & 31;
     // In[q][p]: quantity q (a_x, a_y, a_z, phi) of sink particles 2p and 2p + 1.  Every pair
@@ -405,10 +421,10 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, int ns, 
 #pragma unroll
         for (int p = 0; p < G / 2; ++p) In[q][p] = make_float2(0.f, 0.f);
     // far sources: every pair outside its kernel support, Newtonian only
-    for (int q0 = nclose; q0 < ns; q0 += 32) {
+    for (int q0 = kNearTile - tl.nfar; q0 < kNearTile; q0 += 32) {
         const int j = q0 + lane;
         // padding lanes: a massless source far away (finite r, zero contribution)
-        const float4 b = j < ns ? sm.src[sm.perm[j]] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        const float4 b = j < kNearTile ? sm.src[sm.perm[j]] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
         const float2 nbx = make_float2(-b.x, -b.x), nby = make_float2(-b.y, -b.y), nbz = make_float2(-b.z, -b.z);
         const float2 nbm = make_float2(-b.w, -b.w);
 #pragma unroll
@@ -531,10 +547,6 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
         const int A = c.sinks[s];
         const int fA = c.nfirst[A], nA = c.ncount[A];
         const int nr = c.near_nr[s], nlist = nr + c.near_nn[s];
-        const int64_t base = (int64_t)s * c.cap_near;
-        int64_t S = 0;
-        for (int k = lane; k < nlist; k += 32) S += c.ncount[near_entry(c, base, nr, k)];
-        for (int o = 16; o >= 1; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
         // R_A and H_A of the sink cell (float32 offsets from its centre of mass)
         float RA, HA;
         {
@@ -551,7 +563,7 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             RA = sqrtf(R2) * (1.0f + 0x1p-10f);
             HA = H;
         }
-        int once_ns = -1, once_nc = 0;  // staged tile when all sources fit one tile
+        NearTile once{-1, 0, 0, 0};  // staged tile when all sources fit one tile
         float wmax = 0.f;
         for (int a0 = 0; a0 < nA; a0 += kGroupMixed) {
             const int na = min(kGroupMixed, nA - a0);
@@ -571,15 +583,11 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             }
             __syncwarp();
             float rs = 0.f, rc = 0.f;  // compensated total of value lane mod 4 G (= 4 i + q)
-            for (int64_t t0 = 0; t0 < S; t0 += kNearTile) {
-                int ns = once_ns, nclose = once_nc;
-                if (ns < 0) {
-                    ns = stage_near_mixed<NB>(c, s, A, nlist, nr, t0, sm, wmax);
-                    nclose = partition_near<NB>(sm, ns, RA, HA);
-                    if (S <= kNearTile) {
-                        once_ns = ns;
-                        once_nc = nclose;
-                    }
+            for (int64_t t0 = 0;; t0 += kNearTile) {
+                NearTile tl = once;
+                if (tl.ns < 0) {
+                    tl = stage_near_mixed<NB>(c, s, A, nlist, nr, t0, sm, RA, HA, wmax);
+                    if (tl.S <= kNearTile) once = tl;
                 }
                 if (NB) {
                     // neighbour band of each sink particle for this tile (-1: padding slot)
@@ -599,8 +607,9 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
                     if (lane < kGroupMixed / 2) sm.hi2[lane] = make_float2(sm.band[2 * lane].y, sm.band[2 * lane + 1].y);
                     __syncwarp();
                 }
-                near_tile<kGroupMixed, NB>(c, sm, ns, nclose, rs, rc, g);
+                near_tile<kGroupMixed, NB>(c, sm, tl, rs, rc, g);
                 __syncwarp();
+                if (t0 + kNearTile >= tl.S) break;
             }
             const double tot = __dadd_rn((double)rs, (double)rc);  // lane l < 4 na: particle l/4, quantity l%4
             const double q0v = __shfl_sync(0xffffffffu, tot, (4 * lane) & 31);

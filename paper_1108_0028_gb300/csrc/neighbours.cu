@@ -120,7 +120,7 @@ __device__ int stage_tile(const NbCtx &c, int s, int A, int nr, int64_t t0, floa
         for (int64_t j0 = lo; j0 < hi; j0 += 32) {
             const int64_t j = j0 + lane;
             const int rel = (int)(j - pos);
-            const int cl = warp_find_slot(excl, rel);
+            const int cl = warp_run_of(excl, n, (int)(j0 - pos));
             const int fc = __shfl_sync(kFull, f, cl), ec = __shfl_sync(kFull, excl, cl);
             const float cx = __shfl_sync(kFull, dx, cl), cy = __shfl_sync(kFull, dy, cl), cz = __shfl_sync(kFull, dz, cl);
             if (j < hi) {

@@ -162,17 +162,15 @@ __device__ inline int warp_excl_scan(int v) {
     return incl - v;
 }
 
-// With first[k] (held by lane k) non-decreasing and first[0] = 0 <= rel: the largest k with
-// first[k] <= rel, i.e. the run that holds position rel (empty runs are skipped).
-__device__ inline int warp_find_slot(int first, int rel) {
-    int k = 0;
-#pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
-        const int cand = k + step;
-        const int v = __shfl_sync(0xffffffffu, first, cand & 31);
-        if (cand < 32 && v <= rel) k = cand;
-    }
-    return k;
+// Runs of positive length n_k (lane k) laid end to end from first[k] (exclusive prefix sums),
+// lanes with n_k = 0 after the last run: the run holding position r0 + lane.  One OR-reduction
+// marks the runs that start inside [r0, r0 + 32); a popcount does the rest.
+__device__ inline int warp_run_of(int first, int n, int r0) {
+    const int lane = threadIdx.x & 31;
+    const int st = first - r0;
+    const unsigned starts = __reduce_or_sync(0xffffffffu, (n > 0 && st >= 0 && st < 32) ? (1u << st) : 0u);
+    const int before = __popc(__ballot_sync(0xffffffffu, n > 0 && st < 0));
+    return before + __popc(starts & ((2u << lane) - 1u)) - 1;
 }
 
 __device__ inline void two_sum(float a, float b, float &s, float &e) {
