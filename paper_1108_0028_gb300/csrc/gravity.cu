@@ -311,45 +311,60 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
         const int total = __shfl_sync(0xffffffffu, excl + n, 31);
         const int64_t lo = pos > t0 ? pos : t0;
         const int64_t hi = pos + total < t0 + kNearTile ? pos + total : t0 + kNearTile;
-        // copies in flight for every slot of these cells
-        for (int64_t j0 = lo; j0 < hi; j0 += 32) {
-            const int64_t j = j0 + lane;
-            const int rel = (int)(j - pos);
-            const int cl = warp_run_of(excl, n, (int)(j0 - pos));
-            const int fc = __shfl_sync(0xffffffffu, f, cl), ec = __shfl_sync(0xffffffffu, excl, cl);
-            if (j < hi) {
-                const int b = fc + rel - ec;
-                cp_async16(&sm.src[j - t0], &c.p32[b]);
-                cp_async4(&sm.hs[j - t0], &c.h32[b]);
-                if (NB) sm.sidx[j - t0] = k0 + cl < nr ? b : ~b;
+        // copies in flight for every slot of these cells (two slot chunks per round)
+        for (int64_t j0 = lo; j0 < hi; j0 += 64) {
+            int cl[2], b[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int rel = (int)(j0 + 32 * u + lane - pos);
+                cl[u] = warp_run_of(excl, n, (int)(j0 + 32 * u - pos));
+                b[u] = __shfl_sync(0xffffffffu, f, cl[u]) + rel - __shfl_sync(0xffffffffu, excl, cl[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t j = j0 + 32 * u + lane;
+                if (j < hi) {
+                    cp_async16(&sm.src[j - t0], &c.p32[b[u]]);
+                    cp_async4(&sm.hs[j - t0], &c.h32[b[u]]);
+                    if (NB) sm.sidx[j - t0] = k0 + cl[u] < nr ? b[u] : ~b[u];
+                }
             }
         }
         cp_async_wait_all();
         __syncwarp();
         // cell offsets and classification
-        for (int64_t j0 = lo; j0 < hi; j0 += 32) {
-            const int64_t j = j0 + lane;
-            const int cl = warp_run_of(excl, n, (int)(j0 - pos));
-            const float cx = __shfl_sync(0xffffffffu, ox, cl), cy = __shfl_sync(0xffffffffu, oy, cl),
-                        cz = __shfl_sync(0xffffffffu, oz, cl);
-            const bool act = j < hi;
-            bool far = false;
-            if (act) {
-                const float4 pb = sm.src[j - t0];
-                const float4 v = make_float4(cx + pb.x, cy + pb.y, cz + pb.z, pb.w);
-                sm.src[j - t0] = v;
-                if (NB) wl = fmaxf(wl, (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
-                const float hb = sm.hs[j - t0];
-                const float d2 = fmaf(v.z, v.z, fmaf(v.y, v.y, v.x * v.x));
-                const float X = NB ? fmaxf(HA + hb, HA + HA) : HA + hb;
-                const float R = (RA + X) * (1.0f + 0x1p-10f);
-                far = d2 > R * R;
+        for (int64_t j0 = lo; j0 < hi; j0 += 64) {
+            bool act[2], far[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t j = j0 + 32 * u + lane;
+                const int cl = warp_run_of(excl, n, (int)(j0 + 32 * u - pos));
+                const float cx = __shfl_sync(0xffffffffu, ox, cl), cy = __shfl_sync(0xffffffffu, oy, cl),
+                            cz = __shfl_sync(0xffffffffu, oz, cl);
+                act[u] = j < hi;
+                far[u] = false;
+                if (act[u]) {
+                    const float4 pb = sm.src[j - t0];
+                    const float4 v = make_float4(cx + pb.x, cy + pb.y, cz + pb.z, pb.w);
+                    sm.src[j - t0] = v;
+                    if (NB) wl = fmaxf(wl, (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
+                    const float hb = sm.hs[j - t0];
+                    const float d2 = fmaf(v.z, v.z, fmaf(v.y, v.y, v.x * v.x));
+                    const float X = NB ? fmaxf(HA + hb, HA + HA) : HA + hb;
+                    const float R = (RA + X) * (1.0f + 0x1p-10f);
+                    far[u] = d2 > R * R;
+                }
             }
-            const unsigned mc = __ballot_sync(0xffffffffu, act && !far), mf = __ballot_sync(0xffffffffu, act && far);
-            if (act)
-                sm.perm[far ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt)] = (uint16_t)(j - t0);
-            nclose += __popc(mc);
-            nfar += __popc(mf);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const unsigned mc = __ballot_sync(0xffffffffu, act[u] && !far[u]);
+                const unsigned mf = __ballot_sync(0xffffffffu, act[u] && far[u]);
+                if (act[u])
+                    sm.perm[far[u] ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt)] =
+                        (uint16_t)(j0 + 32 * u + lane - t0);
+                nclose += __popc(mc);
+                nfar += __popc(mf);
+            }
         }
         pos += total;
     }
