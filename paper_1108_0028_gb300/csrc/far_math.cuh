@@ -68,6 +68,62 @@ __device__ inline void far_source(const T x[3], T M, const T Q6[6], T C[20]) {
     C[19] += c3_slot(c, b, f7, f9, x2, x2, x2, Qzz, Qzz, Qzz, v2, v2, v2, t3 * x2, t3 * v2);
 }
 
+// far_source for two far sources at once, (.x, .y) halves, with paired float32 instructions;
+// the products are grouped as in far_source and every accumulation is a fused multiply-add
+// into C.
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float2 c3_slot2(float2 C, float2 cx, float2 b, float2 f7, float2 nf9, float2 xi, float2 xj,
+                                           float2 xk, float2 Qij, float2 Qik, float2 Qjk, float2 vi, float2 vj,
+                                           float2 vk, float2 dsum, float2 vsum) {
+    // c x_i x_j x_k + f7 (Q_ij x_k + Q_ik x_j + Q_jk x_i + vsum) - f9 (v_i x_j x_k + v_j x_i x_k + v_k x_i x_j)
+    // + b dsum, with cx = c x_i
+    const float2 xjk = __fmul2_rn(xj, xk);
+    const float2 t = __ffma2_rn(Qjk, xi, __ffma2_rn(Qik, xj, __fmul2_rn(Qij, xk)));
+    const float2 u = __ffma2_rn(vk, __fmul2_rn(xi, xj), __ffma2_rn(vj, __fmul2_rn(xi, xk), __fmul2_rn(vi, xjk)));
+    return __ffma2_rn(cx, xjk, __ffma2_rn(f7, __fadd2_rn(t, vsum), __ffma2_rn(nf9, u, __ffma2_rn(b, dsum, C))));
+}
+
+__device__ inline void far_source2(float2 x0, float2 x1, float2 x2, float2 M, float2 Qxx, float2 Qxy, float2 Qxz,
+                                   float2 Qyy, float2 Qyz, float2 Qzz, float2 C[20]) {
+    const float2 r2 = __ffma2_rn(x2, x2, __ffma2_rn(x1, x1, __fmul2_rn(x0, x0)));
+    const float2 g = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 g2 = __fmul2_rn(g, g), g3 = __fmul2_rn(g, g2), g5 = __fmul2_rn(g3, g2), g7 = __fmul2_rn(g5, g2);
+    const float2 g9 = __fmul2_rn(g7, g2), g11 = __fmul2_rn(g9, g2);
+    const float2 v0 = __ffma2_rn(Qxz, x2, __ffma2_rn(Qxy, x1, __fmul2_rn(Qxx, x0)));
+    const float2 v1 = __ffma2_rn(Qyz, x2, __ffma2_rn(Qyy, x1, __fmul2_rn(Qxy, x0)));
+    const float2 v2 = __ffma2_rn(Qzz, x2, __ffma2_rn(Qyz, x1, __fmul2_rn(Qxz, x0)));
+    const float2 s = __ffma2_rn(x2, v2, __ffma2_rn(x1, v1, __fmul2_rn(x0, v0)));
+    const float2 a = __ffma2_rn(M, g3, __fmul2_rn(f2s(2.5f), __fmul2_rn(s, g7)));
+    const float2 b = __ffma2_rn(__fmul2_rn(f2s(-3.0f), M), g5, __fmul2_rn(f2s(-17.5f), __fmul2_rn(s, g9)));
+    const float2 c = __ffma2_rn(__fmul2_rn(f2s(15.0f), M), g7, __fmul2_rn(f2s(157.5f), __fmul2_rn(s, g11)));
+    const float2 f7 = __fmul2_rn(f2s(5.0f), g7), nf9 = __fmul2_rn(f2s(-35.0f), g9);
+    const float2 ng5 = f2neg(g5), two = f2s(2.0f), three = f2s(3.0f), zero = f2s(0.0f);
+    C[0] = __ffma2_rn(f2neg(M), g, __ffma2_rn(f2s(-0.5f), __fmul2_rn(s, g5), C[0]));
+    C[1] = __ffma2_rn(a, x0, __ffma2_rn(ng5, v0, C[1]));
+    C[2] = __ffma2_rn(a, x1, __ffma2_rn(ng5, v1, C[2]));
+    C[3] = __ffma2_rn(a, x2, __ffma2_rn(ng5, v2, C[3]));
+    const float2 bx0 = __fmul2_rn(b, x0), bx1 = __fmul2_rn(b, x1), bx2 = __fmul2_rn(b, x2);
+    C[4] = __ffma2_rn(bx0, x0, __ffma2_rn(ng5, Qxx, __ffma2_rn(f7, __fmul2_rn(two, __fmul2_rn(v0, x0)), __fadd2_rn(a, C[4]))));
+    C[5] = __ffma2_rn(bx0, x1, __ffma2_rn(ng5, Qxy, __ffma2_rn(f7, __ffma2_rn(v0, x1, __fmul2_rn(v1, x0)), C[5])));
+    C[6] = __ffma2_rn(bx0, x2, __ffma2_rn(ng5, Qxz, __ffma2_rn(f7, __ffma2_rn(v0, x2, __fmul2_rn(v2, x0)), C[6])));
+    C[7] = __ffma2_rn(bx1, x1, __ffma2_rn(ng5, Qyy, __ffma2_rn(f7, __fmul2_rn(two, __fmul2_rn(v1, x1)), __fadd2_rn(a, C[7]))));
+    C[8] = __ffma2_rn(bx1, x2, __ffma2_rn(ng5, Qyz, __ffma2_rn(f7, __ffma2_rn(v1, x2, __fmul2_rn(v2, x1)), C[8])));
+    C[9] = __ffma2_rn(bx2, x2, __ffma2_rn(ng5, Qzz, __ffma2_rn(f7, __fmul2_rn(two, __fmul2_rn(v2, x2)), __fadd2_rn(a, C[9]))));
+    const float2 cx0 = __fmul2_rn(c, x0), cx1 = __fmul2_rn(c, x1), cx2 = __fmul2_rn(c, x2);
+    C[10] = c3_slot2(C[10], cx0, b, f7, nf9, x0, x0, x0, Qxx, Qxx, Qxx, v0, v0, v0, __fmul2_rn(three, x0), __fmul2_rn(three, v0));
+    C[11] = c3_slot2(C[11], cx0, b, f7, nf9, x0, x0, x1, Qxx, Qxy, Qxy, v0, v0, v1, x1, v1);
+    C[12] = c3_slot2(C[12], cx0, b, f7, nf9, x0, x0, x2, Qxx, Qxz, Qxz, v0, v0, v2, x2, v2);
+    C[13] = c3_slot2(C[13], cx0, b, f7, nf9, x0, x1, x1, Qxy, Qxy, Qyy, v0, v1, v1, x0, v0);
+    C[14] = c3_slot2(C[14], cx0, b, f7, nf9, x0, x1, x2, Qxy, Qxz, Qyz, v0, v1, v2, zero, zero);
+    C[15] = c3_slot2(C[15], cx0, b, f7, nf9, x0, x2, x2, Qxz, Qxz, Qzz, v0, v2, v2, x0, v0);
+    C[16] = c3_slot2(C[16], cx1, b, f7, nf9, x1, x1, x1, Qyy, Qyy, Qyy, v1, v1, v1, __fmul2_rn(three, x1), __fmul2_rn(three, v1));
+    C[17] = c3_slot2(C[17], cx1, b, f7, nf9, x1, x1, x2, Qyy, Qyz, Qyz, v1, v1, v2, x2, v2);
+    C[18] = c3_slot2(C[18], cx1, b, f7, nf9, x1, x2, x2, Qyz, Qyz, Qzz, v1, v2, v2, x1, v1);
+    C[19] = c3_slot2(C[19], cx2, b, f7, nf9, x2, x2, x2, Qzz, Qzz, Qzz, v2, v2, v2, __fmul2_rn(three, x2), __fmul2_rn(three, v2));
+}
+
 // Gradient and Hessian of the sink's third-order Taylor polynomial P at offset d (Eq. 6).
 template <typename T>
 __device__ inline void taylor_grad_hess(const T C[20], T d0, T d1, T d2, T g[3], T H[6]) {

@@ -75,37 +75,58 @@ __global__ void __launch_bounds__(kGWarps * 32) k_far(GCtx c) {
         const int nf = c.far_n[s];
         const int64_t fb = (int64_t)s * c.cap_far;
         if (MIXED) {
-            float C[32];
+            // two far nodes per lane and round (k and k + 32), paired float32 arithmetic
+            float2 C2[20];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) C[i] = 0.f;
+            for (int i = 0; i < 20; ++i) C2[i] = make_float2(0.f, 0.f);
             const float4 ah = c.nfar[4 * (int64_t)A], al = c.nfar[4 * (int64_t)A + 1];
-            // software pipeline: the records of the next far node are loaded before the current
-            // node's tensor arithmetic, so the gather latency overlaps the math
-            int k = lane;
-            float4 p0, p1, p2, p3;
-            if (k < nf) {
-                const float4 *r = c.nfar + 4 * (int64_t)c.far_list[fb + k];
-                p0 = r[0];
-                p1 = r[1];
-                p2 = r[2];
-                p3 = r[3];
-            }
-            while (k < nf) {
-                const float4 q0 = p0, q1 = p1, q2 = p2, q3 = p3;
-                const int kn = k + 32;
-                if (kn < nf) {
-                    const float4 *r = c.nfar + 4 * (int64_t)c.far_list[fb + kn];
-                    p0 = r[0];
-                    p1 = r[1];
-                    p2 = r[2];
-                    p3 = r[3];
+            float4 p[2][4];
+            auto fetch = [&](int k0) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int k = k0 + 32 * u;
+                    if (k < nf) {
+                        const float4 *r = c.nfar + 4 * (int64_t)c.far_list[fb + k];
+                        p[u][0] = r[0];
+                        p[u][1] = r[1];
+                        p[u][2] = r[2];
+                        p[u][3] = r[3];
+                    } else {
+                        // no node: zero mass and quadrupole (its offset is set to (1, 0, 0) below)
+                        p[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        p[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        p[u][2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        p[u][3] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                 }
-                const float x[3] = {(ah.x - q0.x) + (al.x - q1.x), (ah.y - q0.y) + (al.y - q1.y),
-                                    (ah.z - q0.z) + (al.z - q1.z)};
-                const float Q6[6] = {q1.w, q2.x, q2.y, q2.z, q2.w, q3.x};
-                far_source<float>(x, q0.w, Q6, C);
+            };
+            int k = lane;
+            while (k < nf) {
+                fetch(k);
+                float4 q[2][4];
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) q[u][e] = p[u][e];
+                const int kn = k + 64;
+                const bool second = k + 32 < nf;
+                const float2 x0 = make_float2((ah.x - q[0][0].x) + (al.x - q[0][1].x),
+                                              second ? (ah.x - q[1][0].x) + (al.x - q[1][1].x) : 1.f);
+                const float2 x1 = make_float2((ah.y - q[0][0].y) + (al.y - q[0][1].y),
+                                              second ? (ah.y - q[1][0].y) + (al.y - q[1][1].y) : 0.f);
+                const float2 x2 = make_float2((ah.z - q[0][0].z) + (al.z - q[0][1].z),
+                                              second ? (ah.z - q[1][0].z) + (al.z - q[1][1].z) : 0.f);
+                far_source2(x0, x1, x2, make_float2(q[0][0].w, q[1][0].w), make_float2(q[0][1].w, q[1][1].w),
+                            make_float2(q[0][2].x, q[1][2].x), make_float2(q[0][2].y, q[1][2].y),
+                            make_float2(q[0][2].z, q[1][2].z), make_float2(q[0][2].w, q[1][2].w),
+                            make_float2(q[0][3].x, q[1][3].x), C2);
                 k = kn;
             }
+            float C[32];
+#pragma unroll
+            for (int i = 0; i < 20; ++i) C[i] = C2[i].x + C2[i].y;
+#pragma unroll
+            for (int i = 20; i < 32; ++i) C[i] = 0.f;
             float E[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) E[i] = 0.f;
