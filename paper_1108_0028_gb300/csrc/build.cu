@@ -851,7 +851,7 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
 struct PackCtx {
     const int32_t *ncount;
     const double *nmass, *ncom, *nrg, *nH, *nhint, *nQ;
-    float4 *w32a, *w32b, *mq32a, *mq32b;
+    float4 *w32, *mq32a, *mq32b;
     float2 *ncomdf;
     float4 *nfar;
 };
@@ -859,17 +859,17 @@ struct PackCtx {
 __global__ void k_pack_nodes(PackCtx c, int64_t nn) {
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn; n += (int64_t)gridDim.x * blockDim.x) {
         if (n == 0 || c.ncount[n] == 0) {
-            c.w32a[n] = make_float4(0.f, 0.f, 0.f, -1.f);
-            c.w32b[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+            c.w32[2 * n] = make_float4(0.f, 0.f, 0.f, -1.f);
+            c.w32[2 * n + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
             c.mq32a[n] = make_float4(0.f, 0.f, 0.f, 0.f);
             c.mq32b[n] = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int d = 0; d < 3; ++d) c.ncomdf[3 * n + d] = make_float2(0.f, 0.f);
             for (int k = 0; k < 4; ++k) c.nfar[4 * n + k] = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
         }
-        c.w32a[n] = make_float4(__double2float_rn(c.nrg[3 * n]), __double2float_rn(c.nrg[3 * n + 1]),
+        c.w32[2 * n] = make_float4(__double2float_rn(c.nrg[3 * n]), __double2float_rn(c.nrg[3 * n + 1]),
                                 __double2float_rn(c.nrg[3 * n + 2]), __double2float_rn(c.nhint[n]));
-        c.w32b[n] = make_float4(__double2float_rn(c.ncom[3 * n]), __double2float_rn(c.ncom[3 * n + 1]),
+        c.w32[2 * n + 1] = make_float4(__double2float_rn(c.ncom[3 * n]), __double2float_rn(c.ncom[3 * n + 1]),
                                 __double2float_rn(c.ncom[3 * n + 2]), __double2float_rn(c.nH[n]));
         c.mq32a[n] = make_float4(__double2float_rn(c.nmass[n]), __double2float_rn(c.nQ[6 * n]),
                                  __double2float_rn(c.nQ[6 * n + 1]), __double2float_rn(c.nQ[6 * n + 2]));
@@ -1276,8 +1276,7 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
         pc.nH = t->nH;
         pc.nhint = t->nhint;
         pc.nQ = t->nQ;
-        pc.w32a = t->w32a;
-        pc.w32b = t->w32b;
+        pc.w32 = t->w32;
         pc.mq32a = t->mq32a;
         pc.mq32b = t->mq32b;
         pc.ncomdf = t->ncomdf;
@@ -1333,8 +1332,7 @@ int refit_tree(rcb_tree *t, const double *x, const double *m) {
     pc.nH = t->nH;
     pc.nhint = t->nhint;
     pc.nQ = t->nQ;
-    pc.w32a = t->w32a;
-    pc.w32b = t->w32b;
+    pc.w32 = t->w32;
     pc.mq32a = t->mq32a;
     pc.mq32b = t->mq32b;
     pc.ncomdf = t->ncomdf;

@@ -83,8 +83,8 @@ void for_each_array(rcb_tree *t, F f) {
                   (void **)&t->pidx, (void **)&t->p32, (void **)&t->h32, (void **)&t->nfirst, (void **)&t->ncount,
                   (void **)&t->naxis, (void **)&t->nsplit, (void **)&t->nsplitkey, (void **)&t->nS,
                   (void **)&t->nbmin, (void **)&t->nbmax, (void **)&t->nmass, (void **)&t->ncom, (void **)&t->nrg,
-                  (void **)&t->nH, (void **)&t->nhint, (void **)&t->nhnode, (void **)&t->nQ, (void **)&t->w32a,
-                  (void **)&t->w32b, (void **)&t->mq32a, (void **)&t->mq32b, (void **)&t->ncomdf, (void **)&t->nfar,
+                  (void **)&t->nH, (void **)&t->nhint, (void **)&t->nhnode, (void **)&t->nQ, (void **)&t->w32,
+                  (void **)&t->mq32a, (void **)&t->mq32b, (void **)&t->ncomdf, (void **)&t->nfar,
                   (void **)&t->narrive, (void **)&t->roots, (void **)&t->chunks, (void **)&t->cell_chunk0,
                   (void **)&t->chunk_part, (void **)&t->sinks, (void **)&t->sink_of_leaf, (void **)&t->near_nr,
                   (void **)&t->near_nn, (void **)&t->far_n, (void **)&t->near_list, (void **)&t->far_list,
@@ -152,8 +152,7 @@ int allocate_arrays(rcb_tree *t, int64_t N, int L) {
     A((void **)&t->nhint, nn * sizeof(double));
     A((void **)&t->nhnode, nn * sizeof(double));
     A((void **)&t->nQ, 6 * nn * sizeof(double));
-    A((void **)&t->w32a, nn * sizeof(float4));
-    A((void **)&t->w32b, nn * sizeof(float4));
+    A((void **)&t->w32, 2 * nn * sizeof(float4));
     A((void **)&t->mq32a, nn * sizeof(float4));
     A((void **)&t->mq32b, nn * sizeof(float4));
     A((void **)&t->ncomdf, 3 * nn * sizeof(float2));

@@ -230,7 +230,7 @@ struct rcb_tree {
     rcb::i128 *nS;          // [nn][4] exact sums
     int64_t *nbmin, *nbmax;  // [nn][3] keys of the tight box
     double *nmass, *ncom, *nrg, *nH, *nhint, *nhnode, *nQ;  // com, rg: [nn][3]; Q: [nn][6]
-    float4 *w32a, *w32b;     // walk packs: (rg, hint), (com, H) in float32
+    float4 *w32;  // walk packs, two per node: [2n] (rg, hint), [2n + 1] (com, H) in float32; hint = -1: empty
     float4 *mq32a, *mq32b;   // (M, Qxx, Qxy, Qxz), (Qyy, Qyz, Qzz, 0) in float32
     float2 *ncomdf;          // [nn][3] double-float centre of mass
     float4 *nfar;            // [nn][4] far-field record: (COM hi, M), (COM lo, Qxx), (Qxy, Qxz, Qyy, Qyz), (Qzz)

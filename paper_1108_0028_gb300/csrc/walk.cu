@@ -31,8 +31,7 @@ struct WalkCtx {
     int64_t nn;
     double theta2;
     float theta2f;
-    const int32_t *ncount;
-    const float4 *w32a, *w32b;
+    const float4 *w32;  // [2n] (r_g, h_int), [2n + 1] (COM, H); h_int = -1 marks an empty node
     const double *nrg, *nhint, *ncom, *nH, *nhnode;
     const int32_t *sinks;
     int nsinks;
@@ -51,7 +50,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
     bool limit = false;
     if (valid) {
         const int A = c.sinks[s];
-        const float4 a32 = c.w32a[A], b32 = c.w32b[A];
+        const float4 a32 = c.w32[2 * A], b32 = c.w32[2 * A + 1];
         const float3 rgA = make_float3(a32.x, a32.y, a32.z);
         const float3 comA = make_float3(b32.x, b32.y, b32.z);
         const float hA = __double2float_rn(c.nhnode[A]);
@@ -69,8 +68,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
                 break;
             }
             bool open = false;
-            if (c.ncount[n] > 0) {
-                const float4 na = c.w32a[n], nb = c.w32b[n];
+            const float4 na = c.w32[2 * n];
+            if (na.w >= 0.f) {  // non-empty
+                const float4 nb = c.w32[2 * n + 1];
                 const bool is_leaf = n >= leaf0;
                 // reachability
                 const float dx = rgA.x - na.x, dy = rgA.y - na.y, dz = rgA.z - na.z;
@@ -203,9 +203,7 @@ int walk_tree(rcb_tree *t) {
     c.nn = t->nn;
     c.theta2 = t->params.theta * t->params.theta;
     c.theta2f = (float)c.theta2;
-    c.ncount = t->ncount;
-    c.w32a = t->w32a;
-    c.w32b = t->w32b;
+    c.w32 = t->w32;
     c.nrg = t->nrg;
     c.nhint = t->nhint;
     c.ncom = t->ncom;
