@@ -239,14 +239,13 @@ constexpr int kNearTile = 512;    // staged sources per warp
 template <bool NB>
 struct NearSmem {
     static constexpr size_t bytes =
-        kNearTile * (sizeof(float4) + sizeof(float) + sizeof(uint16_t)) + 2 * kGroupMixed * sizeof(float4) +
+        kNearTile * (sizeof(float4) + sizeof(float)) + 2 * kGroupMixed * sizeof(float4) +
         (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * sizeof(float2) + kGroupMixed / 2 * sizeof(float2) : 0);
     float4 *src;    // (d_b relative to the sink's centre of mass, m_b)
     float *hs;      // h_b
     float4 *snk;    // (d_a, h_a) of the current group
     float4 *snk2;   // the same by pairs (i, i + 1): (x_i, x_i+1, y_i, y_i+1), (z_i, z_i+1, h_i, h_i+1)
     float2 *hi2;    // NB: upper band edges by pairs
-    uint16_t *perm;
     int32_t *sidx;  // NB
     float2 *band;   // NB: per sink particle (2h)^2 -+ B
     __device__ NearSmem(unsigned char *p) {
@@ -257,42 +256,32 @@ struct NearSmem {
         band = reinterpret_cast<float2 *>(snk2 + kGroupMixed);
         hi2 = band + (NB ? kGroupMixed : 0);
         sidx = reinterpret_cast<int32_t *>(hi2 + (NB ? kGroupMixed / 2 : 0));
-        perm = reinterpret_cast<uint16_t *>(sidx + (NB ? kNearTile : 0));
     }
 };
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// Staged tile: sources [0, ns) of src/hs (and sidx); perm[0, nclose) lists the close sources,
-// perm[kNearTile - nfar, kNearTile) the far ones (see below).
+// Staged tile: the close sources at [0, nclose) of src/hs (and sidx), the far ones at
+// [kNearTile - nfar, kNearTile) (see below).
 struct NearTile {
-    int ns, nclose, nfar;
+    int nclose, nfar;
     int64_t S;  // all sources of the sink
 };
 
 // Stage sources [t0, t0 + kNearTile) of the sink's near cells.  For 32 cells at a time, lanes
 // first describe the cells (first particle, count, centre-of-mass offset), then take one slot
-// each, find its cell and start an asynchronous copy of the particle's float32 record and h into
-// shared memory; after one wait, a second pass adds the cell offset (float32 offset from the
-// sink's centre of mass) and classifies the source.  The cell offset is the double-float
-// difference of the two centres of mass; with NB it is the float64 difference rounded once (the
-// neighbour bound is derived for that), the sorted index is kept (bitwise complement for
-// sources of non-candidate cells) and wmax gets the tile's largest |dCOM|_1 + |d_b|_1.
+// each (two slot chunks per round, so both gathers are in flight together), find the slot's
+// cell, form the particle's float32 offset from the sink's centre of mass and store it with
+// its mass and h, close sources from the front of the tile and far ones from the back.  The
+// cell offset is the double-float difference of the two centres of mass; with NB it is the
+// float64 difference rounded once (the neighbour bound is derived for that), the sorted index
+// is kept (bitwise complement for sources of non-candidate cells) and wmax gets the tile's
+// largest |dCOM|_1 + |d_b|_1.
 //
-// Classification: with R_A the largest |d_a| and H_A the largest h_a of the sink's particles,
-// a source b with |d_b| > (R_A + X_b)(1 + 2^-10) has r_ab >= |d_b| - |d_a| > X_b for every sink
+// Far sources: with R_A the largest |d_a| and H_A the largest h_a of the sink's particles, a
+// source b with |d_b| > (R_A + X_b)(1 + 2^-10) has r_ab >= |d_b| - |d_a| > X_b for every sink
 // particle a.  X_b = H_A + h_b puts all its pairs on the Newtonian branch of Eq. 10 (q >= 2);
 // with NB, X_b = max(H_A + h_b, 2 H_A) also keeps it out of every sink particle's neighbour
 // sphere (r < 2 h_a).  The 2^-10 margin is far above the float32 rounding of the test, of q and
-// of the neighbour filter.  Such sources fill perm from the back, the others from the front.
+// of the neighbour filter.
 template <bool NB>
 __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, int64_t t0, const NearSmem<NB> &sm,
                                      float RA, float HA, float &wmax) {
@@ -332,57 +321,50 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
         const int total = __shfl_sync(0xffffffffu, excl + n, 31);
         const int64_t lo = pos > t0 ? pos : t0;
         const int64_t hi = pos + total < t0 + kNearTile ? pos + total : t0 + kNearTile;
-        // copies in flight for every slot of these cells (two slot chunks per round)
         for (int64_t j0 = lo; j0 < hi; j0 += 64) {
-            int cl[2], b[2];
+            int b[2], cl[2];
+            float cx[2], cy[2], cz[2];
+            bool act[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int rel = (int)(j0 + 32 * u + lane - pos);
                 cl[u] = warp_run_of(excl, n, (int)(j0 + 32 * u - pos));
                 b[u] = __shfl_sync(0xffffffffu, f, cl[u]) + rel - __shfl_sync(0xffffffffu, excl, cl[u]);
+                cx[u] = __shfl_sync(0xffffffffu, ox, cl[u]);
+                cy[u] = __shfl_sync(0xffffffffu, oy, cl[u]);
+                cz[u] = __shfl_sync(0xffffffffu, oz, cl[u]);
+                act[u] = j0 + 32 * u + lane < hi;
             }
+            float4 pb[2];
+            float hb[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const int64_t j = j0 + 32 * u + lane;
-                if (j < hi) {
-                    cp_async16(&sm.src[j - t0], &c.p32[b[u]]);
-                    cp_async4(&sm.hs[j - t0], &c.h32[b[u]]);
-                    if (NB) sm.sidx[j - t0] = k0 + cl[u] < nr ? b[u] : ~b[u];
-                }
-            }
-        }
-        cp_async_wait_all();
-        __syncwarp();
-        // cell offsets and classification
-        for (int64_t j0 = lo; j0 < hi; j0 += 64) {
-            bool act[2], far[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int64_t j = j0 + 32 * u + lane;
-                const int cl = warp_run_of(excl, n, (int)(j0 + 32 * u - pos));
-                const float cx = __shfl_sync(0xffffffffu, ox, cl), cy = __shfl_sync(0xffffffffu, oy, cl),
-                            cz = __shfl_sync(0xffffffffu, oz, cl);
-                act[u] = j < hi;
-                far[u] = false;
+                pb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                hb[u] = 0.f;
                 if (act[u]) {
-                    const float4 pb = sm.src[j - t0];
-                    const float4 v = make_float4(cx + pb.x, cy + pb.y, cz + pb.z, pb.w);
-                    sm.src[j - t0] = v;
-                    if (NB) wl = fmaxf(wl, (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
-                    const float hb = sm.hs[j - t0];
-                    const float d2 = fmaf(v.z, v.z, fmaf(v.y, v.y, v.x * v.x));
-                    const float X = NB ? fmaxf(HA + hb, HA + HA) : HA + hb;
-                    const float R = (RA + X) * (1.0f + 0x1p-10f);
-                    far[u] = d2 > R * R;
+                    pb[u] = c.p32[b[u]];
+                    hb[u] = c.h32[b[u]];
                 }
             }
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const unsigned mc = __ballot_sync(0xffffffffu, act[u] && !far[u]);
-                const unsigned mf = __ballot_sync(0xffffffffu, act[u] && far[u]);
-                if (act[u])
-                    sm.perm[far[u] ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt)] =
-                        (uint16_t)(j0 + 32 * u + lane - t0);
+                const float4 v = make_float4(cx[u] + pb[u].x, cy[u] + pb[u].y, cz[u] + pb[u].z, pb[u].w);
+                const float d2 = fmaf(v.z, v.z, fmaf(v.y, v.y, v.x * v.x));
+                const float X = NB ? fmaxf(HA + hb[u], HA + HA) : HA + hb[u];
+                const float R = (RA + X) * (1.0f + 0x1p-10f);
+                const bool far = d2 > R * R;
+                const unsigned mc = __ballot_sync(0xffffffffu, act[u] && !far);
+                const unsigned mf = __ballot_sync(0xffffffffu, act[u] && far);
+                if (act[u]) {
+                    const int at = far ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt);
+                    sm.src[at] = v;
+                    sm.hs[at] = hb[u];
+                    if (NB) {
+                        sm.sidx[at] = k0 + cl[u] < nr ? b[u] : ~b[u];
+                        wl = fmaxf(wl, (fabsf(cx[u]) + fabsf(cy[u]) + fabsf(cz[u])) + fabsf(pb[u].x) + fabsf(pb[u].y) +
+                                           fabsf(pb[u].z));
+                    }
+                }
                 nclose += __popc(mc);
                 nfar += __popc(mf);
             }
@@ -394,8 +376,7 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
         wmax = wl;
     }
     __syncwarp();
-    const int64_t left = pos - t0;
-    return NearTile{(int)(left < kNearTile ? left : kNearTile), nclose, nfar, pos};
+    return NearTile{nclose, nfar, pos};
 }
 
 // Neighbour-search state of one group of sink particles.
@@ -460,7 +441,7 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const Ne
     for (int q0 = kNearTile - tl.nfar; q0 < kNearTile; q0 += 32) {
         const int j = q0 + lane;
         // padding lanes: a massless source far away (finite r, zero contribution)
-        const float4 b = j < kNearTile ? sm.src[sm.perm[j]] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        const float4 b = j < kNearTile ? sm.src[j] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
         const float2 nbx = make_float2(-b.x, -b.x), nby = make_float2(-b.y, -b.y), nbz = make_float2(-b.z, -b.z);
         const float2 nbm = make_float2(-b.w, -b.w);
 #pragma unroll
@@ -492,10 +473,9 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const Ne
         float hb = 1.f;
         int sb = -1;
         if (j < nclose) {
-            const int pj = sm.perm[j];
-            b = sm.src[pj];
-            hb = sm.hs[pj];
-            if (NB) sb = sm.sidx[pj];
+            b = sm.src[j];
+            hb = sm.hs[j];
+            if (NB) sb = sm.sidx[j];
         }
         const unsigned cand = NB ? __ballot_sync(0xffffffffu, sb >= 0) : 0u;  // candidate-cell sources
         const bool own = NB && __any_sync(0xffffffffu, sb >= g.a0 && sb < g.a0 + G);
@@ -599,7 +579,7 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             RA = sqrtf(R2) * (1.0f + 0x1p-10f);
             HA = H;
         }
-        NearTile once{-1, 0, 0, 0};  // staged tile when all sources fit one tile
+        NearTile once{-1, 0, 0};  // staged tile when all sources fit one tile
         float wmax = 0.f;
         for (int a0 = 0; a0 < nA; a0 += kGroupMixed) {
             const int na = min(kGroupMixed, nA - a0);
@@ -621,7 +601,7 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             float rs = 0.f, rc = 0.f;  // compensated total of value lane mod 4 G (= 4 i + q)
             for (int64_t t0 = 0;; t0 += kNearTile) {
                 NearTile tl = once;
-                if (tl.ns < 0) {
+                if (tl.nclose < 0) {
                     tl = stage_near_mixed<NB>(c, s, A, nlist, nr, t0, sm, RA, HA, wmax);
                     if (tl.S <= kNearTile) once = tl;
                 }
