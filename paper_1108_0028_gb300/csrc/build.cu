@@ -180,7 +180,8 @@ __global__ void k_exponents(const unsigned long long *maxbits, int *E) {
 }
 
 __global__ void k_ingest_write(const double *__restrict__ x, const double *__restrict__ m, int64_t N, int64_t capN,
-                               const int *E, double *bx, double *by, double *bz, int64_t *bP, int32_t *bidx,
+                               const int *E, double *__restrict__ bx, double *__restrict__ by,
+                               double *__restrict__ bz, int64_t *__restrict__ bP, int32_t *__restrict__ bidx,
                                Red *partials, int *status) {
     __shared__ Red scratch[32];
     Red r;
@@ -289,9 +290,10 @@ __global__ void k_chunk_plan(const int32_t *big, const int32_t *nbig_ptr, const 
 }
 
 // Per chunk: number of particles left of the split, their exact sums, and both sides' boxes.
-__global__ void __launch_bounds__(kChunkThreads) k_level_reduce(Ctx c, const int4 *chunks, const int *nchunks_ptr,
-                                                                const double *bx, const double *by, const double *bz,
-                                                                const int64_t *bP, ChunkPart *parts) {
+__global__ void __launch_bounds__(kChunkThreads)
+    k_level_reduce(Ctx c, const int4 *chunks, const int *nchunks_ptr, const double *__restrict__ bx,
+                   const double *__restrict__ by, const double *__restrict__ bz, const int64_t *__restrict__ bP,
+                   ChunkPart *parts) {
     __shared__ Red scratch[kChunkThreads / 32];
     int nchunks = *nchunks_ptr;
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
@@ -429,12 +431,12 @@ __global__ void k_level_finalize(Ctx c, int level, const int32_t *big, const int
 }
 
 // Stable scatter of each chunk's records to their children's ranges in the other buffer.
-__global__ void __launch_bounds__(kChunkThreads) k_level_scatter(Ctx c, const int4 *chunks, const int *nchunks_ptr,
-                                                                 const ChunkPart *parts, const double *bx,
-                                                                 const double *by, const double *bz,
-                                                                 const int64_t *bP, const int32_t *bidx,
-                                                                 double *ox, double *oy, double *oz, int64_t *oP,
-                                                                 int32_t *oidx) {
+__global__ void __launch_bounds__(kChunkThreads)
+    k_level_scatter(Ctx c, const int4 *chunks, const int *nchunks_ptr, const ChunkPart *parts,
+                    const double *__restrict__ bx, const double *__restrict__ by, const double *__restrict__ bz,
+                    const int64_t *__restrict__ bP, const int32_t *__restrict__ bidx, double *__restrict__ ox,
+                    double *__restrict__ oy, double *__restrict__ oz, int64_t *__restrict__ oP,
+                    int32_t *__restrict__ oidx) {
     __shared__ int wsum[kChunkThreads / 32];
     int nchunks = *nchunks_ptr;
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
