@@ -304,16 +304,37 @@ __global__ void __launch_bounds__(kChunkThreads)
         Red rl, rr;
         red_init(rl);
         red_init(rr);
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-            int64_t e = start + i;
-            int64_t key[3] = {dkey(bx[e]), dkey(by[e]), dkey(bz[e])};
-            int64_t P[4];
-            for (int k = 0; k < 4; ++k) P[k] = bP[k * c.capN + e];
-            if (key[ax] < sk) red_add_particle(rl, P, key);
-            else {
-                for (int d = 0; d < 3; ++d) {
-                    rr.lo[d] = min(rr.lo[d], key[d]);
-                    rr.hi[d] = max(rr.hi[d], key[d]);
+        // the chunk's elements, kChunk / kChunkThreads per thread, in batches of four whose loads
+        // are all issued before their arithmetic
+        constexpr int kPer = kChunk / kChunkThreads, kBatch = 4;
+#pragma unroll
+        for (int j0 = 0; j0 < kPer; j0 += kBatch) {
+            double vx[kBatch], vy[kBatch], vz[kBatch];
+            int64_t vP[kBatch][4];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int i = threadIdx.x + (j0 + u) * kChunkThreads;
+                if (i < cnt) {
+                    const int64_t e = start + i;
+                    vx[u] = bx[e];
+                    vy[u] = by[e];
+                    vz[u] = bz[e];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) vP[u][k] = bP[k * c.capN + e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int i = threadIdx.x + (j0 + u) * kChunkThreads;
+                if (i < cnt) {
+                    int64_t key[3] = {dkey(vx[u]), dkey(vy[u]), dkey(vz[u])};
+                    if (key[ax] < sk) red_add_particle(rl, vP[u], key);
+                    else {
+                        for (int d = 0; d < 3; ++d) {
+                            rr.lo[d] = min(rr.lo[d], key[d]);
+                            rr.hi[d] = max(rr.hi[d], key[d]);
+                        }
+                    }
                 }
             }
         }
@@ -471,19 +492,43 @@ __global__ void __launch_bounds__(kChunkThreads)
         __syncthreads();
         unsigned lt = (1u << lane) - 1u;
         int run = before;
-        for (int j = 0; j < kPer; ++j) {
-            int i = w * 32 * kPer + j * 32 + lane;
-            bool left = (masks[j] >> lane) & 1u;
-            int lrank = run + __popc(masks[j] & lt);
-            run += __popc(masks[j]);
-            if (i < cnt) {
-                int64_t e = start + i;
-                int64_t dst = left ? (int64_t)f + leftoff + lrank : (int64_t)f + nLcell + rightoff + (i - lrank);
-                ox[dst] = bx[e];
-                oy[dst] = by[e];
-                oz[dst] = bz[e];
-                for (int k = 0; k < 4; ++k) oP[k * c.capN + dst] = bP[k * c.capN + e];
-                oidx[dst] = bidx[e];
+        // two batches of four elements: every field load of a batch is issued before its stores
+        constexpr int kBatch = 4;
+#pragma unroll
+        for (int j0 = 0; j0 < kPer; j0 += kBatch) {
+            double vx[kBatch], vy[kBatch], vz[kBatch];
+            int64_t vP[kBatch][4];
+            int32_t vi[kBatch];
+            int64_t dst[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int j = j0 + u;
+                const int i = w * 32 * kPer + j * 32 + lane;
+                const bool left = (masks[j] >> lane) & 1u;
+                const int lrank = run + __popc(masks[j] & lt);
+                run += __popc(masks[j]);
+                dst[u] = left ? (int64_t)f + leftoff + lrank : (int64_t)f + nLcell + rightoff + (i - lrank);
+                if (i < cnt) {
+                    const int64_t e = start + i;
+                    vx[u] = bx[e];
+                    vy[u] = by[e];
+                    vz[u] = bz[e];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) vP[u][k] = bP[k * c.capN + e];
+                    vi[u] = bidx[e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int i = w * 32 * kPer + (j0 + u) * 32 + lane;
+                if (i < cnt) {
+                    ox[dst[u]] = vx[u];
+                    oy[dst[u]] = vy[u];
+                    oz[dst[u]] = vz[u];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) oP[k * c.capN + dst[u]] = vP[u][k];
+                    oidx[dst[u]] = vi[u];
+                }
             }
         }
     }
