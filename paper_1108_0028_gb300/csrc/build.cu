@@ -594,10 +594,11 @@ struct Bufs {
     const int32_t *idx[2];
 };
 
-__global__ void __launch_bounds__(kCtaThreads, 1)
+__global__ void __launch_bounds__(kCtaThreads, 2)
     k_subtree(Ctx c, const int32_t *roots, const int *nroots_ptr, Bufs B, const double *__restrict__ m_in,
-              const double *__restrict__ h_in, double *px, double *py, double *pz, double *pm, double *ph,
-              int32_t *pidx) {
+              const double *__restrict__ h_in, double *__restrict__ px, double *__restrict__ py,
+              double *__restrict__ pz, double *__restrict__ pm, double *__restrict__ ph,
+              int32_t *__restrict__ pidx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SubtreeSmem &s = *reinterpret_cast<SubtreeSmem *>(smem_raw);
     const int nroots = *nroots_ptr;
@@ -855,12 +856,17 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
     if (s >= nsinks) return;
     int n = sinks[s];
     int f = c.nfirst[n], cnt = c.ncount[n];
+    // the particle arrays are read-only here and never alias the float32 copies written below
+    const double *__restrict__ px = c.px, *__restrict__ py = c.py, *__restrict__ pz = c.pz;
+    const double *__restrict__ pm = c.pm, *__restrict__ ph = c.ph;
+    float4 *__restrict__ p32 = c.p32;
+    float *__restrict__ h32 = c.h32;
     double com[3] = {c.ncom[3 * (int64_t)n], c.ncom[3 * (int64_t)n + 1], c.ncom[3 * (int64_t)n + 2]};
     double rg[3] = {c.nrg[3 * (int64_t)n], c.nrg[3 * (int64_t)n + 1], c.nrg[3 * (int64_t)n + 2]};
     double Q[6] = {0, 0, 0, 0, 0, 0};
     double hint = 0.0, hnode = 0.0;
     for (int a = f; a < f + cnt; ++a) {
-        double x = c.px[a], y = c.py[a], z = c.pz[a], m = c.pm[a], h = c.ph[a];
+        double x = px[a], y = py[a], z = pz[a], m = pm[a], h = ph[a];
         double dx[3] = {__dsub_rn(x, com[0]), __dsub_rn(y, com[1]), __dsub_rn(z, com[2])};
         double dr2 = __dadd_rn(__dadd_rn(__dmul_rn(dx[0], dx[0]), __dmul_rn(dx[1], dx[1])), __dmul_rn(dx[2], dx[2]));
         double tm = __dmul_rn(3.0, m);
@@ -874,9 +880,9 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
         double d = __dsqrt_rn(dist2_rn(x, y, z, rg[0], rg[1], rg[2]));
         hint = fmax(hint, d);
         hnode = fmax(hnode, __dadd_rn(d, __dmul_rn(2.0, h)));
-        c.p32[a] = make_float4(__double2float_rn(dx[0]), __double2float_rn(dx[1]), __double2float_rn(dx[2]),
-                               __double2float_rn(m));
-        c.h32[a] = __double2float_rn(h);
+        p32[a] = make_float4(__double2float_rn(dx[0]), __double2float_rn(dx[1]), __double2float_rn(dx[2]),
+                             __double2float_rn(m));
+        h32[a] = __double2float_rn(h);
     }
     for (int k = 0; k < 6; ++k) c.nQ[6 * (int64_t)n + k] = Q[k];
     c.nhint[n] = hint;
@@ -1270,7 +1276,7 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
         stage_begin(t, SG_SUBTREE);
         size_t smem = sizeof(SubtreeSmem);
         RCB_CUDA_TRY(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int g = std::max(1, std::min(nroots, nsm));
+        int g = std::max(1, std::min(nroots, 2 * nsm));
         k_subtree<<<g, kCtaThreads, smem, st>>>(c, t->roots, t->d_status + ST_NROOTS, B, m, h, t->px, t->py, t->pz,
                                                 t->pm, t->ph, t->pidx); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());

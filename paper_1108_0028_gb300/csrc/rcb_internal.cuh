@@ -14,8 +14,8 @@ typedef unsigned __int128 u128;
 
 constexpr int kNbRowCap = 128;  // slots of a particle's neighbour row before the compaction
 constexpr int kMaxL = 28;           // deepest supported lowest level (node labels < 2^29)
-constexpr int kTcta = 2048;         // largest cell whose subtree one CTA builds in shared memory
-constexpr int kCtaThreads = 512;    // threads of that CTA
+constexpr int kTcta = 1024;        // largest cell whose subtree one CTA builds in shared memory (two CTAs per SM)
+constexpr int kCtaThreads = 256;    // threads of that CTA
 constexpr int kChunk = 2048;        // particles per chunk in the level passes over large cells
 constexpr int kChunkThreads = 256;
 
