@@ -62,6 +62,28 @@ def workload_name(a):
             f"theta={a.theta}")
 
 
+def bench_config(a, world):
+    """The `config` object of the JSON line (both arms)."""
+    return {"workload": workload_name(a), "N": a.n, "theta": a.theta, "n_ll": N_LL, "form": "mixed",
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs (164 MB) exceed L2 and a 256 MB buffer is written between timed steps"}
+
+
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the slowest replica's time); value itself on one rank."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n, ms):
+    """Mparticles/s of the whole job: every replica processes n particles per step of ms."""
+    return world * n / (ms * 1e-3) / 1e6
+
+
 # ------------------------------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
@@ -160,7 +182,7 @@ def run_reference(a, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a)},
+            "config": bench_config(a, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -189,7 +211,7 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
     e = (torch.linalg.norm(acc_m - acc_d, dim=1) / torch.linalg.norm(acc_d, dim=1)).cpu().numpy()
     ep = (torch.abs(pot_m - pot_d) / torch.abs(pot_d)).cpu().numpy()
     t_fp64 = ms - (stage_ms["far"] + stage_ms["near"]) + statistics.mean(f64_grav)
-    fp64 = {"value": world * a.n / (t_fp64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": t_fp64,
+    fp64 = {"value": job_throughput(world, a.n, t_fp64), "unit": UNIT, "ms_per_step": t_fp64,
             "gravity_ms": statistics.mean(f64_grav)}
     accuracy = {"reference": "FP64 GPU form on the same tree (parity of the FP64 form with the FP64 oracle is "
                              "tested separately: RMS 1e-15)",
@@ -223,14 +245,10 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    ems = statistics.mean(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([ems], device=xt.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
+    ems = max_over_ranks(statistics.mean(e2e_ms), dist, xt.device)
     h2d = (x.nbytes + m.nbytes + h.nbytes)
     d2h = offh.numel() * 8 + idx0.numel() * 4 + acch.numel() * 8 + poth.numel() * 8
-    e2e = {"value": world * a.n / (ems * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ems,
+    e2e = {"value": job_throughput(world, a.n, ems), "unit": UNIT, "ms_per_step": ems,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     return fp64, accuracy, e2e, int(idx0.numel())
 
@@ -287,12 +305,8 @@ def run_ours(a, rank, world, local_rank):
         stages.append(tree.stage_times())
     barrier()
     launches = tree.info()["launches"] - launches0
-    ms = statistics.mean(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * a.n / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(statistics.mean(step_ms), dist, dev)
+    value = job_throughput(world, a.n, ms)
     stage_ms = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
     info = tree.info()
 
@@ -339,9 +353,7 @@ def run_ours(a, rank, world, local_rank):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "mixed: f32 near/far tensors, f64 build + Taylor coefficients; int64/int128 tree keys",
         "data": "synthetic",
-        "config": {"workload": workload_name(a), "N": a.n, "theta": a.theta, "n_ll": N_LL, "form": "mixed",
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs (164 MB) exceed L2 and a 256 MB buffer is written between timed steps"},
+        "config": bench_config(a, world),
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
