@@ -849,8 +849,7 @@ __device__ void parent_moments(const LeafCtx &c, int P) {
     c.nhnode[P] = 0.0;
 }
 
-// One thread per sink: Eq. 1, radii, float32 copies; then climb while this thread is the
-// second child to finish.
+// One thread per sink: Eq. 1, radii, float32 copies.
 __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsinks) return;
@@ -887,17 +886,15 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
     for (int k = 0; k < 6; ++k) c.nQ[6 * (int64_t)n + k] = Q[k];
     c.nhint[n] = hint;
     c.nhnode[n] = hnode;
-    // climb
-    while (n > 1) {
-        int sib = n ^ 1, P = n >> 1;
-        __threadfence();
-        if (__ldcg(&c.ncount[sib]) > 0) {
-            int old = atomicAdd(&c.narrive[P], 1);
-            if (old == 0) return;  // the sibling's thread will compute the parent
-            __threadfence();
-        }
-        parent_moments(c, P);
-        n = P;
+}
+
+// Eq. 2 for every non-empty node of one level from its children (one launch per level, from
+// the level above the ll-cells up to the root).
+__global__ void k_level_up(LeafCtx c, int level) {
+    const int64_t first = (int64_t)1 << level, count = first;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const int P = (int)(first + i);
+        if (c.ncount[P] > 0) parent_moments(c, P);
     }
 }
 
@@ -1194,6 +1191,15 @@ int scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, void *t
     return cudaGetLastError() == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
 }
 
+// Eq. 2 level by level, from the level above the ll-cells up to the root.
+static void launch_levels_up(const LeafCtx &lc, int L, int nsm, cudaStream_t st) {
+    for (int level = L - 1; level >= 0; --level) {
+        const int64_t nodes = (int64_t)1 << level;
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nodes + 255) / 256, (int64_t)nsm * 8));
+        k_level_up<<<g, 256, 0, st>>>(lc, level); note_launch();
+    }
+}
+
 int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
     cudaStream_t st = t->stream;
     const int64_t N = t->N;
@@ -1321,6 +1327,7 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
         lc.p32 = t->p32;
         lc.h32 = t->h32;
         if (t->nsinks > 0) k_leaves_up<<<(t->nsinks + 127) / 128, 128, 0, st>>>(lc, t->sinks, t->nsinks); note_launch();
+        launch_levels_up(lc, t->L, nsm, st);
         PackCtx pc;
         pc.ncount = t->ncount;
         pc.nmass = t->nmass;
@@ -1377,6 +1384,7 @@ int refit_tree(rcb_tree *t, const double *x, const double *m) {
     lc.p32 = t->p32;
     lc.h32 = t->h32;
     k_leaves_up<<<(t->nsinks + 127) / 128, 128, 0, st>>>(lc, t->sinks, t->nsinks); note_launch();
+    launch_levels_up(lc, t->L, sm_count(), st);
     PackCtx pc;
     pc.ncount = t->ncount;
     pc.nmass = t->nmass;
