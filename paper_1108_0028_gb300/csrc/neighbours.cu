@@ -318,36 +318,57 @@ __device__ inline void warp_sort(int32_t (&v)[R]) {
     }
 }
 
-template <int R>
-__device__ inline void sort_row(const int32_t *row, const int32_t *pidx, int n, int32_t *dst) {
+// A warp takes 32 consecutive particles (sorted indices): their permutation entries and offsets
+// are loaded once, coalesced; then row by row the slot entries are mapped to original indices,
+// sorted in registers and written at the row's offset, the next row's entries being gathered
+// before the current row is sorted.  Rows longer than kRowCap are written by k_nb_long.
+__device__ inline void load_row(const int32_t *rows, const int32_t *pidx, int64_t a, int n, int32_t v[4]) {
     const int lane = threadIdx.x & 31;
-    int32_t v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = r * 32 + lane < n ? pidx[row[r * 32 + lane]] : INT32_MAX;
-    warp_sort<R>(v);
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-        if (r * 32 + lane < n) dst[r * 32 + lane] = v[r];
+    for (int r = 0; r < 4; ++r) {
+        const int q = r * 32 + lane;
+        v[r] = (n <= kRowCap && q < n) ? pidx[rows[a * kRowCap + q]] : INT32_MAX;
+    }
 }
 
-// One warp per particle (sorted index a): map its slot row to original indices, sort it and
-// write it at its offset.
 __global__ void __launch_bounds__(256) k_nb_compact(const int32_t *rows, const int32_t *pidx, const int64_t *offsets,
                                                     int32_t *idx, int64_t N) {
+    const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t a = gw; a < N; a += nw) {
-        const int r = pidx[a];
-        const int64_t o = offsets[r];
-        const int n = (int)(offsets[r + 1] - o);
-        if (n > kRowCap) continue;  // written by k_nb_long
-        const int32_t *row = rows + a * kRowCap;
-        if (n <= 32)
-            sort_row<1>(row, pidx, n, idx + o);
-        else if (n <= 64)
-            sort_row<2>(row, pidx, n, idx + o);
-        else
-            sort_row<4>(row, pidx, n, idx + o);
+    for (int64_t base = gw * 32; base < N; base += nw * 32) {
+        int64_t ol = 0;
+        int nl = 0;
+        if (base + lane < N) {
+            const int r = pidx[base + lane];
+            ol = offsets[r];
+            nl = (int)(offsets[r + 1] - ol);
+        }
+        const int cnt = (int)(N - base < 32 ? N - base : 32);
+        int32_t cur[4], nxt[4];
+        load_row(rows, pidx, base, __shfl_sync(0xffffffffu, nl, 0), cur);
+        for (int i = 0; i < cnt; ++i) {
+            if (i + 1 < cnt) load_row(rows, pidx, base + i + 1, __shfl_sync(0xffffffffu, nl, i + 1), nxt);
+            const int n = __shfl_sync(0xffffffffu, nl, i);
+            const int64_t o = __shfl_sync(0xffffffffu, ol, i);
+            if (n <= 32) {
+                int32_t v[1] = {cur[0]};
+                warp_sort<1>(v);
+                if (lane < n) idx[o + lane] = v[0];
+            } else if (n <= 64) {
+                int32_t v[2] = {cur[0], cur[1]};
+                warp_sort<2>(v);
+                idx[o + lane] = v[0];
+                if (lane + 32 < n) idx[o + lane + 32] = v[1];
+            } else if (n <= kRowCap) {
+                warp_sort<4>(cur);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r * 32 + lane < n) idx[o + r * 32 + lane] = cur[r];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) cur[r] = nxt[r];
+        }
     }
 }
 
