@@ -250,7 +250,34 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
     d2h = offh.numel() * 8 + idx0.numel() * 4 + acch.numel() * 8 + poth.numel() * 8
     e2e = {"value": job_throughput(world, a.n, ems), "unit": UNIT, "ms_per_step": ems,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
-    return fp64, accuracy, e2e, int(idx0.numel())
+    # per stage (Sec. 2.1-2.2 build with the walk; Sec. 2.3 neighbours alone; Sec. 2.4 gravity
+    # alone; and the fused pass the step uses), each timed by the library's stage events
+    def staged(fn, keys, reps=5):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            fn()
+            st = tree.stage_times()
+            out.append(sum(st[k] for k in keys))
+        return statistics.mean(out)
+
+    build_ms = staged(lambda: tree.rebuild(xt, mt, ht), ["build"])
+    nb_ms = staged(lambda: (tree.refit(xt, mt), tree.neighbours()), ["nb_count", "nb_fill", "nb_sort"])
+    grav_ms = staged(lambda: tree.gravity(), ["far", "near"])
+    fused_ms = staged(lambda: (tree.refit(xt, mt), tree.gravity_neighbours()),
+                      ["far", "near", "nb_count", "nb_fill", "nb_sort"])
+    L = tree.info()["L"]
+    build_bytes = a.n * (72 * L + 56)  # every level reads and writes 36 B per particle, h gathered once
+    per_stage = {
+        "build": {"ms": build_ms, "mparticles_s": job_throughput(world, a.n, build_ms),
+                  "algorithmic_bytes": build_bytes, "achieved_gbs": build_bytes / (build_ms * 1e-3) / 1e9},
+        "neighbours": {"ms": nb_ms, "mparticles_s": job_throughput(world, a.n, nb_ms), "path": "rcb_neighbours alone"},
+        "gravity": {"ms": grav_ms, "mparticles_s": job_throughput(world, a.n, grav_ms), "path": "rcb_gravity alone"},
+        "neighbours_gravity_fused": {"ms": fused_ms, "mparticles_s": job_throughput(world, a.n, fused_ms),
+                                     "path": "rcb_gravity_neighbours + compaction (the step's path)"},
+    }
+    return fp64, accuracy, e2e, int(idx0.numel()), per_stage
 
 
 def run_ours(a, rank, world, local_rank):
@@ -310,10 +337,10 @@ def run_ours(a, rank, world, local_rank):
     stage_ms = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
     info = tree.info()
 
-    fp64 = accuracy = e2e = None
+    fp64 = accuracy = e2e = per_stage = None
     idx_total = None
     if not a.headline_only:
-        fp64, accuracy, e2e, idx_total = extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step,
+        fp64, accuracy, e2e, idx_total, per_stage = extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step,
                                                     barrier, ms, stage_ms)
     clocks = sampler.stop() if sampler else None
 
@@ -339,6 +366,9 @@ def run_ours(a, rank, world, local_rank):
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
+    if per_stage:
+        per_stage["build"]["hbm_peak_gbs"] = hbm
+        per_stage["build"]["frac"] = per_stage["build"]["achieved_gbs"] / hbm
     cpu = None
     if not a.no_cpu_baseline and not a.headline_only and world == 1:
         import oracle
@@ -360,6 +390,7 @@ def run_ours(a, rank, world, local_rank):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "stages_ms": stage_ms,
+        "per_stage": per_stage,
         "fp64": fp64,
         "accuracy_mixed_vs_fp64": accuracy,
         "tree": {k: info[k] for k in ("L", "nsinks", "near_total", "far_total", "reach_total", "near_pairs",
