@@ -863,7 +863,14 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
     double com[3] = {c.ncom[3 * (int64_t)n], c.ncom[3 * (int64_t)n + 1], c.ncom[3 * (int64_t)n + 2]};
     double rg[3] = {c.nrg[3 * (int64_t)n], c.nrg[3 * (int64_t)n + 1], c.nrg[3 * (int64_t)n + 2]};
     double Q[6] = {0, 0, 0, 0, 0, 0};
-    double hint = 0.0, hnode = 0.0;
+    // h_int = max_a |r_a - r_g| = sqrt(max_a |r_a - r_g|^2): a correctly rounded square root is
+    // monotonic, so one root per cell gives the same double.  h_node = max_a (|r_a - r_g| + 2 h_a):
+    // float32 estimates (relative error < 2^-21) find the leader; when the runner-up estimate is
+    // more than 2^-18 below it, the exact maximum is the leader's (only it is evaluated in
+    // float64), otherwise every particle is.
+    double d2max = 0.0;
+    float e1 = -1.f, e2 = -1.f;  // largest and second largest estimates
+    int a1 = f;
     for (int a = f; a < f + cnt; ++a) {
         double x = px[a], y = py[a], z = pz[a], m = pm[a], h = ph[a];
         double dx[3] = {__dsub_rn(x, com[0]), __dsub_rn(y, com[1]), __dsub_rn(z, com[2])};
@@ -876,13 +883,26 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
                 if (i == j) v -= m * dr2;
                 Q[k] += v;
             }
-        double d = __dsqrt_rn(dist2_rn(x, y, z, rg[0], rg[1], rg[2]));
-        hint = fmax(hint, d);
-        hnode = fmax(hnode, __dadd_rn(d, __dmul_rn(2.0, h)));
+        const double d2 = dist2_rn(x, y, z, rg[0], rg[1], rg[2]);
+        d2max = fmax(d2max, d2);
+        const float est = __fadd_rn(__fsqrt_rn(__double2float_rn(d2)), __double2float_rn(__dmul_rn(2.0, h)));
+        if (est > e1) {
+            e2 = e1;
+            e1 = est;
+            a1 = a;
+        } else if (est > e2) {
+            e2 = est;
+        }
         p32[a] = make_float4(__double2float_rn(dx[0]), __double2float_rn(dx[1]), __double2float_rn(dx[2]),
                              __double2float_rn(m));
         h32[a] = __double2float_rn(h);
     }
+    const double hint = __dsqrt_rn(d2max);
+    double hnode = 0.0;
+    const bool clear = e2 < __fmul_rn(e1, 1.0f - 0x1p-18f);
+    for (int a = clear ? a1 : f; a < (clear ? a1 + 1 : f + cnt); ++a)
+        hnode = fmax(hnode, __dadd_rn(__dsqrt_rn(dist2_rn(px[a], py[a], pz[a], rg[0], rg[1], rg[2])),
+                                      __dmul_rn(2.0, ph[a])));
     for (int k = 0; k < 6; ++k) c.nQ[6 * (int64_t)n + k] = Q[k];
     c.nhint[n] = hint;
     c.nhnode[n] = hnode;
