@@ -271,10 +271,12 @@ struct NearTile {
 // each (two slot chunks per round, so both gathers are in flight together), find the slot's
 // cell, form the particle's float32 offset from the sink's centre of mass and store it with
 // its mass and h, close sources from the front of the tile and far ones from the back.  The
-// cell offset is the double-float difference of the two centres of mass; with NB it is the
-// float64 difference rounded once (the neighbour bound is derived for that), the sorted index
-// is kept (bitwise complement for sources of non-candidate cells) and wmax gets the tile's
-// largest |dCOM|_1 + |d_b|_1.
+// cell offset o is the double-float difference of the two centres of mass: it differs from the
+// float64 difference by at most 2u |dCOM| + 3 2^-48 (|COM_A|_1 + |COM_B|_1) per component
+// (u = 2^-24; the second term is the double-float representation).  With NB the sorted index is
+// kept (bitwise complement for sources of non-candidate cells) and wmax gets the tile's largest
+// w = |o|_1 + |d_b|_1 + 2^-20 (|COM_A|_1 + |COM_B|_1): the last term makes the representation
+// error's share of the d^2 error at most 6 2^-28 F, well inside the neighbour band.
 //
 // Far sources: with R_A the largest |d_a| and H_A the largest h_a of the sink's particles, a
 // source b with |d_b| > (R_A + X_b)(1 + 2^-10) has r_ab >= |d_b| - |d_a| > X_b for every sink
@@ -289,14 +291,14 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
     const unsigned lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)s * c.cap_near;
     const float2 a0 = c.ncomdf[3 * (int64_t)A], a1 = c.ncomdf[3 * (int64_t)A + 1], a2 = c.ncomdf[3 * (int64_t)A + 2];
-    const double cAx = c.ncom[3 * (int64_t)A], cAy = c.ncom[3 * (int64_t)A + 1], cAz = c.ncom[3 * (int64_t)A + 2];
+    const float aabs = fabsf(a0.x) + fabsf(a1.x) + fabsf(a2.x);
     int64_t pos = 0;
     float wl = 0.f;
     int nclose = 0, nfar = 0;
     for (int k0 = 0; k0 < nlist; k0 += 32) {
         const int k = k0 + lane;
         int f = 0, n = 0;
-        float ox = 0.f, oy = 0.f, oz = 0.f;
+        float ox = 0.f, oy = 0.f, oz = 0.f, ow = 0.f;
         const bool inside = pos < t0 + kNearTile;  // cells beyond the tile are only counted
         if (k < nlist) {
             const int B = near_entry(c, base, nr, k);
@@ -305,17 +307,12 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
         if (k < nlist && inside) {
             const int B = near_entry(c, base, nr, k);
             f = c.nfirst[B];
-            if (NB) {
-                ox = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B], cAx));
-                oy = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B + 1], cAy));
-                oz = __double2float_rn(__dsub_rn(c.ncom[3 * (int64_t)B + 2], cAz));
-            } else {
-                const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1],
-                             b2 = c.ncomdf[3 * (int64_t)B + 2];
-                ox = (b0.x - a0.x) + (b0.y - a0.y);
-                oy = (b1.x - a1.x) + (b1.y - a1.y);
-                oz = (b2.x - a2.x) + (b2.y - a2.y);
-            }
+            const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1],
+                         b2 = c.ncomdf[3 * (int64_t)B + 2];
+            ox = (b0.x - a0.x) + (b0.y - a0.y);
+            oy = (b1.x - a1.x) + (b1.y - a1.y);
+            oz = (b2.x - a2.x) + (b2.y - a2.y);
+            if (NB) ow = 0x1p-20f * (aabs + (fabsf(b0.x) + fabsf(b1.x) + fabsf(b2.x)));
         }
         const int excl = warp_excl_scan(n);
         const int total = __shfl_sync(0xffffffffu, excl + n, 31);
@@ -323,7 +320,7 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
         const int64_t hi = pos + total < t0 + kNearTile ? pos + total : t0 + kNearTile;
         for (int64_t j0 = lo; j0 < hi; j0 += 64) {
             int b[2], cl[2];
-            float cx[2], cy[2], cz[2];
+            float cx[2], cy[2], cz[2], cw[2];
             bool act[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
@@ -333,6 +330,7 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
                 cx[u] = __shfl_sync(0xffffffffu, ox, cl[u]);
                 cy[u] = __shfl_sync(0xffffffffu, oy, cl[u]);
                 cz[u] = __shfl_sync(0xffffffffu, oz, cl[u]);
+                cw[u] = NB ? __shfl_sync(0xffffffffu, ow, cl[u]) : 0.f;
                 act[u] = j0 + 32 * u + lane < hi;
             }
             float4 pb[2];
@@ -362,7 +360,7 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
                     if (NB) {
                         sm.sidx[at] = k0 + cl[u] < nr ? b[u] : ~b[u];
                         wl = fmaxf(wl, (fabsf(cx[u]) + fabsf(cy[u]) + fabsf(cz[u])) + fabsf(pb[u].x) + fabsf(pb[u].y) +
-                                           fabsf(pb[u].z));
+                                           fabsf(pb[u].z) + cw[u]);
                     }
                 }
                 nclose += __popc(mc);
@@ -549,9 +547,10 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const Ne
 
 // Mixed near field; with NB also the neighbour search of Sec. 2.3 on the same staged sources
 // (counts to nb_counts by original index, rows of kNbRowCap slots to nb_rows, longer rows
-// queued).  The float32 neighbour filter is the one of the neighbour kernels: d^2 against
-// (2h)^2 -+ B, B = 2^-19 ((W + |d_a|_1)^2 + (2h)^2) + 1e-30 with W the tile's largest
-// |dCOM|_1 + |d_b|_1, the float64 test inside the band.
+// queued).  The float32 neighbour filter compares d^2 with (2h)^2 -+ B,
+// B = 2^-19 ((W + |d_a|_1)^2 + (2h)^2) + 1e-30, W the tile's largest w (see stage_near_mixed):
+// the input and offset roundings, the squares and sums and the roundings of (2h)^2 -+ B stay
+// below 16 u F, half of B; inside the band the float64 test (the definition) decides.
 template <bool NB>
 __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
