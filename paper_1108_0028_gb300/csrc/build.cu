@@ -115,16 +115,17 @@ __device__ void write_cell(const Ctx &c, int node, int level, int first, const R
     for (int k = 0; k < 4; ++k) c.nS[4 * (int64_t)node + k] = r.S[k];
     double ext[3];
     double H = 0.0;
+    const double mass = mass_from_sum(r.S[0], c.E[3]);
     for (int d = 0; d < 3; ++d) {
         c.nbmin[3 * (int64_t)node + d] = r.lo[d];
         c.nbmax[3 * (int64_t)node + d] = r.hi[d];
         double lo = dkey_inv(r.lo[d]), hi = dkey_inv(r.hi[d]);
-        c.ncom[3 * (int64_t)node + d] = com_from_sums(r.S[1 + d], c.E[d], r.S[0], c.E[3]);
+        c.ncom[3 * (int64_t)node + d] = com_from_sums_m(r.S[1 + d], c.E[d], mass);
         c.nrg[3 * (int64_t)node + d] = __dmul_rn(0.5, __dadd_rn(lo, hi));
         ext[d] = __dsub_rn(hi, lo);
         H = fmax(H, ext[d]);
     }
-    c.nmass[node] = mass_from_sum(r.S[0], c.E[3]);
+    c.nmass[node] = mass;
     c.nH[node] = H;
     if (level < c.L) {
         int ax = 0;

@@ -117,12 +117,16 @@ __device__ inline double i128_to_double(i128 v) {
 }
 
 // Centre-of-mass coordinate from the exact sums: RN(RN(S) 2^(E-62) / (RN(M) 2^(Em-62))).
-__device__ inline double com_from_sums(i128 S, int E, i128 M, int Em) {
-    double num = scalbn(i128_to_double(S), E - 62);
-    double den = scalbn(i128_to_double(M), Em - 62);
-    return __ddiv_rn(num, den);
+// x 2^k rounded to nearest: a product with the exact power of two where that power is a normal
+// double (the product then rounds exactly as scalbn does), scalbn otherwise.
+__device__ inline double scale2(double x, int k) {
+    return (k >= -1022 && k <= 1023) ? __dmul_rn(x, pow2i(k)) : scalbn(x, k);
 }
-__device__ inline double mass_from_sum(i128 M, int Em) { return scalbn(i128_to_double(M), Em - 62); }
+// M = RN(RN(S_m) 2^(Em - 62)) and COM_d = RN(RN(RN(S_d) 2^(E_d - 62)) / M).
+__device__ inline double mass_from_sum(i128 M, int Em) { return scale2(i128_to_double(M), Em - 62); }
+__device__ inline double com_from_sums_m(i128 S, int E, double mass) {
+    return __ddiv_rn(scale2(i128_to_double(S), E - 62), mass);
+}
 
 // |a - b|^2 rounded after every operation (no contraction).
 __device__ inline double dist2_rn(double ax, double ay, double az, double bx, double by, double bz) {
