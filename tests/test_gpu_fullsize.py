@@ -22,6 +22,7 @@ FULL = [
     ("plummer", 4194304, "loguniform10", 0.5, 3, 1),
     ("plummer", 1000000, "equal", 0.5, 2, 0),
     ("cube", 10000000, "equal", 0.7, 4, 0),
+    ("cube", 100000000, "equal", 0.7, 4, 2),          # the largest size of the scaling sweep
 ]
 
 
