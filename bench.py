@@ -267,6 +267,13 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
     grav_ms = staged(lambda: tree.gravity(), ["far", "near"])
     fused_ms = staged(lambda: (tree.refit(xt, mt), tree.gravity_neighbours()),
                       ["far", "near", "nb_count", "nb_fill", "nb_sort"])
+    # backward (the VJP of the forces through the frozen tree, Sec. 2.4 differentiated): the
+    # adjoint of loss = sum |a|^2 on the current tree, in the mixed form
+    tree.rebuild(xt, mt, ht)
+    acc_b, _ = tree.gravity()
+    g_acc = 2.0 * acc_b
+    tree.gravity_backward(g_acc)
+    bwd_ms = staged(lambda: tree.gravity_backward(g_acc), ["backward"])
     L = tree.info()["L"]
     build_bytes = a.n * (72 * L + 56)  # every level reads and writes 36 B per particle, h gathered once
     per_stage = {
@@ -276,6 +283,8 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
         "gravity": {"ms": grav_ms, "mparticles_s": job_throughput(world, a.n, grav_ms), "path": "rcb_gravity alone"},
         "neighbours_gravity_fused": {"ms": fused_ms, "mparticles_s": job_throughput(world, a.n, fused_ms),
                                      "path": "rcb_gravity_neighbours + compaction (the step's path)"},
+        "gravity_backward": {"ms": bwd_ms, "mparticles_s": job_throughput(world, a.n, bwd_ms),
+                             "path": "rcb_gravity_backward on the built tree (lists already transposed)"},
     }
     return fp64, accuracy, e2e, int(idx0.numel()), per_stage
 
