@@ -3,86 +3,31 @@
 // in the paper; the forward it differentiates is Sec. 2.4).  Smoothing lengths are constants.
 //
 // Given v_a = dL/da_a and w_a = dL/dPhi_a (sorted order after a gather):
-//   taylor   per sink: the coefficients C (Eq. 6) are recomputed in FP64; for every particle
+//   taylor   per sink: the coefficients C (Eq. 6) are recomputed; for every particle
 //            dL/dd_a = w grad P(d_a) - Hess P(d_a) v_a goes to x_a and, negated, to the sink's
 //            centre of mass; dL/dC = sum_a (w dP/dC - v . d(grad P)/dC) per sink.
 //   far      per (sink A, far node B): the 20 coefficients are functions of x = COM_A - COM_B,
-//            M_B and Q_B (Eq. 5).  dL/dx comes from the same coefficient code run on dual
-//            numbers (value + 3 partials); dL/dM and dL/dQ from its linearity in M and Q.
-//            dL/dx is added to COM_A's adjoint and subtracted from COM_B's; M_B and Q_B adjoints
-//            accumulate per node (atomic adds).
+//            M_B and Q_B (Eq. 5); one hand-written reverse of that formula gives dL/dx, dL/dM
+//            and dL/dQ.  dL/dx is added to COM_A's adjoint and subtracted from COM_B's; M_B and
+//            Q_B adjoints accumulate per node (atomic adds).
 //   near     pair terms are recomputed (never stored): the sink side pulls over its near list;
 //            the source side pulls over a transposed near list (sinks that list the cell).
-//   nodes    every particle climbs its ancestors and adds the moment adjoints of each node:
-//            M = sum m_b, COM = sum m_b x_b / M, Q = sum m_b (3 d d - d^2 I), d = x_b - COM
-//            (Eq. 1; Eq. 2 reproduces it exactly); Q has no derivative through the COM
-//            because sum m_b d_b = 0.
+//   nodes    a node's adjoints reach the particles below it through a quadratic polynomial of
+//            the particle's position (from M = sum m_b, COM = sum m_b x_b / M,
+//            Q = sum m_b (3 d d - d^2 I), Eq. 1); the polynomials of all ancestors are summed
+//            top-down, re-centred on each node's centre of mass, and evaluated once per particle.
+// The FP64 form runs every step in FP64.  The mixed form takes the float32 coefficients of the
+// mixed forward and runs the Taylor, far and near parts in float32 (compensated per-tile sums in
+// the near part); node adjoints and the polynomials stay FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "far_math.cuh"
 #include "rcb_internal.cuh"
 
 namespace rcb {
-
-// Forward-mode dual number with K partial derivatives (FP64).
-template <int K>
-struct Dual {
-    double v;
-    double d[K];
-    __device__ Dual() {}
-    __device__ Dual(double x) : v(x) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) d[k] = 0.0;
-    }
-};
-template <int K>
-__device__ inline Dual<K> operator+(const Dual<K> &a, const Dual<K> &b) {
-    Dual<K> r;
-    r.v = a.v + b.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k];
-    return r;
-}
-template <int K>
-__device__ inline Dual<K> operator-(const Dual<K> &a, const Dual<K> &b) {
-    Dual<K> r;
-    r.v = a.v - b.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] - b.d[k];
-    return r;
-}
-template <int K>
-__device__ inline Dual<K> operator-(const Dual<K> &a) {
-    Dual<K> r;
-    r.v = -a.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = -a.d[k];
-    return r;
-}
-template <int K>
-__device__ inline Dual<K> operator*(const Dual<K> &a, const Dual<K> &b) {
-    Dual<K> r;
-    r.v = a.v * b.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.v * b.d[k] + b.v * a.d[k];
-    return r;
-}
-template <int K>
-__device__ inline Dual<K> &operator+=(Dual<K> &a, const Dual<K> &b) {
-    a = a + b;
-    return a;
-}
-template <int K>
-__device__ inline Dual<K> rsqrt(const Dual<K> &a) {
-    Dual<K> r;
-    r.v = ::rsqrt(a.v);
-    const double f = -0.5 * r.v * r.v * r.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = f * a.d[k];
-    return r;
-}
 
 namespace {
 
@@ -98,8 +43,12 @@ struct BCtx {
     const int32_t *nfirst, *ncount;
     const double *ncom, *nmass, *nQ;
     const double *px, *py, *pz, *pm, *ph;
+    const float4 *nfar;     // mixed form: per node (COM hi, M), (COM lo, Qxx), (Qxy, Qxz, Qyy, Qyz), (Qzz)
+    const float2 *ncomdf;   // mixed form: double-float centres of mass
+    const float4 *p32;      // mixed form: (x - COM of the particle's leaf, m)
+    const float *h32;
     const int32_t *pidx;
-    const double *coef;     // [nsinks][20] FP64 coefficients (recomputed)
+    const double *coef;     // [nsinks][20] coefficients in the tree's precision (recomputed)
     double *cbar;           // [nsinks][20] dL/dC
     const double *gA, *gP;  // sorted order: [3N], [N]
     double *gxs, *gms;      // sorted-order accumulators
@@ -129,6 +78,61 @@ __global__ void k_bwd_pleaf(BCtx c) {
     for (int s = gw; s < c.nsinks; s += nw) {
         const int A = c.sinks[s];
         for (int p = c.nfirst[A] + lane; p < c.nfirst[A] + c.ncount[A]; p += 32) const_cast<int32_t *>(c.pleaf)[p] = A;
+    }
+}
+
+// Taylor part, mixed form: the same in float32 from the float coefficients and the particle
+// offsets from the sink's centre of mass.
+__global__ void __launch_bounds__(kBW * 32) k_bwd_taylor_mixed(BCtx c, const float *coef32) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int s = gw; s < c.nsinks; s += nw) {
+        const int A = c.sinks[s];
+        const int f = c.nfirst[A], n = c.ncount[A];
+        float C[20];
+#pragma unroll
+        for (int i = 0; i < 20; ++i) C[i] = coef32[(int64_t)s * 20 + i];
+        float cb[20];
+#pragma unroll
+        for (int i = 0; i < 20; ++i) cb[i] = 0.f;
+        float comb[3] = {0.f, 0.f, 0.f};
+        for (int a0 = 0; a0 < n; a0 += 32) {
+            const int a = f + a0 + lane;
+            if (a0 + lane < n) {
+                const float4 pa = c.p32[a];
+                const float v[3] = {(float)c.gA[3 * (int64_t)a], (float)c.gA[3 * (int64_t)a + 1],
+                                    (float)c.gA[3 * (int64_t)a + 2]};
+                const float w = (float)c.gP[a];
+                float g[3], H[6];
+                taylor_grad_hess<float>(C, pa.x, pa.y, pa.z, g, H);
+                const float gd[3] = {w * g[0] - (v[0] * H[0] + v[1] * H[1] + v[2] * H[2]),
+                                     w * g[1] - (v[0] * H[1] + v[1] * H[3] + v[2] * H[4]),
+                                     w * g[2] - (v[0] * H[2] + v[1] * H[4] + v[2] * H[5])};
+                c.gxs[3 * (int64_t)a] = gd[0];
+                c.gxs[3 * (int64_t)a + 1] = gd[1];
+                c.gxs[3 * (int64_t)a + 2] = gd[2];
+                c.gms[a] = 0.0;
+                comb[0] -= gd[0];
+                comb[1] -= gd[1];
+                comb[2] -= gd[2];
+                taylor_cbar<float>(pa.x, pa.y, pa.z, v[0], v[1], v[2], w, cb);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+            for (int i = 0; i < 20; ++i) cb[i] += __shfl_xor_sync(0xffffffffu, cb[i], o);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) comb[k] += __shfl_xor_sync(0xffffffffu, comb[k], o);
+        }
+        if (lane < 20) {
+            float val = cb[0];
+#pragma unroll
+            for (int i = 1; i < 20; ++i)
+                if (lane == i) val = cb[i];
+            c.cbar[(int64_t)s * 20 + lane] = val;
+        }
+        if (lane < 3) atomicAdd(&c.adj[10 * (int64_t)A + 1 + lane], (double)(lane == 0 ? comb[0] : (lane == 1 ? comb[1] : comb[2])));
     }
 }
 
@@ -190,79 +194,182 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_taylor(BCtx c) {
     }
 }
 
-// Far interactions: per sink (warp), lanes over its far nodes.
+// Far interactions: per sink (warp), lanes over its far nodes, by a hand-written reverse of the
+// coefficient formula (far_source).  With P1, P2, P3 the coefficient adjoints spread over the full
+// symmetric tensors (a slot's adjoint divided by its multiplicity), t3_k = P3_iik, T = P3 x,
+// u = T x, v = Q x, s = x.v and the scalars of far_source (a, b, c; d = -105 M g^9 - 3465/2 s g^13
+// continues the sequence),
+//   L = sum cbar.C = M mu + sigma s + nu.v + Q:K,
+//   alpha = P1.x + tr P2,  beta = x.P2 x + 3 t3.x,  gamma = u.x,
+//   mu    = g^3 alpha - 3 g^5 beta + 15 g^7 gamma - cbar_0 g                      (= dL/dM)
+//   sigma = 5/2 g^7 alpha - 35/2 g^9 beta + 315/2 g^11 gamma - cbar_0 g^5 / 2
+//   nu    = -g^5 P1 + 10 g^7 P2 x - 105 g^9 u + 15 g^7 t3,   K = -g^5 P2 + 15 g^7 T,
+//   dL/dQ_ij = sigma x_i x_j + nu_i x_j + K_ij (summed over (i, j) and (j, i) for off-diagonal slots),
+//   dL/dx = x S + a P1 + b (2 P2 x + 3 t3) + 3 c u + 2 sigma v + Q nu + 10 g^7 P2 v - 210 g^9 T v
+//           + 15 g^7 W,   W_k = Q_ij P3_ijk,
+//   S = cbar_0 a + alpha b + beta c + gamma d + 5 g^7 (P1.v + Q:P2) - 70 g^9 v.P2 x
+//       - 105 g^9 (t3.v + Q:T) + 945 g^11 u.v.
+// dL/dx is added to COM_A's adjoint and subtracted from COM_B's; M_B and Q_B adjoints accumulate
+// per node (FP64 atomic adds).  The mixed form reads the offsets from the double-float node
+// records as the forward does and computes in float32.
+template <typename T>
+struct FarCbar {
+    T cb0, P1[3], p2xx, p2xy, p2xz, p2yy, p2yz, p2zz, p3[10], t3[3], trP2;
+    __device__ explicit FarCbar(const double *cbs) {
+        cb0 = (T)cbs[0];
+        P1[0] = (T)cbs[1];
+        P1[1] = (T)cbs[2];
+        P1[2] = (T)cbs[3];
+        // slots xx, xy, xz, yy, yz, zz
+        p2xx = (T)cbs[4];
+        p2xy = T(0.5) * (T)cbs[5];
+        p2xz = T(0.5) * (T)cbs[6];
+        p2yy = (T)cbs[7];
+        p2yz = T(0.5) * (T)cbs[8];
+        p2zz = (T)cbs[9];
+        // slots xxx, xxy, xxz, xyy, xyz, xzz, yyy, yyz, yzz, zzz (multiplicities 1 3 3 3 6 3 1 3 3 1)
+        const T mult[10] = {T(1), T(3), T(3), T(3), T(6), T(3), T(1), T(3), T(3), T(1)};
+#pragma unroll
+        for (int i = 0; i < 10; ++i) p3[i] = (T)cbs[10 + i] / mult[i];
+        t3[0] = p3[0] + p3[3] + p3[5];
+        t3[1] = p3[1] + p3[6] + p3[8];
+        t3[2] = p3[2] + p3[7] + p3[9];
+        trP2 = p2xx + p2yy + p2zz;
+    }
+};
+
+template <typename T>
+__device__ inline T rsqrt_t(T x);
+template <>
+__device__ inline float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ inline double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+// Adjoints of one (sink, far node) pair: mu = dL/dM, q = dL/dQ slots, gx = dL/dx.
+template <typename T>
+__device__ inline void far_adjoint(const FarCbar<T> &P, T x0, T x1, T x2, T M, T Qxx, T Qxy, T Qxz, T Qyy, T Qyz,
+                                   T Qzz, T &mu, T q[6], T gx[3]) {
+    const T rr = x0 * x0 + x1 * x1 + x2 * x2;
+    const T g = rsqrt_t(rr), g2 = g * g, g3 = g * g2, g5 = g3 * g2, g7 = g5 * g2, g9 = g7 * g2, g11 = g9 * g2;
+    const T v0 = Qxx * x0 + Qxy * x1 + Qxz * x2, v1 = Qxy * x0 + Qyy * x1 + Qyz * x2,
+            v2 = Qxz * x0 + Qyz * x1 + Qzz * x2;
+    const T sv = x0 * v0 + x1 * v1 + x2 * v2;
+    const T gs = sv * g2;  // s g^2 keeps s g^13 = (s g^2) g^11 in range
+    const T *p3 = P.p3;
+    // T = P3 x (symmetric), u = T x, gamma = u.x
+    const T Txx = p3[0] * x0 + p3[1] * x1 + p3[2] * x2, Txy = p3[1] * x0 + p3[3] * x1 + p3[4] * x2,
+            Txz = p3[2] * x0 + p3[4] * x1 + p3[5] * x2, Tyy = p3[3] * x0 + p3[6] * x1 + p3[7] * x2,
+            Tyz = p3[4] * x0 + p3[7] * x1 + p3[8] * x2, Tzz = p3[5] * x0 + p3[8] * x1 + p3[9] * x2;
+    const T u0 = Txx * x0 + Txy * x1 + Txz * x2, u1 = Txy * x0 + Tyy * x1 + Tyz * x2,
+            u2 = Txz * x0 + Tyz * x1 + Tzz * x2;
+    const T gam = u0 * x0 + u1 * x1 + u2 * x2;
+    const T w0 = P.p2xx * x0 + P.p2xy * x1 + P.p2xz * x2, w1 = P.p2xy * x0 + P.p2yy * x1 + P.p2yz * x2,
+            w2 = P.p2xz * x0 + P.p2yz * x1 + P.p2zz * x2;  // P2 x
+    const T alpha = P.P1[0] * x0 + P.P1[1] * x1 + P.P1[2] * x2 + P.trP2;
+    const T beta = w0 * x0 + w1 * x1 + w2 * x2 + T(3) * (P.t3[0] * x0 + P.t3[1] * x1 + P.t3[2] * x2);
+    const T a = M * g3 + T(2.5) * gs * g5, b = T(-3) * M * g5 - T(17.5) * gs * g7,
+            cc = T(15) * M * g7 + T(157.5) * gs * g9, d = T(-105) * M * g9 - T(1732.5) * gs * g11;
+    mu = g3 * alpha - T(3) * g5 * beta + T(15) * g7 * gam - P.cb0 * g;
+    const T sig = T(2.5) * g7 * alpha - T(17.5) * g9 * beta + T(157.5) * g11 * gam - T(0.5) * P.cb0 * g5;
+    const T e7 = T(15) * g7, e9 = T(-105) * g9, e7b = T(10) * g7;
+    const T n0 = -g5 * P.P1[0] + e7b * w0 + e9 * u0 + e7 * P.t3[0];
+    const T n1 = -g5 * P.P1[1] + e7b * w1 + e9 * u1 + e7 * P.t3[1];
+    const T n2 = -g5 * P.P1[2] + e7b * w2 + e9 * u2 + e7 * P.t3[2];
+    const T Kxx = -g5 * P.p2xx + e7 * Txx, Kxy = -g5 * P.p2xy + e7 * Txy, Kxz = -g5 * P.p2xz + e7 * Txz,
+            Kyy = -g5 * P.p2yy + e7 * Tyy, Kyz = -g5 * P.p2yz + e7 * Tyz, Kzz = -g5 * P.p2zz + e7 * Tzz;
+    q[0] = sig * x0 * x0 + n0 * x0 + Kxx;
+    q[1] = T(2) * sig * x0 * x1 + n0 * x1 + n1 * x0 + T(2) * Kxy;
+    q[2] = T(2) * sig * x0 * x2 + n0 * x2 + n2 * x0 + T(2) * Kxz;
+    q[3] = sig * x1 * x1 + n1 * x1 + Kyy;
+    q[4] = T(2) * sig * x1 * x2 + n1 * x2 + n2 * x1 + T(2) * Kyz;
+    q[5] = sig * x2 * x2 + n2 * x2 + Kzz;
+    const T QP2 = Qxx * P.p2xx + Qyy * P.p2yy + Qzz * P.p2zz + T(2) * (Qxy * P.p2xy + Qxz * P.p2xz + Qyz * P.p2yz);
+    const T QT = Qxx * Txx + Qyy * Tyy + Qzz * Tzz + T(2) * (Qxy * Txy + Qxz * Txz + Qyz * Tyz);
+    const T P1v = P.P1[0] * v0 + P.P1[1] * v1 + P.P1[2] * v2;
+    const T vw = v0 * w0 + v1 * w1 + v2 * w2;
+    const T t3v = P.t3[0] * v0 + P.t3[1] * v1 + P.t3[2] * v2;
+    const T uv = u0 * v0 + u1 * v1 + u2 * v2;
+    const T S = P.cb0 * a + alpha * b + beta * cc + gam * d + T(5) * g7 * (P1v + QP2) - T(70) * g9 * vw +
+                e9 * (t3v + QT) + T(945) * g11 * uv;
+    const T W0 = Qxx * p3[0] + Qyy * p3[3] + Qzz * p3[5] + T(2) * (Qxy * p3[1] + Qxz * p3[2] + Qyz * p3[4]);
+    const T W1 = Qxx * p3[1] + Qyy * p3[6] + Qzz * p3[8] + T(2) * (Qxy * p3[3] + Qxz * p3[4] + Qyz * p3[7]);
+    const T W2 = Qxx * p3[2] + Qyy * p3[7] + Qzz * p3[9] + T(2) * (Qxy * p3[4] + Qxz * p3[5] + Qyz * p3[8]);
+    const T P2v0 = P.p2xx * v0 + P.p2xy * v1 + P.p2xz * v2, P2v1 = P.p2xy * v0 + P.p2yy * v1 + P.p2yz * v2,
+            P2v2 = P.p2xz * v0 + P.p2yz * v1 + P.p2zz * v2;
+    const T Tv0 = Txx * v0 + Txy * v1 + Txz * v2, Tv1 = Txy * v0 + Tyy * v1 + Tyz * v2,
+            Tv2 = Txz * v0 + Tyz * v1 + Tzz * v2;
+    const T Qn0 = Qxx * n0 + Qxy * n1 + Qxz * n2, Qn1 = Qxy * n0 + Qyy * n1 + Qyz * n2,
+            Qn2 = Qxz * n0 + Qyz * n1 + Qzz * n2;
+    const T c3 = T(3) * cc, s2 = T(2) * sig, f10 = T(10) * g7, f210 = T(-210) * g9;
+    gx[0] = x0 * S + a * P.P1[0] + b * (T(2) * w0 + T(3) * P.t3[0]) + c3 * u0 + s2 * v0 + Qn0 + f10 * P2v0 +
+            f210 * Tv0 + e7 * W0;
+    gx[1] = x1 * S + a * P.P1[1] + b * (T(2) * w1 + T(3) * P.t3[1]) + c3 * u1 + s2 * v1 + Qn1 + f10 * P2v1 +
+            f210 * Tv1 + e7 * W1;
+    gx[2] = x2 * S + a * P.P1[2] + b * (T(2) * w2 + T(3) * P.t3[2]) + c3 * u2 + s2 * v2 + Qn2 + f10 * P2v2 +
+            f210 * Tv2 + e7 * W2;
+}
+
+template <bool MIXED>
 __global__ void __launch_bounds__(kBW * 32) k_bwd_far(BCtx c) {
+    using T = typename std::conditional<MIXED, float, double>::type;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int s = gw; s < c.nsinks; s += nw) {
         const int A = c.sinks[s];
         const int nf = c.far_n[s];
-        double cb[20];
+        const FarCbar<T> P(c.cbar + (int64_t)s * 20);
+        float4 ah = make_float4(0.f, 0.f, 0.f, 0.f), al = ah;
+        double cA[3] = {0.0, 0.0, 0.0};
+        if (MIXED) {
+            ah = c.nfar[4 * (int64_t)A];
+            al = c.nfar[4 * (int64_t)A + 1];
+        } else {
 #pragma unroll
-        for (int i = 0; i < 20; ++i) cb[i] = c.cbar[(int64_t)s * 20 + i];
-        const double cA[3] = {c.ncom[3 * (int64_t)A], c.ncom[3 * (int64_t)A + 1], c.ncom[3 * (int64_t)A + 2]};
-        double RA[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < 3; ++k) cA[k] = c.ncom[3 * (int64_t)A + k];
+        }
+        T RA[3] = {T(0), T(0), T(0)};
         for (int k = lane; k < nf; k += 32) {
             const int B = c.far_list[(int64_t)s * c.cap_far + k];
-            const double x[3] = {cA[0] - c.ncom[3 * (int64_t)B], cA[1] - c.ncom[3 * (int64_t)B + 1],
-                                 cA[2] - c.ncom[3 * (int64_t)B + 2]};
-            double q6[6];
+            T x0, x1, x2, M, Q[6];
+            if (MIXED) {
+                const float4 r0 = c.nfar[4 * (int64_t)B], r1 = c.nfar[4 * (int64_t)B + 1],
+                             r2 = c.nfar[4 * (int64_t)B + 2], r3 = c.nfar[4 * (int64_t)B + 3];
+                x0 = (ah.x - r0.x) + (al.x - r1.x);
+                x1 = (ah.y - r0.y) + (al.y - r1.y);
+                x2 = (ah.z - r0.z) + (al.z - r1.z);
+                M = r0.w;
+                Q[0] = r1.w;
+                Q[1] = r2.x;
+                Q[2] = r2.y;
+                Q[3] = r2.z;
+                Q[4] = r2.w;
+                Q[5] = r3.x;
+            } else {
+                x0 = cA[0] - c.ncom[3 * (int64_t)B];
+                x1 = cA[1] - c.ncom[3 * (int64_t)B + 1];
+                x2 = cA[2] - c.ncom[3 * (int64_t)B + 2];
+                M = c.nmass[B];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) q6[q] = c.nQ[6 * (int64_t)B + q];
-            const double M = c.nmass[B];
-            // dL/dx by dual numbers
-            Dual<3> xd[3], Qd[6], Cd[20];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                xd[i] = Dual<3>(x[i]);
-                xd[i].d[i] = 1.0;
+                for (int qq = 0; qq < 6; ++qq) Q[qq] = c.nQ[6 * (int64_t)B + qq];
             }
+            T mu, qa[6], gx[3];
+            far_adjoint<T>(P, x0, x1, x2, M, Q[0], Q[1], Q[2], Q[3], Q[4], Q[5], mu, qa, gx);
+            RA[0] += gx[0];
+            RA[1] += gx[1];
+            RA[2] += gx[2];
+            double *aB = c.adj + 10 * (int64_t)B;
+            atomicAdd(aB, (double)mu);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) Qd[q] = Dual<3>(q6[q]);
+            for (int k2 = 0; k2 < 3; ++k2) atomicAdd(aB + 1 + k2, -(double)gx[k2]);
 #pragma unroll
-            for (int i = 0; i < 20; ++i) Cd[i] = Dual<3>(0.0);
-            far_source<Dual<3>>(xd, Dual<3>(M), Qd, Cd);
-            double Rb[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-            for (int i = 0; i < 20; ++i)
-#pragma unroll
-                for (int k2 = 0; k2 < 3; ++k2) Rb[k2] += cb[i] * Cd[i].d[k2];
-            // dL/dM and dL/dQ: the coefficients are linear in M and in the stored Q slots
-            double basis[20];
-            const double zero6[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-            for (int i = 0; i < 20; ++i) basis[i] = 0.0;
-            far_source<double>(x, 1.0, zero6, basis);
-            double Mb = 0.0;
-#pragma unroll
-            for (int i = 0; i < 20; ++i) Mb += cb[i] * basis[i];
-            atomicAdd(&c.adj[10 * (int64_t)B], Mb);
-#pragma unroll 1
-            for (int q = 0; q < 6; ++q) {
-                double e6[6] = {0, 0, 0, 0, 0, 0};
-                e6[q] = 1.0;
-#pragma unroll
-                for (int i = 0; i < 20; ++i) basis[i] = 0.0;
-                far_source<double>(x, 0.0, e6, basis);
-                double Qb = 0.0;
-#pragma unroll
-                for (int i = 0; i < 20; ++i) Qb += cb[i] * basis[i];
-                atomicAdd(&c.adj[10 * (int64_t)B + 4 + q], Qb);
-            }
-#pragma unroll
-            for (int k2 = 0; k2 < 3; ++k2) {
-                RA[k2] += Rb[k2];
-                atomicAdd(&c.adj[10 * (int64_t)B + 1 + k2], -Rb[k2]);
-            }
+            for (int qq = 0; qq < 6; ++qq) atomicAdd(aB + 4 + qq, (double)qa[qq]);
         }
+        double R[3] = {RA[0], RA[1], RA[2]};
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1)
 #pragma unroll
-            for (int k2 = 0; k2 < 3; ++k2) RA[k2] += __shfl_xor_sync(0xffffffffu, RA[k2], o);
-        if (lane < 3) {
-            const double val = lane == 0 ? RA[0] : (lane == 1 ? RA[1] : RA[2]);
-            atomicAdd(&c.adj[10 * (int64_t)A + 1 + lane], val);
-        }
+            for (int k2 = 0; k2 < 3; ++k2) R[k2] += __shfl_xor_sync(0xffffffffu, R[k2], o);
+        if (lane < 3) atomicAdd(&c.adj[10 * (int64_t)A + 1 + lane], lane == 0 ? R[0] : (lane == 1 ? R[1] : R[2]));
     }
 }
 
@@ -430,6 +537,234 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_near(BCtx c) {
     }
 }
 
+// ------------------------------------------------------------------------------ near (mixed)
+// The pair gradient of pair_grad in float32: 2 / (h_a + h_b) and 3 / q by the fast reciprocal
+// (3 / q = 3/2 (h_a + h_b) / r), 1 / r by rsqrtf.
+__device__ inline void pair_grad32(float dx, float dy, float dz, float hsum, float mb, float vx, float vy, float vz,
+                                   float w, float &gx, float &gy, float &gz, float &gm) {
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float r = r2 * rinv;
+    const float hinv = __fdividef(2.0f, hsum);
+    const float q = r * hinv;
+    const float rinv2 = rinv * rinv;
+    float sr = rinv * rinv2;
+    float dsr = -3.f * sr * rinv2;
+    float p = -rinv;
+    if (q < 2.f) {
+        const float h2 = hinv * hinv, h3 = h2 * hinv, h5 = h3 * h2;
+        const float q2 = q * q;
+        if (q < 1.f) {
+            sr = h3 * (4.0f / 3.0f + q2 * (-1.2f + 0.5f * q));
+            dsr = h5 * (-2.4f + 1.5f * q);
+            p = hinv * (q2 * (2.0f / 3.0f + q2 * (-0.3f + 0.1f * q)) - 1.4f);
+        } else {
+            const float r3 = sr;
+            sr = h3 * (8.0f / 3.0f + q * (-3.f + q * (1.2f - q * (1.0f / 6.0f)))) - (1.0f / 15.0f) * r3;
+            dsr = h5 * (-1.5f * hsum * rinv + 2.4f - 0.5f * q) + 0.2f * r3 * rinv2;
+            p = hinv * (q2 * (4.0f / 3.0f + q * (-1.f + q * (0.3f - q * (1.0f / 30.0f)))) - 1.6f) +
+                (1.0f / 15.0f) * rinv;
+        }
+    }
+    const float rv = dx * vx + dy * vy + dz * vz;
+    const float k1 = mb * sr, k2 = mb * dsr * rv, k3 = w * mb * sr;
+    gx = k3 * dx - (k1 * vx + k2 * dx);
+    gy = k3 * dy - (k1 * vy + k2 * dy);
+    gz = k3 * dz - (k1 * vz + k2 * dz);
+    gm = w * p - sr * rv;
+}
+
+constexpr int kMTile = 384;   // staged particles per warp (mixed)
+constexpr int kMGroup = 8;    // own particles per pass (mixed)
+
+// Per-warp staging.  SIDE 0 (sources b): a = (x, y, z, m_b), hb = h_b.  SIDE 1 (sink particles a):
+// a = (x, y, z, h_a), v = (dL/da_a, dL/dPhi_a).  Positions relative to the own cell's centre of mass.
+struct BNearSmem {
+    float4 a[kMTile];
+    float4 v[kMTile];
+    float hb[kMTile];
+    int32_t id[kMTile];
+    static constexpr size_t bytes = (size_t)kMTile * (2 * sizeof(float4) + sizeof(float) + sizeof(int32_t));
+};
+
+// Stage slots [t0, t0 + kMTile) of the concatenated cells; one lane per slot.
+template <int SIDE, typename CellAt>
+__device__ int stage_cells_mixed(const BCtx &c, int ncells, CellAt cell_at, int64_t t0, float2 cO[3],
+                                 BNearSmem &sm) {
+    const int lane = threadIdx.x & 31;
+    int64_t pos = 0;
+    int staged = 0;
+    for (int k0 = 0; k0 < ncells; k0 += 32) {
+        const int k = k0 + lane;
+        int f = 0, n = 0;
+        float ox = 0.f, oy = 0.f, oz = 0.f;
+        if (k < ncells) {
+            const int B = cell_at(k);
+            f = c.nfirst[B];
+            n = c.ncount[B];
+            const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1],
+                         b2 = c.ncomdf[3 * (int64_t)B + 2];
+            ox = (b0.x - cO[0].x) + (b0.y - cO[0].y);
+            oy = (b1.x - cO[1].x) + (b1.y - cO[1].y);
+            oz = (b2.x - cO[2].x) + (b2.y - cO[2].y);
+        }
+        const int excl = warp_excl_scan(n);
+        const int total = __shfl_sync(0xffffffffu, excl + n, 31);
+        const int64_t lo = pos > t0 ? pos : t0;
+        const int64_t hi = pos + total < t0 + kMTile ? pos + total : t0 + kMTile;
+        for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+            const int j = warp_run_of(excl, n, (int)(r0 - pos));
+            const int jf = __shfl_sync(0xffffffffu, f, j & 31), je = __shfl_sync(0xffffffffu, excl, j & 31);
+            const float bx = __shfl_sync(0xffffffffu, ox, j & 31), by = __shfl_sync(0xffffffffu, oy, j & 31),
+                        bz = __shfl_sync(0xffffffffu, oz, j & 31);
+            const int64_t q = r0 + lane;
+            if (q < hi) {
+                const int b = jf + (int)(q - pos) - je;
+                const int slot = (int)(q - t0);
+                const float4 pb = c.p32[b];
+                if (SIDE == 0) {
+                    sm.a[slot] = make_float4(pb.x + bx, pb.y + by, pb.z + bz, pb.w);
+                    sm.hb[slot] = c.h32[b];
+                } else {
+                    sm.a[slot] = make_float4(pb.x + bx, pb.y + by, pb.z + bz, c.h32[b]);
+                    sm.v[slot] = make_float4((float)c.gA[3 * (int64_t)b], (float)c.gA[3 * (int64_t)b + 1],
+                                             (float)c.gA[3 * (int64_t)b + 2], (float)c.gP[b]);
+                }
+                sm.id[slot] = b;
+            }
+        }
+        if (hi > lo) staged = (int)(hi - t0);
+        pos += total;
+        if (pos >= t0 + kMTile) break;
+    }
+    __syncwarp();
+    return staged;
+}
+
+// SIDE 0: sink side, a in the sink, b over the near cells: gxs[a] += g.
+// SIDE 1: source side, b in a leaf, a over the sink particles listing it: gxs[b] -= g, gms[b] += gm.
+// Per tile the float32 sums fold into compensated (sum, error) pairs; lanes reduce at the end.
+template <int SIDE>
+__global__ void __launch_bounds__(kBW * 32, 2) k_bwd_near_mixed(BCtx c) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    BNearSmem &sm = *reinterpret_cast<BNearSmem *>(smem_raw + (size_t)w * BNearSmem::bytes);
+    constexpr int NQ = SIDE == 0 ? 3 : 4;
+    const int nunits = SIDE == 0 ? c.nsinks : (int)c.nleaves;
+    for (int u = blockIdx.x * kBW + w; u < nunits; u += gridDim.x * kBW) {
+        int own, ncells = 0;
+        int64_t list0 = 0;
+        int nr = 0;
+        if (SIDE == 0) {
+            own = c.sinks[u];
+            nr = c.near_nr[u];
+            ncells = nr + c.near_nn[u];
+            list0 = (int64_t)u * c.cap_near;
+        } else {
+            own = (int)c.nleaves + u;
+            if (c.ncount[own] == 0) continue;
+            list0 = c.tnear_off[u];
+            ncells = c.tnear_off[u + 1] - c.tnear_off[u];
+        }
+        auto cell_at = [&](int k) -> int {
+            if (SIDE == 0) return k < nr ? c.near_list[list0 + k] : c.near_list[list0 + c.cap_near - 1 - (k - nr)];
+            return c.sinks[c.tnear_sink[list0 + k]];
+        };
+        float2 cO[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cO[d] = c.ncomdf[3 * (int64_t)own + d];
+        int64_t S = 0;
+        for (int k = lane; k < ncells; k += 32) S += c.ncount[cell_at(k)];
+        for (int o = 16; o >= 1; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+        const int f = c.nfirst[own], n = c.ncount[own];
+        for (int p0 = 0; p0 < n; p0 += kMGroup) {
+            const int np = min(kMGroup, n - p0);
+            float ox[kMGroup], oy[kMGroup], oz[kMGroup], oh[kMGroup], om[kMGroup], ovx[kMGroup], ovy[kMGroup],
+                ovz[kMGroup], ow[kMGroup];
+            int oid[kMGroup];
+#pragma unroll
+            for (int i = 0; i < kMGroup; ++i) {
+                const int p = f + p0 + min(i, np - 1);
+                const float4 pp = c.p32[p];
+                ox[i] = pp.x;
+                oy[i] = pp.y;
+                oz[i] = pp.z;
+                om[i] = pp.w;
+                oh[i] = c.h32[p];
+                if (SIDE == 0) {
+                    ovx[i] = (float)c.gA[3 * (int64_t)p];
+                    ovy[i] = (float)c.gA[3 * (int64_t)p + 1];
+                    ovz[i] = (float)c.gA[3 * (int64_t)p + 2];
+                    ow[i] = (float)c.gP[p];
+                }
+                oid[i] = i < np ? p : -1;
+            }
+            float cs[NQ * kMGroup], ce[NQ * kMGroup];
+#pragma unroll
+            for (int i = 0; i < NQ * kMGroup; ++i) cs[i] = ce[i] = 0.f;
+            for (int64_t t0 = 0; t0 < S; t0 += kMTile) {
+                const int ns = stage_cells_mixed<SIDE>(c, ncells, cell_at, t0, cO, sm);
+                float acc[NQ * kMGroup];
+#pragma unroll
+                for (int i = 0; i < NQ * kMGroup; ++i) acc[i] = 0.f;
+                for (int j = lane; j < ns; j += 32) {
+                    const float4 ja = sm.a[j];
+                    const int jid = sm.id[j];
+                    if (SIDE == 0) {
+                        const float jh = sm.hb[j];
+#pragma unroll
+                        for (int i = 0; i < kMGroup; ++i) {
+                            float gx, gy, gz, gmv;
+                            pair_grad32(ox[i] - ja.x, oy[i] - ja.y, oz[i] - ja.z, oh[i] + jh, ja.w, ovx[i], ovy[i],
+                                        ovz[i], ow[i], gx, gy, gz, gmv);
+                            if (jid != oid[i]) {
+                                acc[3 * i] += gx;
+                                acc[3 * i + 1] += gy;
+                                acc[3 * i + 2] += gz;
+                            }
+                        }
+                    } else {
+                        const float4 jv = sm.v[j];
+#pragma unroll
+                        for (int i = 0; i < kMGroup; ++i) {
+                            float gx, gy, gz, gmv;
+                            pair_grad32(ja.x - ox[i], ja.y - oy[i], ja.z - oz[i], ja.w + oh[i], om[i], jv.x, jv.y, jv.z,
+                                        jv.w, gx, gy, gz, gmv);
+                            if (jid != oid[i]) {
+                                acc[4 * i] -= gx;
+                                acc[4 * i + 1] -= gy;
+                                acc[4 * i + 2] -= gz;
+                                acc[4 * i + 3] += gmv;
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < NQ * kMGroup; ++i) comp_add(cs[i], ce[i], acc[i]);
+                __syncwarp();
+            }
+            // lanes reduce; lane l ends with quantity l (of NQ * kMGroup <= 32)
+            float V[32], E[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                V[i] = i < NQ * kMGroup ? cs[i] : 0.f;
+                E[i] = i < NQ * kMGroup ? ce[i] : 0.f;
+            }
+            reduce_scatter_df<32>(V, E);
+            const double tot = (double)V[0] + (double)E[0];
+            if (lane < NQ * np) {
+                const int i = lane / NQ, qq = lane - NQ * i;
+                const int p = f + p0 + i;
+                if (qq < 3)
+                    c.gxs[3 * (int64_t)p + qq] += tot;
+                else
+                    c.gms[p] += tot;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Transposed near list: for every ll-cell B, the sinks whose near list holds B.
 __global__ void k_tnear_count(BCtx c, int32_t *cnt) {
     const int lane = threadIdx.x & 31;
@@ -474,44 +809,62 @@ __global__ void k_tnear_sort(const int32_t *off, int64_t nleaves, int32_t *rows)
     }
 }
 
-// Node adjoints to particles (climb), then scatter to original order.
-__global__ void k_bwd_nodes(BCtx c) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.N; p += (int64_t)gridDim.x * blockDim.x) {
-        const double x[3] = {c.px[p], c.py[p], c.pz[p]};
-        const double mb = c.pm[p];
-        double gx[3] = {c.gxs[3 * p], c.gxs[3 * p + 1], c.gxs[3 * p + 2]};
-        double gm = c.gms[p];
-        for (int n = c.pleaf[p]; n >= 1; n >>= 1) {
-            const double *a = c.adj + 10 * (int64_t)n;
-            const double Mb = a[0];
-            const double Cb[3] = {a[1], a[2], a[3]};
-            const double Qb[6] = {a[4], a[5], a[6], a[7], a[8], a[9]};
-            bool nz = Mb != 0.0 || Cb[0] != 0.0 || Cb[1] != 0.0 || Cb[2] != 0.0;
+// Node adjoints to particles.  Node n's adjoints (M, COM, Q) reach a particle b below it as
+//   dL/dm_b += phi_n(x_b),  dL/dx_b += m_b grad phi_n(x_b),
+//   phi_n(x) = Mbar + COMbar.d / M + Qbar:(3 d d - d^2 I),  d = x - COM_n
+// (M = sum m_b, COM = sum m_b x_b / M, Q = sum m_b (3 d d - d^2 I), Eq. 1; Q has no derivative
+// through the COM because sum m_b d_b = 0).  phi_n is a quadratic polynomial, so the sum over a
+// particle's ancestors is one quadratic Phi per node, built top-down a level at a time:
+// Phi_n = phi_n + Phi_parent re-centred on COM_n.  adj[10 n] is overwritten with Phi_n as
+// (c0, c1[3], C2 slots xx, xy, xz, yy, yz, zz) with Phi(x) = c0 + c1.d + d.C2 d.
+__global__ void k_bwd_phi_level(BCtx c, int level) {
+    const int64_t n0 = (int64_t)1 << level, n1 = n0 << 1;
+    for (int64_t n = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < n1; n += (int64_t)gridDim.x * blockDim.x) {
+        double *a = c.adj + 10 * n;
+        if (c.ncount[n] == 0) {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) nz = nz || Qb[q] != 0.0;
-            if (!nz) continue;
-            const double M = c.nmass[n];
-            double d[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) d[k] = x[k] - c.ncom[3 * (int64_t)n + k];
-            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            gm += Mb + (Cb[0] * d[0] + Cb[1] * d[1] + Cb[2] * d[2]) / M;
-            // slots xx, xy, xz, yy, yz, zz of Q = sum m (3 d d - d^2 I):
-            //   dQ_ij/dm = 3 d_i d_j - d^2 d_ij
-            //   dQ_ij/dx_k = m (3 (d_ik d_j + d_i d_jk) - 2 d_k d_ij)
-            gm += Qb[0] * (3.0 * d[0] * d[0] - d2) + Qb[1] * 3.0 * d[0] * d[1] + Qb[2] * 3.0 * d[0] * d[2] +
-                  Qb[3] * (3.0 * d[1] * d[1] - d2) + Qb[4] * 3.0 * d[1] * d[2] + Qb[5] * (3.0 * d[2] * d[2] - d2);
-            const double tr = Qb[0] + Qb[3] + Qb[5];
-            gx[0] += mb * (6.0 * Qb[0] * d[0] + 3.0 * Qb[1] * d[1] + 3.0 * Qb[2] * d[2] - 2.0 * tr * d[0]);
-            gx[1] += mb * (3.0 * Qb[1] * d[0] + 6.0 * Qb[3] * d[1] + 3.0 * Qb[4] * d[2] - 2.0 * tr * d[1]);
-            gx[2] += mb * (3.0 * Qb[2] * d[0] + 3.0 * Qb[4] * d[1] + 6.0 * Qb[5] * d[2] - 2.0 * tr * d[2]);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) gx[k] += Cb[k] * mb / M;
+            for (int q = 0; q < 10; ++q) a[q] = 0.0;
+            continue;
         }
+        const double M = c.nmass[n];
+        const double tr = a[4] + a[7] + a[9];
+        double P[10] = {a[0],          a[1] / M,      a[2] / M,      a[3] / M,      3.0 * a[4] - tr,
+                        1.5 * a[5],    1.5 * a[6],    3.0 * a[7] - tr, 1.5 * a[8],  3.0 * a[9] - tr};
+        if (level > 0) {
+            const int64_t p = n >> 1;
+            const double *q = c.adj + 10 * p;
+            const double e[3] = {c.ncom[3 * n] - c.ncom[3 * p], c.ncom[3 * n + 1] - c.ncom[3 * p + 1],
+                                 c.ncom[3 * n + 2] - c.ncom[3 * p + 2]};
+            const double Ce[3] = {q[4] * e[0] + q[5] * e[1] + q[6] * e[2], q[5] * e[0] + q[7] * e[1] + q[8] * e[2],
+                                  q[6] * e[0] + q[8] * e[1] + q[9] * e[2]};
+            P[0] += q[0] + q[1] * e[0] + q[2] * e[1] + q[3] * e[2] + (Ce[0] * e[0] + Ce[1] * e[1] + Ce[2] * e[2]);
+            P[1] += q[1] + 2.0 * Ce[0];
+            P[2] += q[2] + 2.0 * Ce[1];
+            P[3] += q[3] + 2.0 * Ce[2];
+#pragma unroll
+            for (int k = 4; k < 10; ++k) P[k] += q[k];
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) a[q] = P[q];
+    }
+}
+
+// Evaluate the sink's Phi at every particle, add the particle's own terms and scatter to
+// original order.
+__global__ void k_bwd_particles(BCtx c) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.N; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = c.pleaf[p];
+        const double *q = c.adj + 10 * n;
+        const double d[3] = {c.px[p] - c.ncom[3 * n], c.py[p] - c.ncom[3 * n + 1], c.pz[p] - c.ncom[3 * n + 2]};
+        const double Cd[3] = {q[4] * d[0] + q[5] * d[1] + q[6] * d[2], q[5] * d[0] + q[7] * d[1] + q[8] * d[2],
+                              q[6] * d[0] + q[8] * d[1] + q[9] * d[2]};
+        const double mb = c.pm[p];
+        const double gm = c.gms[p] + (q[0] + q[1] * d[0] + q[2] * d[1] + q[3] * d[2] +
+                                      (Cd[0] * d[0] + Cd[1] * d[1] + Cd[2] * d[2]));
         const int64_t o = c.pidx[p];
-        c.gx[3 * o] = gx[0];
-        c.gx[3 * o + 1] = gx[1];
-        c.gx[3 * o + 2] = gx[2];
+        c.gx[3 * o] = c.gxs[3 * p] + mb * (q[1] + 2.0 * Cd[0]);
+        c.gx[3 * o + 1] = c.gxs[3 * p + 1] + mb * (q[2] + 2.0 * Cd[1]);
+        c.gx[3 * o + 2] = c.gxs[3 * p + 2] + mb * (q[3] + 2.0 * Cd[2]);
         c.gm[o] = gm;
     }
 }
@@ -529,7 +882,7 @@ int sm_count_b() {
 
 }  // namespace
 
-int far_coefficients_fp64(rcb_tree *t);  // gravity.cu
+int far_coefficients(rcb_tree *t);  // gravity.cu
 
 int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double *gx, double *gm) {
     cudaStream_t st = t->stream;
@@ -585,6 +938,10 @@ int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double
     c.pz = t->pz;
     c.pm = t->pm;
     c.ph = t->ph;
+    c.nfar = t->nfar;
+    c.ncomdf = t->ncomdf;
+    c.p32 = t->p32;
+    c.h32 = t->h32;
     c.pidx = t->pidx;
     c.coef = t->coef;
     c.cbar = cbar;
@@ -620,19 +977,36 @@ int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double
         RCB_CUDA_TRY(cudaGetLastError());
         t->bwd_valid = 1;
     }
-    int rc = far_coefficients_fp64(t);
+    int rc = far_coefficients(t);
     if (rc) return rc;
     RCB_CUDA_TRY(cudaMemsetAsync(adj, 0, (size_t)nn * 10 * sizeof(double), st));
     k_bwd_gather<<<gridp, 256, 0, st>>>(c); note_launch();
-    k_bwd_taylor<<<gridw, kBW * 32, 0, st>>>(c); note_launch();
-    k_bwd_far<<<gridw, kBW * 32, 0, st>>>(c); note_launch();
-    const size_t smem = kBW * kBSmemPerWarp;
-    RCB_CUDA_TRY(cudaFuncSetAttribute(k_bwd_near<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RCB_CUDA_TRY(cudaFuncSetAttribute(k_bwd_near<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bwd_near<0><<<gridw, kBW * 32, smem, st>>>(c); note_launch();
+    if (t->params.precision == RCB_MIXED) {
+        k_bwd_taylor_mixed<<<gridw, kBW * 32, 0, st>>>(c, t->coef32); note_launch();
+    } else {
+        k_bwd_taylor<<<gridw, kBW * 32, 0, st>>>(c); note_launch();
+    }
     const int gridl = (int)std::max<int64_t>(1, std::min<int64_t>((nl + kBW - 1) / kBW, (int64_t)nsm * 16));
-    k_bwd_near<1><<<gridl, kBW * 32, smem, st>>>(c); note_launch();
-    k_bwd_nodes<<<gridp, 256, 0, st>>>(c); note_launch();
+    if (t->params.precision == RCB_MIXED) {
+        k_bwd_far<true><<<gridw, kBW * 32, 0, st>>>(c); note_launch();
+        const size_t smem = kBW * BNearSmem::bytes;
+        RCB_CUDA_TRY(cudaFuncSetAttribute(k_bwd_near_mixed<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RCB_CUDA_TRY(cudaFuncSetAttribute(k_bwd_near_mixed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_bwd_near_mixed<0><<<gridw, kBW * 32, smem, st>>>(c); note_launch();
+        k_bwd_near_mixed<1><<<gridl, kBW * 32, smem, st>>>(c); note_launch();
+    } else {
+        k_bwd_far<false><<<gridw, kBW * 32, 0, st>>>(c); note_launch();
+        const size_t smem = kBW * kBSmemPerWarp;
+        RCB_CUDA_TRY(cudaFuncSetAttribute(k_bwd_near<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RCB_CUDA_TRY(cudaFuncSetAttribute(k_bwd_near<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_bwd_near<0><<<gridw, kBW * 32, smem, st>>>(c); note_launch();
+        k_bwd_near<1><<<gridl, kBW * 32, smem, st>>>(c); note_launch();
+    }
+    for (int l = 0; l <= t->L; ++l) {
+        const int64_t cnt = (int64_t)1 << l;
+        k_bwd_phi_level<<<(int)std::min<int64_t>((cnt + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(c, l); note_launch();
+    }
+    k_bwd_particles<<<gridp, 256, 0, st>>>(c); note_launch();
     stage_end(t, SG_BWD);
     RCB_CUDA_TRY(cudaGetLastError());
     return RCB_OK;

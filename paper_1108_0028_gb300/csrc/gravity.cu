@@ -771,26 +771,6 @@ int sm_count_g() {
 }  // namespace
 
 // FP64 Taylor coefficients of every sink into t->coef (used by the backward pass).
-int far_coefficients_fp64(rcb_tree *t) {
-    GCtx c;
-    std::memset(&c, 0, sizeof(c));
-    c.nsinks = t->nsinks;
-    c.sinks = t->sinks;
-    c.far_list = t->far_list;
-    c.far_n = t->far_n;
-    c.cap_far = t->cap_far;
-    c.ncom = t->ncom;
-    c.nmass = t->nmass;
-    c.nQ = t->nQ;
-    c.coef = t->coef;
-    if (t->nsinks == 0) return RCB_OK;
-    const int nsm = sm_count_g();
-    const int blocks = std::max(1, std::min((t->nsinks + kGWarps - 1) / kGWarps, nsm * 32));
-    k_far<false><<<blocks, kGWarps * 32, 0, t->stream>>>(c); note_launch();
-    RCB_CUDA_TRY(cudaGetLastError());
-    return RCB_OK;
-}
-
 namespace {
 
 GCtx make_gctx(rcb_tree *t, double *acc, double *pot) {
@@ -833,6 +813,26 @@ GCtx make_gctx(rcb_tree *t, double *acc, double *pot) {
     c.status = t->d_status;
     return c;
 }
+
+}  // namespace
+
+// Far-field coefficients alone, in the tree's precision (the backward pass differentiates the
+// Taylor polynomial of the same coefficients the forward evaluated).
+int far_coefficients(rcb_tree *t) {
+    if (t->nsinks == 0) return RCB_OK;
+    const GCtx c = make_gctx(t, nullptr, nullptr);
+    const int nsm = sm_count_g();
+    const int blocks = std::max(1, std::min((t->nsinks + kGWarps - 1) / kGWarps, nsm * 32));
+    if (t->params.precision == RCB_MIXED) {
+        k_far<true><<<blocks, kGWarps * 32, 0, t->stream>>>(c); note_launch();
+    } else {
+        k_far<false><<<blocks, kGWarps * 32, 0, t->stream>>>(c); note_launch();
+    }
+    RCB_CUDA_TRY(cudaGetLastError());
+    return RCB_OK;
+}
+
+namespace {
 
 template <bool NB>
 int launch_near_mixed(rcb_tree *t, const GCtx &c) {
