@@ -373,6 +373,102 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_far(BCtx c) {
     }
 }
 
+// Mixed form of the far interactions with the node adjoints merged per CTA before they reach
+// global memory: a CTA takes kFGroup consecutive sinks (siblings and cousins in tree order, whose
+// far lists share most nodes), adds each pair's ten node adjoints into a shared-memory hash table
+// keyed by node (float32; at most one term per sink and node), then flushes every entry once with
+// FP64 atomic adds.  A node that finds no slot within kFProbe probes goes straight to global
+// memory.
+constexpr int kFWarps = 8;
+constexpr int kFGroup = 16;
+constexpr int kFHash = 2048;
+constexpr int kFProbe = 32;
+
+struct FarHash {
+    int32_t key[kFHash];
+    float val[10][kFHash];
+    static constexpr size_t bytes = (size_t)kFHash * (sizeof(int32_t) + 10 * sizeof(float));
+};
+
+__device__ inline int far_hash_slot(FarHash &hs, int B) {
+    unsigned h = ((unsigned)B * 2654435761u) >> 21;  // 11 bits: kFHash = 2048
+    volatile int32_t *key = hs.key;
+    for (int probe = 0; probe < kFProbe; ++probe) {
+        const int k = key[h];
+        if (k == B) return (int)h;
+        if (k == -1) {
+            const int old = atomicCAS(&hs.key[h], -1, B);
+            if (old == -1 || old == B) return (int)h;
+        }
+        h = (h + 1) & (kFHash - 1);
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(kFWarps * 32) k_bwd_far_mixed(BCtx c) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FarHash &hs = *reinterpret_cast<FarHash *>(smem_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kFHash; i += blockDim.x) {
+        hs.key[i] = -1;
+#pragma unroll
+        for (int q = 0; q < 10; ++q) hs.val[q][i] = 0.f;
+    }
+    __syncthreads();
+    for (int g0 = blockIdx.x * kFGroup; g0 < c.nsinks; g0 += gridDim.x * kFGroup) {
+        const int g1 = min(g0 + kFGroup, c.nsinks);
+        for (int s = g0 + w; s < g1; s += kFWarps) {
+            const int A = c.sinks[s];
+            const int nf = c.far_n[s];
+            const FarCbar<float> P(c.cbar + (int64_t)s * 20);
+            const float4 ah = c.nfar[4 * (int64_t)A], al = c.nfar[4 * (int64_t)A + 1];
+            float RA[3] = {0.f, 0.f, 0.f};
+            for (int k = lane; k < nf; k += 32) {
+                const int B = c.far_list[(int64_t)s * c.cap_far + k];
+                const float4 r0 = c.nfar[4 * (int64_t)B], r1 = c.nfar[4 * (int64_t)B + 1],
+                             r2 = c.nfar[4 * (int64_t)B + 2], r3 = c.nfar[4 * (int64_t)B + 3];
+                const float x0 = (ah.x - r0.x) + (al.x - r1.x), x1 = (ah.y - r0.y) + (al.y - r1.y),
+                            x2 = (ah.z - r0.z) + (al.z - r1.z);
+                float mu, qa[6], gx[3];
+                far_adjoint<float>(P, x0, x1, x2, r0.w, r1.w, r2.x, r2.y, r2.z, r2.w, r3.x, mu, qa, gx);
+                RA[0] += gx[0];
+                RA[1] += gx[1];
+                RA[2] += gx[2];
+                const float vals[10] = {mu, -gx[0], -gx[1], -gx[2], qa[0], qa[1], qa[2], qa[3], qa[4], qa[5]};
+                const int slot = far_hash_slot(hs, B);
+                if (slot >= 0) {
+#pragma unroll
+                    for (int q = 0; q < 10; ++q) atomicAdd(&hs.val[q][slot], vals[q]);
+                } else {
+                    double *aB = c.adj + 10 * (int64_t)B;
+#pragma unroll
+                    for (int q = 0; q < 10; ++q) atomicAdd(aB + q, (double)vals[q]);
+                }
+            }
+            double R[3] = {RA[0], RA[1], RA[2]};
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+                for (int k2 = 0; k2 < 3; ++k2) R[k2] += __shfl_xor_sync(0xffffffffu, R[k2], o);
+            if (lane < 3) atomicAdd(&c.adj[10 * (int64_t)A + 1 + lane], lane == 0 ? R[0] : (lane == 1 ? R[1] : R[2]));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kFHash; i += blockDim.x) {
+            const int B = hs.key[i];
+            if (B >= 0) {
+                double *aB = c.adj + 10 * (int64_t)B;
+#pragma unroll
+                for (int q = 0; q < 10; ++q) {
+                    atomicAdd(aB + q, (double)hs.val[q][i]);
+                    hs.val[q][i] = 0.f;
+                }
+                hs.key[i] = -1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Stage particles [t0, t0 + kBTile) of a list of cells (cell ids given by a functor).
 template <typename CellAt>
 __device__ int stage_cells(const BCtx &c, int ncells, CellAt cell_at, int64_t t0, double *X, int32_t *I) {
@@ -538,20 +634,21 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_near(BCtx c) {
 }
 
 // ------------------------------------------------------------------------------ near (mixed)
-// The pair gradient of pair_grad in float32: 2 / (h_a + h_b) and 3 / q by the fast reciprocal
-// (3 / q = 3/2 (h_a + h_b) / r), 1 / r by rsqrtf.
+// The pair gradient of pair_grad in float32.  q = 2 r / (h_a + h_b) < 2 is tested as
+// r < h_a + h_b, so the reciprocal 2 / (h_a + h_b) (fast division) is taken only for softened
+// pairs; 3 / q = 3/2 (h_a + h_b) / r; 1 / r by rsqrtf.
 __device__ inline void pair_grad32(float dx, float dy, float dz, float hsum, float mb, float vx, float vy, float vz,
                                    float w, float &gx, float &gy, float &gz, float &gm) {
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
     const float r = r2 * rinv;
-    const float hinv = __fdividef(2.0f, hsum);
-    const float q = r * hinv;
     const float rinv2 = rinv * rinv;
     float sr = rinv * rinv2;
     float dsr = -3.f * sr * rinv2;
     float p = -rinv;
-    if (q < 2.f) {
+    if (r < hsum) {
+        const float hinv = __fdividef(2.0f, hsum);
+        const float q = r * hinv;
         const float h2 = hinv * hinv, h3 = h2 * hinv, h5 = h3 * h2;
         const float q2 = q * q;
         if (q < 1.f) {
@@ -988,7 +1085,9 @@ int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double
     }
     const int gridl = (int)std::max<int64_t>(1, std::min<int64_t>((nl + kBW - 1) / kBW, (int64_t)nsm * 16));
     if (t->params.precision == RCB_MIXED) {
-        k_bwd_far<true><<<gridw, kBW * 32, 0, st>>>(c); note_launch();
+        RCB_CUDA_TRY(cudaFuncSetAttribute(k_bwd_far_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FarHash::bytes));
+        const int gridf = std::max(1, std::min((t->nsinks + kFGroup - 1) / kFGroup, nsm * 2));
+        k_bwd_far_mixed<<<gridf, kFWarps * 32, FarHash::bytes, st>>>(c); note_launch();
         const size_t smem = kBW * BNearSmem::bytes;
         RCB_CUDA_TRY(cudaFuncSetAttribute(k_bwd_near_mixed<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         RCB_CUDA_TRY(cudaFuncSetAttribute(k_bwd_near_mixed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

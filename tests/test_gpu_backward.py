@@ -40,9 +40,13 @@ def test_backward_matches_oracle_vjp(kind, N, theta, precision):
     print(f"{precision} {kind} N={N}: dx max {ex:.2e} norm {nx:.2e}; dm max {em:.2e} norm {nm:.2e}")
     tol = 1e-9 if precision == "fp64" else 1e-5
     assert ex < tol and em < tol and nx < tol and nm < tol
-    # a second call reuses the transposed lists and gives the same result
+    # a second call reuses the transposed lists and gives the same result up to the order of
+    # atomic additions: FP64 node adjoints in the FP64 form; in the mixed form the far part first
+    # merges node adjoints in float32 shared-memory sums, so the order shows at float32 level
     gx2, gm2 = tree.gravity_backward(*_gpu(gA, gP))
-    assert np.allclose(gx2.cpu().numpy(), gx, rtol=0, atol=1e-12 * np.abs(gx).max())
+    rep = 1e-12 if precision == "fp64" else 1e-6
+    assert np.allclose(gx2.cpu().numpy(), gx, rtol=0, atol=rep * np.abs(gx).max())
+    assert np.allclose(gm2.cpu().numpy(), gm, rtol=0, atol=rep * np.abs(gm).max())
 
 
 def test_backward_theta_zero_equals_direct_gradient():
