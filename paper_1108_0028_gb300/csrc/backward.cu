@@ -811,6 +811,7 @@ __global__ void __launch_bounds__(kBW * 32, 2) k_bwd_near_mixed(BCtx c) {
                         const float jh = sm.hb[j];
 #pragma unroll
                         for (int i = 0; i < kMGroup; ++i) {
+                            if (i > 0 && i >= np) break;  // padding of a short group (warp-uniform)
                             float gx, gy, gz, gmv;
                             pair_grad32(ox[i] - ja.x, oy[i] - ja.y, oz[i] - ja.z, oh[i] + jh, ja.w, ovx[i], ovy[i],
                                         ovz[i], ow[i], gx, gy, gz, gmv);
@@ -824,6 +825,7 @@ __global__ void __launch_bounds__(kBW * 32, 2) k_bwd_near_mixed(BCtx c) {
                         const float4 jv = sm.v[j];
 #pragma unroll
                         for (int i = 0; i < kMGroup; ++i) {
+                            if (i > 0 && i >= np) break;  // padding of a short group (warp-uniform)
                             float gx, gy, gz, gmv;
                             pair_grad32(ja.x - ox[i], ja.y - oy[i], ja.z - oz[i], ja.w + oh[i], om[i], jv.x, jv.y, jv.z,
                                         jv.w, gx, gy, gz, gmv);

@@ -232,6 +232,7 @@ __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_
 
 constexpr int kNearWarps = 8;     // warps per block of the mixed near kernel
 constexpr int kNearTile = 512;    // staged sources per warp
+constexpr int kNbChunks = kNearTile / 32;  // 32-source chunks of a tile
 
 // Shared memory of one warp of the mixed near kernel.  With the neighbour search (NB) it also
 // holds each source's sorted index (bitwise complement for sources of non-candidate cells) and
@@ -240,14 +241,19 @@ template <bool NB>
 struct NearSmem {
     static constexpr size_t bytes =
         kNearTile * (sizeof(float4) + sizeof(float)) + 2 * kGroupMixed * sizeof(float4) +
-        (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * sizeof(float2) + kGroupMixed / 2 * sizeof(float2) : 0);
+        (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * sizeof(float2) + kGroupMixed * sizeof(float2) +
+                  2 * kNbChunks * kGroupMixed * sizeof(unsigned)
+            : 0);
     float4 *src;    // (d_b relative to the sink's centre of mass, m_b)
     float *hs;      // h_b
     float4 *snk;    // (d_a, h_a) of the current group
     float4 *snk2;   // the same by pairs (i, i + 1): (x_i, x_i+1, y_i, y_i+1), (z_i, z_i+1, h_i, h_i+1)
     float2 *hi2;    // NB: upper band edges by pairs
+    float2 *lo2;    // NB: lower band edges by pairs
     int32_t *sidx;  // NB
     float2 *band;   // NB: per sink particle (2h)^2 -+ B
+    unsigned *mlo;  // NB: [chunk][sink particle] sources below the band (neighbours)
+    unsigned *mamb; // NB: [chunk][sink particle] sources inside the band (float64 decides)
     __device__ NearSmem(unsigned char *p) {
         src = reinterpret_cast<float4 *>(p);
         hs = reinterpret_cast<float *>(src + kNearTile);
@@ -255,7 +261,10 @@ struct NearSmem {
         snk2 = snk + kGroupMixed;
         band = reinterpret_cast<float2 *>(snk2 + kGroupMixed);
         hi2 = band + (NB ? kGroupMixed : 0);
-        sidx = reinterpret_cast<int32_t *>(hi2 + (NB ? kGroupMixed / 2 : 0));
+        lo2 = hi2 + (NB ? kGroupMixed / 2 : 0);
+        sidx = reinterpret_cast<int32_t *>(lo2 + (NB ? kGroupMixed / 2 : 0));
+        mlo = reinterpret_cast<unsigned *>(sidx + (NB ? kNearTile : 0));
+        mamb = mlo + (NB ? kNbChunks * kGroupMixed : 0);
     }
 };
 
@@ -384,47 +393,71 @@ struct NbGroup {
     int nfb;  // float64 decisions taken
 };
 
-// Neighbour test of staged source b (lane) against sink particle i of the group: float32 d^2
-// against the particle's band, float64 inside it; b's sorted index is appended to a's row.
-// own: the chunk holds one of the group's own particles.
-template <bool NB>
-__device__ __forceinline__ void near_neighbours_of(const GCtx &c, const NearSmem<NB> &sm, int i, float4 b, int sb,
-                                                   unsigned cand, bool own, NbGroup &g) {
-    const int lane = threadIdx.x & 31;
-    const float4 sa = sm.snk[i];
-    const float dx = sa.x - b.x, dy = sa.y - b.y, dz = sa.z - b.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    const float2 bd = sm.band[i];
-    unsigned bl = __ballot_sync(0xffffffffu, r2 < bd.x) & cand;
-    const unsigned bh = __ballot_sync(0xffffffffu, r2 <= bd.y) & cand;
-    if (bl != bh) {
-        // inside the band: the float64 test decides
-        bool nb = false;
-        if (((bh & ~bl) >> lane) & 1u) {
-            const int a = g.a0 + i;
-            const double s2 = __dmul_rn(2.0, c.ph[a]);
-            nb = dist2_rn(c.px[a], c.py[a], c.pz[a], c.px[sb], c.py[sb], c.pz[sb]) < __dmul_rn(s2, s2);
-            ++g.nfb;
+// Neighbour rows of one tile.  The close loop left, per 32-source chunk k and sink particle i,
+// mlo (float32 d^2 below the particle's band: neighbours) and mamb (inside the band: the float64
+// test decides).  Four lanes per sink particle (lane = 4 i + q) take chunks q, q + 4, ...:
+// they settle the in-band sources in float64, count, offset their counts by a scan over the
+// four lanes and append the sources' sorted indices to the particle's row.  The order inside a
+// row is free (the compaction sorts each row).
+template <int G>
+__device__ inline void emit_neighbours(const GCtx &c, const NearSmem<true> &sm, int nchunks, int na, NbGroup &g) {
+    static_assert(4 * G == 32, "four lanes per sink particle");
+    const int lane = threadIdx.x & 31, i = lane >> 2, q = lane & 3;
+    const int a = g.a0 + i;
+    int cnt = 0;
+    if (i < na) {
+        double s2 = 0.0;
+        for (int k = q; k < nchunks; k += 4) {
+            unsigned m = sm.mlo[k * G + i];
+            unsigned amb = sm.mamb[k * G + i];
+            if (amb) {
+                if (s2 == 0.0) s2 = __dmul_rn(2.0, c.ph[a]);
+                do {
+                    const int j = __ffs(amb) - 1;
+                    amb &= amb - 1;
+                    const int sb = sm.sidx[32 * k + j];
+                    if (dist2_rn(c.px[a], c.py[a], c.pz[a], c.px[sb], c.py[sb], c.pz[sb]) < __dmul_rn(s2, s2))
+                        m |= 1u << j;
+                    ++g.nfb;
+                } while (amb);
+                sm.mlo[k * G + i] = m;
+            }
+            cnt += __popc(m);
         }
-        bl |= __ballot_sync(0xffffffffu, nb);
     }
-    if (own) bl &= ~__ballot_sync(0xffffffffu, sb == g.a0 + i);  // not itself
-    const int run = __shfl_sync(0xffffffffu, g.run, i);
-    if ((bl >> lane) & 1u) {
-        const int p = run + __popc(bl & ((1u << lane) - 1u));
-        if (p < kNbRowCap) c.nb_rows[(int64_t)(g.a0 + i) * kNbRowCap + p] = sb;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o, 4);
+        if (q >= o) incl += t;
     }
-    if (lane == i) g.run += __popc(bl);
+    int pos = __shfl_sync(0xffffffffu, g.run, i) + incl - cnt;
+    if (i < na) {
+        int32_t *row = c.nb_rows + (int64_t)a * kNbRowCap;
+        for (int k = q; k < nchunks; k += 4) {
+            unsigned m = sm.mlo[k * G + i];
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                if (pos < kNbRowCap) row[pos] = sm.sidx[32 * k + j];
+                ++pos;
+            }
+        }
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 4 * (lane & (G - 1)) + 3);
+    if (lane < G) g.run += tot;
 }
 
 // The pair loops of one staged tile for G sink particles (snk[0, G)), folded into the lane's
 // compensated total (rs, rc) of value (lane mod 4 G) = 4 i + q.  With NB the close loop also
-// tests every candidate pair (a, b) for |r_a - r_b| < 2 h_a: float32 d^2 against the band of
-// sink particle i, float64 inside it, and appends b's original index to a's row of slots.
+// tests every candidate pair (a, b) for |r_a - r_b| < 2 h_a (float32 d^2 against the band of
+// sink particle i, one ballot per band edge) and records the masks from which emit_neighbours
+// settles the in-band pairs in float64 and appends b's sorted index to a's row of slots.
 template <int G, bool NB>
-__device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const NearTile &tl, float &rs, float &rc,
-                                 NbGroup &g) {
+__device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const NearTile &tl, int na, float &rs,
+                                 float &rc, NbGroup &g) {
     const int nclose = tl.nclose;
+    const int npair = (na + 1) >> 1;  // sink particle pairs holding a real particle (warp-uniform)
     static_assert(G % 2 == 0, "sink particles go by pairs");
     const int lane = threadIdx.x & 31;
     // In[q][p]: quantity q (a_x, a_y, a_z, phi) of sink particles 2p and 2p + 1.  Every pair
@@ -444,6 +477,7 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const Ne
         const float2 nbm = make_float2(-b.w, -b.w);
 #pragma unroll
         for (int p = 0; p < G / 2; ++p) {
+            if (p > 0 && p >= npair) break;  // padding pairs of a short group
             const float4 sxy = sm.snk2[2 * p], szh = sm.snk2[2 * p + 1];
             const float2 dx = __fadd2_rn(make_float2(sxy.x, sxy.y), nbx);
             const float2 dy = __fadd2_rn(make_float2(sxy.z, sxy.w), nby);
@@ -476,12 +510,12 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const Ne
             if (NB) sb = sm.sidx[j];
         }
         const unsigned cand = NB ? __ballot_sync(0xffffffffu, sb >= 0) : 0u;  // candidate-cell sources
-        const bool own = NB && __any_sync(0xffffffffu, sb >= g.a0 && sb < g.a0 + G);
-        unsigned pend = 0;  // sink particles with a possible neighbour in this chunk
+        const int kc = q0 >> 5;                                                  // chunk of the tile
         const float2 nbx = make_float2(-b.x, -b.x), nby = make_float2(-b.y, -b.y), nbz = make_float2(-b.z, -b.z);
         const float2 bm = make_float2(b.w, b.w), nbm = make_float2(-b.w, -b.w), hb2 = make_float2(hb, hb);
 #pragma unroll
         for (int p = 0; p < G / 2; ++p) {
+            if (p > 0 && p >= npair) break;  // padding pairs of a short group
             // sink particles 2p and 2p + 1 against this lane's source (the self pair has r = 0:
             // zero force; its potential m_a phi(0) is removed in the epilogue)
             const float4 sxy = sm.snk2[2 * p], szh = sm.snk2[2 * p + 1];
@@ -515,19 +549,35 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const Ne
             In[2][p] = __ffma2_rn(nw, dz, In[2][p]);
             In[3][p] = __ffma2_rn(bm, ph, In[3][p]);
             if (NB) {
-                // upper band edge only here; the rest of the test runs out of the unrolled loop
-                const float2 hi = sm.hi2[p];
-                if (__ballot_sync(0xffffffffu, r2.x <= hi.x) & cand) pend |= 1u << (2 * p);
-                if (__ballot_sync(0xffffffffu, r2.y <= hi.y) & cand) pend |= 2u << (2 * p);
+                // neighbour masks of sink particles 2p and 2p + 1 against this chunk: below the
+                // band, and inside it (settled in float64 by emit_neighbours)
+                const float2 hi = sm.hi2[p], lo = sm.lo2[p];
+                const unsigned l0 = __ballot_sync(0xffffffffu, r2.x < lo.x) & cand;
+                const unsigned h0 = __ballot_sync(0xffffffffu, r2.x <= hi.x) & cand;
+                const unsigned l1 = __ballot_sync(0xffffffffu, r2.y < lo.y) & cand;
+                const unsigned h1 = __ballot_sync(0xffffffffu, r2.y <= hi.y) & cand;
+                if (lane == 0) {
+                    sm.mlo[kc * G + 2 * p] = l0;
+                    sm.mamb[kc * G + 2 * p] = h0 & ~l0;
+                    sm.mlo[kc * G + 2 * p + 1] = l1;
+                    sm.mamb[kc * G + 2 * p + 1] = h1 & ~l1;
+                }
             }
         }
-        if (NB) {
-            while (pend) {
-                const int i = __ffs(pend) - 1;
-                pend &= pend - 1;
-                near_neighbours_of<NB>(c, sm, i, b, sb, cand, own, g);
+        if (NB && __any_sync(0xffffffffu, sb >= g.a0 && sb < g.a0 + G)) {
+            // the chunk holds some of the group's own particles: a particle is not its own neighbour
+            for (int i = 0; i < G; ++i) {
+                const unsigned ob = __ballot_sync(0xffffffffu, sb == g.a0 + i);
+                if (lane == 0 && ob) {
+                    sm.mlo[kc * G + i] &= ~ob;
+                    sm.mamb[kc * G + i] &= ~ob;
+                }
             }
         }
+    }
+    if constexpr (NB) {
+        __syncwarp();
+        emit_neighbours<G>(c, sm, (nclose + 31) >> 5, na, g);
     }
     // fold this tile: compensated reduce-scatter across lanes, then into (rs, rc)
     float Vs[4 * G], Vc[4 * G];
@@ -619,10 +669,13 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
                         sm.band[lane] = bd;
                     }
                     __syncwarp();
-                    if (lane < kGroupMixed / 2) sm.hi2[lane] = make_float2(sm.band[2 * lane].y, sm.band[2 * lane + 1].y);
+                    if (lane < kGroupMixed / 2) {
+                        sm.hi2[lane] = make_float2(sm.band[2 * lane].y, sm.band[2 * lane + 1].y);
+                        sm.lo2[lane] = make_float2(sm.band[2 * lane].x, sm.band[2 * lane + 1].x);
+                    }
                     __syncwarp();
                 }
-                near_tile<kGroupMixed, NB>(c, sm, tl, rs, rc, g);
+                near_tile<kGroupMixed, NB>(c, sm, tl, na, rs, rc, g);
                 __syncwarp();
                 if (t0 + kNearTile >= tl.S) break;
             }
