@@ -242,7 +242,7 @@ struct NearSmem {
     static constexpr size_t bytes =
         kNearTile * (sizeof(float4) + sizeof(float)) + 2 * kGroupMixed * sizeof(float4) +
         (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * sizeof(float2) + kGroupMixed * sizeof(float2) +
-                  2 * kNbChunks * kGroupMixed * sizeof(unsigned)
+                  kNbChunks * kGroupMixed * sizeof(unsigned)
             : 0);
     float4 *src;    // (d_b relative to the sink's centre of mass, m_b)
     float *hs;      // h_b
@@ -252,7 +252,6 @@ struct NearSmem {
     float2 *lo2;    // NB: lower band edges by pairs
     int32_t *sidx;  // NB
     float2 *band;   // NB: per sink particle (2h)^2 -+ B
-    unsigned *mlo;  // NB: [chunk][sink particle] sources below the band (neighbours)
     unsigned *mamb; // NB: [chunk][sink particle] sources inside the band (float64 decides)
     __device__ NearSmem(unsigned char *p) {
         src = reinterpret_cast<float4 *>(p);
@@ -263,8 +262,7 @@ struct NearSmem {
         hi2 = band + (NB ? kGroupMixed : 0);
         lo2 = hi2 + (NB ? kGroupMixed / 2 : 0);
         sidx = reinterpret_cast<int32_t *>(lo2 + (NB ? kGroupMixed / 2 : 0));
-        mlo = reinterpret_cast<unsigned *>(sidx + (NB ? kNearTile : 0));
-        mamb = mlo + (NB ? kNbChunks * kGroupMixed : 0);
+        mamb = reinterpret_cast<unsigned *>(sidx + (NB ? kNearTile : 0));
     }
 };
 
@@ -388,64 +386,50 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
 
 // Neighbour-search state of one group of sink particles.
 struct NbGroup {
-    int a0;   // sorted index of the group's first sink particle
-    int run;  // lane i < G: neighbours of sink particle i found so far
-    int nfb;  // float64 decisions taken
+    int a0;                 // sorted index of the group's first sink particle
+    int run[kGroupMixed];   // neighbours of sink particle i found so far (the same in every lane)
+    int nfb;                // float64 decisions taken (per lane)
 };
 
-// Neighbour rows of one tile.  The close loop left, per 32-source chunk k and sink particle i,
-// mlo (float32 d^2 below the particle's band: neighbours) and mamb (inside the band: the float64
-// test decides).  Four lanes per sink particle (lane = 4 i + q) take chunks q, q + 4, ...:
-// they settle the in-band sources in float64, count, offset their counts by a scan over the
-// four lanes and append the sources' sorted indices to the particle's row.  The order inside a
-// row is free (the compaction sorts each row).
+// Append the sources of mask m (bits = lanes of chunk k) to sink particle i's row: the lanes
+// whose bit is set write consecutive slots.  The order inside a row is free (the compaction
+// sorts each row).
+__device__ __forceinline__ void nb_append(const GCtx &c, int a, int &run, unsigned m, int sb) {
+    const int lane = threadIdx.x & 31;
+    if ((m >> lane) & 1u) {
+        const int p = run + __popc(m & ((1u << lane) - 1u));
+        if (p < kNbRowCap) c.nb_rows[(int64_t)a * kNbRowCap + p] = sb;
+    }
+    run += __popc(m);
+}
+
+// Sources inside a sink particle's float32 band (mamb, recorded by the close loop per chunk and
+// sink particle) are settled by the float64 test, every lane of the chunk at once, and appended.
 template <int G>
-__device__ inline void emit_neighbours(const GCtx &c, const NearSmem<true> &sm, int nchunks, int na, NbGroup &g) {
-    static_assert(4 * G == 32, "four lanes per sink particle");
-    const int lane = threadIdx.x & 31, i = lane >> 2, q = lane & 3;
-    const int a = g.a0 + i;
-    int cnt = 0;
-    if (i < na) {
-        double s2 = 0.0;
-        for (int k = q; k < nchunks; k += 4) {
-            unsigned m = sm.mlo[k * G + i];
-            unsigned amb = sm.mamb[k * G + i];
-            if (amb) {
-                if (s2 == 0.0) s2 = __dmul_rn(2.0, c.ph[a]);
-                do {
-                    const int j = __ffs(amb) - 1;
-                    amb &= amb - 1;
-                    const int sb = sm.sidx[32 * k + j];
-                    if (dist2_rn(c.px[a], c.py[a], c.pz[a], c.px[sb], c.py[sb], c.pz[sb]) < __dmul_rn(s2, s2))
-                        m |= 1u << j;
-                    ++g.nfb;
-                } while (amb);
-                sm.mlo[k * G + i] = m;
+__device__ inline void settle_band(const GCtx &c, const NearSmem<true> &sm, int nchunks, int na, NbGroup &g) {
+    const int lane = threadIdx.x & 31;
+    for (int e0 = 0; e0 < nchunks * G; e0 += 32) {
+        const int e = e0 + lane;
+        unsigned todo = __ballot_sync(0xffffffffu, e < nchunks * G && (e % G) < na && sm.mamb[e] != 0u);
+        while (todo) {
+            const int ee = e0 + __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int k = ee / G, i = ee % G;
+            const unsigned amb = sm.mamb[ee];
+            const int a = g.a0 + i;
+            const int sb = sm.sidx[32 * k + lane];
+            bool nb = false;
+            if (((amb >> lane) & 1u) && sb != a) {
+                const double s2 = __dmul_rn(2.0, c.ph[a]);
+                nb = dist2_rn(c.px[a], c.py[a], c.pz[a], c.px[sb], c.py[sb], c.pz[sb]) < __dmul_rn(s2, s2);
+                ++g.nfb;
             }
-            cnt += __popc(m);
-        }
-    }
-    int incl = cnt;
+            const unsigned m = __ballot_sync(0xffffffffu, nb);
 #pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o, 4);
-        if (q >= o) incl += t;
-    }
-    int pos = __shfl_sync(0xffffffffu, g.run, i) + incl - cnt;
-    if (i < na) {
-        int32_t *row = c.nb_rows + (int64_t)a * kNbRowCap;
-        for (int k = q; k < nchunks; k += 4) {
-            unsigned m = sm.mlo[k * G + i];
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                if (pos < kNbRowCap) row[pos] = sm.sidx[32 * k + j];
-                ++pos;
-            }
+            for (int q = 0; q < G; ++q)
+                if (q == i) nb_append(c, a, g.run[q], m, sb);
         }
     }
-    const int tot = __shfl_sync(0xffffffffu, incl, 4 * (lane & (G - 1)) + 3);
-    if (lane < G) g.run += tot;
 }
 
 // The pair loops of one staged tile for G sink particles (snk[0, G)), folded into the lane's
@@ -511,6 +495,7 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const Ne
         }
         const unsigned cand = NB ? __ballot_sync(0xffffffffu, sb >= 0) : 0u;  // candidate-cell sources
         const int kc = q0 >> 5;                                                  // chunk of the tile
+        const bool own = NB && __any_sync(0xffffffffu, sb >= g.a0 && sb < g.a0 + G);  // holds group particles
         const float2 nbx = make_float2(-b.x, -b.x), nby = make_float2(-b.y, -b.y), nbz = make_float2(-b.z, -b.z);
         const float2 bm = make_float2(b.w, b.w), nbm = make_float2(-b.w, -b.w), hb2 = make_float2(hb, hb);
 #pragma unroll
@@ -549,35 +534,30 @@ __device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const Ne
             In[2][p] = __ffma2_rn(nw, dz, In[2][p]);
             In[3][p] = __ffma2_rn(bm, ph, In[3][p]);
             if (NB) {
-                // neighbour masks of sink particles 2p and 2p + 1 against this chunk: below the
-                // band, and inside it (settled in float64 by emit_neighbours)
+                // neighbour test of sink particles 2p and 2p + 1 against this chunk: sources below
+                // the band are appended now, those inside it are recorded for settle_band; a
+                // particle is not its own neighbour
                 const float2 hi = sm.hi2[p], lo = sm.lo2[p];
-                const unsigned l0 = __ballot_sync(0xffffffffu, r2.x < lo.x) & cand;
+                unsigned l0 = __ballot_sync(0xffffffffu, r2.x < lo.x) & cand;
                 const unsigned h0 = __ballot_sync(0xffffffffu, r2.x <= hi.x) & cand;
-                const unsigned l1 = __ballot_sync(0xffffffffu, r2.y < lo.y) & cand;
+                unsigned l1 = __ballot_sync(0xffffffffu, r2.y < lo.y) & cand;
                 const unsigned h1 = __ballot_sync(0xffffffffu, r2.y <= hi.y) & cand;
                 if (lane == 0) {
-                    sm.mlo[kc * G + 2 * p] = l0;
                     sm.mamb[kc * G + 2 * p] = h0 & ~l0;
-                    sm.mlo[kc * G + 2 * p + 1] = l1;
                     sm.mamb[kc * G + 2 * p + 1] = h1 & ~l1;
                 }
-            }
-        }
-        if (NB && __any_sync(0xffffffffu, sb >= g.a0 && sb < g.a0 + G)) {
-            // the chunk holds some of the group's own particles: a particle is not its own neighbour
-            for (int i = 0; i < G; ++i) {
-                const unsigned ob = __ballot_sync(0xffffffffu, sb == g.a0 + i);
-                if (lane == 0 && ob) {
-                    sm.mlo[kc * G + i] &= ~ob;
-                    sm.mamb[kc * G + i] &= ~ob;
+                if (own) {
+                    l0 &= ~__ballot_sync(0xffffffffu, sb == g.a0 + 2 * p);
+                    l1 &= ~__ballot_sync(0xffffffffu, sb == g.a0 + 2 * p + 1);
                 }
+                nb_append(c, g.a0 + 2 * p, g.run[2 * p], l0, sb);
+                nb_append(c, g.a0 + 2 * p + 1, g.run[2 * p + 1], l1, sb);
             }
         }
     }
     if constexpr (NB) {
         __syncwarp();
-        emit_neighbours<G>(c, sm, (nclose + 31) >> 5, na, g);
+        settle_band<G>(c, sm, (nclose + 31) >> 5, na, g);
     }
     // fold this tile: compensated reduce-scatter across lanes, then into (rs, rc)
     float Vs[4 * G], Vc[4 * G];
@@ -644,7 +624,8 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             }
             if (NB) {
                 g.a0 = fA + a0;
-                g.run = 0;
+#pragma unroll
+                for (int i = 0; i < kGroupMixed; ++i) g.run[i] = 0;
             }
             __syncwarp();
             float rs = 0.f, rc = 0.f;  // compensated total of value lane mod 4 G (= 4 i + q)
@@ -705,7 +686,10 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             }
             if (NB && lane < na) {
                 const int a = fA + a0 + lane;
-                const int n = g.run;
+                int n = g.run[0];
+#pragma unroll
+                for (int i = 1; i < kGroupMixed; ++i)
+                    if (lane == i) n = g.run[i];
                 c.nb_counts[c.pidx[a]] = n;
                 if (n > kNbRowCap) {
                     const int q = atomicAdd(&c.status[ST_LONGROWS], 1);
