@@ -50,6 +50,8 @@ struct BCtx {
     const int32_t *pidx;
     const double *coef;     // [nsinks][20] coefficients in the tree's precision (recomputed)
     double *cbar;           // [nsinks][20] dL/dC
+    float *cbar32;          // mixed form: the same in float32
+    float4 *gv32;           // mixed form: (dL/da, dL/dPhi) per particle in float32, sorted order
     const double *gA, *gP;  // sorted order: [3N], [N]
     double *gxs, *gms;      // sorted-order accumulators
     double *adj;            // [nn][10]: M, COM x/y/z, Q (6 slots)
@@ -69,6 +71,8 @@ __global__ void k_bwd_gather(BCtx c) {
         gA[3 * p + 1] = c.gacc[3 * o + 1];
         gA[3 * p + 2] = c.gacc[3 * o + 2];
         gP[p] = c.gpot ? c.gpot[o] : 0.0;
+        if (c.gv32)
+            c.gv32[p] = make_float4((float)gA[3 * p], (float)gA[3 * p + 1], (float)gA[3 * p + 2], (float)gP[p]);
     }
 }
 
@@ -100,9 +104,9 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_taylor_mixed(BCtx c, const flo
             const int a = f + a0 + lane;
             if (a0 + lane < n) {
                 const float4 pa = c.p32[a];
-                const float v[3] = {(float)c.gA[3 * (int64_t)a], (float)c.gA[3 * (int64_t)a + 1],
-                                    (float)c.gA[3 * (int64_t)a + 2]};
-                const float w = (float)c.gP[a];
+                const float4 gv = c.gv32[a];
+                const float v[3] = {gv.x, gv.y, gv.z};
+                const float w = gv.w;
                 float g[3], H[6];
                 taylor_grad_hess<float>(C, pa.x, pa.y, pa.z, g, H);
                 const float gd[3] = {w * g[0] - (v[0] * H[0] + v[1] * H[1] + v[2] * H[2]),
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_taylor_mixed(BCtx c, const flo
 #pragma unroll
             for (int i = 1; i < 20; ++i)
                 if (lane == i) val = cb[i];
-            c.cbar[(int64_t)s * 20 + lane] = val;
+            c.cbar32[(int64_t)s * 20 + lane] = val;
         }
         if (lane < 3) atomicAdd(&c.adj[10 * (int64_t)A + 1 + lane], (double)(lane == 0 ? comb[0] : (lane == 1 ? comb[1] : comb[2])));
     }
@@ -215,7 +219,8 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_taylor(BCtx c) {
 template <typename T>
 struct FarCbar {
     T cb0, P1[3], p2xx, p2xy, p2xz, p2yy, p2yz, p2zz, p3[10], t3[3], trP2;
-    __device__ explicit FarCbar(const double *cbs) {
+    template <typename S>
+    __device__ explicit FarCbar(const S *cbs) {
         cb0 = (T)cbs[0];
         P1[0] = (T)cbs[1];
         P1[1] = (T)cbs[2];
@@ -420,7 +425,7 @@ __global__ void __launch_bounds__(kFWarps * 32) k_bwd_far_mixed(BCtx c) {
         for (int s = g0 + w; s < g1; s += kFWarps) {
             const int A = c.sinks[s];
             const int nf = c.far_n[s];
-            const FarCbar<float> P(c.cbar + (int64_t)s * 20);
+            const FarCbar<float> P(c.cbar32 + (int64_t)s * 20);
             const float4 ah = c.nfar[4 * (int64_t)A], al = c.nfar[4 * (int64_t)A + 1];
             float RA[3] = {0.f, 0.f, 0.f};
             for (int k = lane; k < nf; k += 32) {
@@ -724,8 +729,7 @@ __device__ int stage_cells_mixed(const BCtx &c, int ncells, CellAt cell_at, int6
                     sm.hb[slot] = c.h32[b];
                 } else {
                     sm.a[slot] = make_float4(pb.x + bx, pb.y + by, pb.z + bz, c.h32[b]);
-                    sm.v[slot] = make_float4((float)c.gA[3 * (int64_t)b], (float)c.gA[3 * (int64_t)b + 1],
-                                             (float)c.gA[3 * (int64_t)b + 2], (float)c.gP[b]);
+                    sm.v[slot] = c.gv32[b];
                 }
                 sm.id[slot] = b;
             }
@@ -789,10 +793,11 @@ __global__ void __launch_bounds__(kBW * 32, 2) k_bwd_near_mixed(BCtx c) {
                 om[i] = pp.w;
                 oh[i] = c.h32[p];
                 if (SIDE == 0) {
-                    ovx[i] = (float)c.gA[3 * (int64_t)p];
-                    ovy[i] = (float)c.gA[3 * (int64_t)p + 1];
-                    ovz[i] = (float)c.gA[3 * (int64_t)p + 2];
-                    ow[i] = (float)c.gP[p];
+                    const float4 gv = c.gv32[p];
+                    ovx[i] = gv.x;
+                    ovy[i] = gv.y;
+                    ovz[i] = gv.z;
+                    ow[i] = gv.w;
                 }
                 oid[i] = i < np ? p : -1;
             }
@@ -1006,7 +1011,8 @@ int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double
         t->tfar_off = (int32_t *)dev_alloc(t, std::max<int64_t>(nl, 1) * sizeof(int32_t));   // cursor scratch
         t->tfar_sink = (int32_t *)dev_alloc(t, N * sizeof(int32_t));                          // leaf of each particle
         t->adj = (double *)dev_alloc(t, (size_t)nn * 10 * sizeof(double) + (size_t)N * 8 * sizeof(double) +
-                                            (size_t)t->nsinks * 20 * sizeof(double));
+                                            (size_t)t->nsinks * 20 * sizeof(double) + (size_t)N * sizeof(float4) +
+                                            (size_t)t->nsinks * 20 * sizeof(float));
         if (!t->tnear_off || !t->tnear_sink || !t->tfar_off || !t->tfar_sink || !t->adj) return RCB_ERR_ALLOC;
     }
     double *adj = t->adj;
@@ -1015,6 +1021,8 @@ int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double
     double *gA = gms + N;
     double *gP = gA + 3 * N;
     double *cbar = gP + N;
+    float4 *gv32 = reinterpret_cast<float4 *>(cbar + (size_t)t->nsinks * 20);
+    float *cbar32 = reinterpret_cast<float *>(gv32 + N);
     BCtx c;
     c.nsinks = t->nsinks;
     c.nleaves = nl;
@@ -1044,6 +1052,8 @@ int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double
     c.pidx = t->pidx;
     c.coef = t->coef;
     c.cbar = cbar;
+    c.cbar32 = cbar32;
+    c.gv32 = t->params.precision == RCB_MIXED ? gv32 : nullptr;
     c.gA = gA;
     c.gP = gP;
     c.gxs = gxs;
