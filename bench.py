@@ -35,6 +35,11 @@ UNIT = "Mparticles/s"
 N_LL = 12
 FLOPS_PER_PAIR = 38        # float32 flops of one kernel-softened near-field pair, Eq. 10 with its potential (FMA = 2, MUFU = 1)
 FLOPS_PER_PAIR_NEWTON = 24  # the same pair on its Newtonian branch (q >= 2), the form most pairs take
+# DRAM bytes of one near-kernel launch at the headline workload: dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture at N = 2,097,152 (1,057,838,848 B for 1,038,400,525
+# pairs) scaled by the pair count to N = 4,194,304 (2,065,548,119 pairs).  Valid only for the
+# kernel source it was taken on; any later change of gravity.cu reports null.
+NEAR_TRAFFIC = {"bytes": 2104213000, "gravity_cu_sha1": "bca4f9df67d9d38e84d5c737a74470ffb7139bf1"}
 SMS = 152
 FP32_LANES = 128           # FP32 lanes per SM
 L2_FLUSH_BYTES = 256 << 20
@@ -371,8 +376,17 @@ def run_ours(a, rank, world, local_rank):
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
     near_s = stage_ms["near"] * 1e-3
     achieved = info["near_pairs"] * FLOPS_PER_PAIR / near_s / 1e12
+    traffic = None
+    try:
+        import hashlib
+        src = os.path.join(ROOT, "paper_1108_0028_gb300", "csrc", "gravity.cu")
+        if hashlib.sha1(open(src, "rb").read()).hexdigest() == NEAR_TRAFFIC["gravity_cu_sha1"] and \
+                (a.n, a.kind, a.mass, a.theta) == (4194304, "sphere", "loguniform10", 0.7):
+            traffic = NEAR_TRAFFIC["bytes"]
+    except OSError:
+        pass
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_near_mixed",
+                "traffic": traffic, "traffic_unit": "B per launch", "kernel": "k_near_mixed",
                 "frac_newtonian_count": achieved * FLOPS_PER_PAIR_NEWTON / FLOPS_PER_PAIR / peak,
                 "basis": f"{info['near_pairs']} near pairs x {FLOPS_PER_PAIR} FP32 flops (one kernel-softened pair of "
                          f"Eq. 10; frac_newtonian_count counts {FLOPS_PER_PAIR_NEWTON}, the Newtonian branch; the "
