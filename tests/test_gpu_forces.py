@@ -232,3 +232,35 @@ def test_gravity_neighbours_after_rebuild_and_refit():
     ro, ri = ref.neighbours()
     _, _, go, gi = tree.gravity_neighbours()
     assert np.array_equal(go.cpu().numpy(), ro) and np.array_equal(gi.cpu().numpy(), ri)
+
+
+@pytest.mark.parametrize("bump", [False, True])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_neighbour_ties_on_a_lattice(bump, precision):
+    # 16^3 particles on a lattice of spacing s = 1/16 with h = s/2: every face neighbour sits at
+    # exactly 2h and is not a neighbour (the test is strict); with h one ulp above s/2 all six
+    # are.  The float32 filters cannot tell the two apart, so every face pair is decided by the
+    # float64 definition (the in-band path of both the fused kernel and rcb_neighbours).
+    import paper_1108_0028_gb300 as rcb
+    s = 1.0 / 16
+    g = (np.arange(16) + 0.5) * s
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    N = len(x)
+    x = np.ascontiguousarray(x[np.random.default_rng(11).permutation(N)])
+    m = np.full(N, 1.0 / N)
+    h = np.full(N, np.nextafter(s / 2, 1.0) if bump else s / 2)
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(0.6)
+    ro, ri = ref.neighbours()
+    if bump:
+        k = np.rint(x / s - 0.5).astype(int)   # lattice index: 6 face neighbours inside, fewer on the boundary
+        expect = sum((k[:, d] > 0).astype(int) + (k[:, d] < 15).astype(int) for d in range(3))
+        assert np.array_equal(np.diff(ro), expect)
+    else:
+        assert ro[-1] == 0
+    tree = rcb.RCBTree(*_gpu(x, m, h), theta=0.6, precision=precision)
+    _, _, go, gi = tree.gravity_neighbours()
+    assert np.array_equal(go.cpu().numpy(), ro) and np.array_equal(gi.cpu().numpy(), ri)
+    plain = rcb.RCBTree(*_gpu(x, m, h), theta=0.6, precision=precision)
+    po, pi = plain.neighbours()
+    assert np.array_equal(po.cpu().numpy(), ro) and np.array_equal(pi.cpu().numpy(), ri)
