@@ -233,6 +233,7 @@ __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_
 constexpr int kNearWarps = 8;     // warps per block of the mixed near kernel
 constexpr int kNearTile = 512;    // staged sources per warp
 constexpr int kNbChunks = kNearTile / 32;  // 32-source chunks of a tile
+constexpr int kSuper = 3;                   // groups of sink particles sharing one staged tile
 
 // Shared memory of one warp of the mixed near kernel.  With the neighbour search (NB) it also
 // holds each source's sorted index (bitwise complement for sources of non-candidate cells) and
@@ -241,6 +242,7 @@ template <bool NB>
 struct NearSmem {
     static constexpr size_t bytes =
         kNearTile * (sizeof(float4) + sizeof(float)) + 2 * kGroupMixed * sizeof(float4) +
+        kSuper * 32 * sizeof(float2) + (NB ? kSuper * kGroupMixed * sizeof(int) : 0) +
         (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * sizeof(float2) + kGroupMixed * sizeof(float2) +
                   kNbChunks * kGroupMixed * sizeof(unsigned)
             : 0);
@@ -253,6 +255,8 @@ struct NearSmem {
     int32_t *sidx;  // NB
     float2 *band;   // NB: per sink particle (2h)^2 -+ B
     unsigned *mamb; // NB: [chunk][sink particle] sources inside the band (float64 decides)
+    float2 *gacc;   // [group][lane] the lanes' compensated totals of the groups sharing a tile
+    int *grun;      // NB: [group][sink particle] neighbours found so far
     __device__ NearSmem(unsigned char *p) {
         src = reinterpret_cast<float4 *>(p);
         hs = reinterpret_cast<float *>(src + kNearTile);
@@ -263,6 +267,8 @@ struct NearSmem {
         lo2 = hi2 + (NB ? kGroupMixed / 2 : 0);
         sidx = reinterpret_cast<int32_t *>(lo2 + (NB ? kGroupMixed / 2 : 0));
         mamb = reinterpret_cast<unsigned *>(sidx + (NB ? kNearTile : 0));
+        gacc = reinterpret_cast<float2 *>(mamb + (NB ? kNbChunks * kGroupMixed : 0));
+        grun = reinterpret_cast<int *>(gacc + kSuper * 32);
     }
 };
 
@@ -608,92 +614,108 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             RA = sqrtf(R2) * (1.0f + 0x1p-10f);
             HA = H;
         }
-        NearTile once{-1, 0, 0};  // staged tile when all sources fit one tile
+        // Up to kSuper groups of eight sink particles share each staged tile: the tile loop is
+        // outside the group loop, and each group's lane totals and neighbour counts wait in
+        // shared memory while another group runs.  Sinks with more particles take several
+        // such passes.
         float wmax = 0.f;
-        for (int a0 = 0; a0 < nA; a0 += kGroupMixed) {
-            const int na = min(kGroupMixed, nA - a0);
-            if (lane < kGroupMixed) {
-                const int i = min(lane, na - 1);
-                const float4 pa = c.p32[fA + a0 + i];
-                sm.snk[lane] = make_float4(pa.x, pa.y, pa.z, c.h32[fA + a0 + i]);
+        for (int A0 = 0; A0 < nA; A0 += kSuper * kGroupMixed) {
+            const int ng = min(kSuper, (nA - A0 + kGroupMixed - 1) / kGroupMixed);
+            for (int gi = 0; gi < ng; ++gi) {
+                sm.gacc[gi * 32 + lane] = make_float2(0.f, 0.f);
+                if (NB && lane < kGroupMixed) sm.grun[gi * kGroupMixed + lane] = 0;
             }
             __syncwarp();
-            if (lane < kGroupMixed) {
-                const float4 u = sm.snk[lane & ~1], v = sm.snk[lane | 1];
-                sm.snk2[lane] = (lane & 1) ? make_float4(u.z, v.z, u.w, v.w) : make_float4(u.x, v.x, u.y, v.y);
-            }
-            if (NB) {
-                g.a0 = fA + a0;
-#pragma unroll
-                for (int i = 0; i < kGroupMixed; ++i) g.run[i] = 0;
-            }
-            __syncwarp();
-            float rs = 0.f, rc = 0.f;  // compensated total of value lane mod 4 G (= 4 i + q)
             for (int64_t t0 = 0;; t0 += kNearTile) {
-                NearTile tl = once;
-                if (tl.nclose < 0) {
-                    tl = stage_near_mixed<NB>(c, s, A, nlist, nr, t0, sm, RA, HA, wmax);
-                    if (tl.S <= kNearTile) once = tl;
-                }
-                if (NB) {
-                    // neighbour band of each sink particle for this tile (-1: padding slot)
+                const NearTile tl = stage_near_mixed<NB>(c, s, A, nlist, nr, t0, sm, RA, HA, wmax);
+                for (int gi = 0; gi < ng; ++gi) {
+                    const int a0 = A0 + gi * kGroupMixed;
+                    const int na = min(kGroupMixed, nA - a0);
                     if (lane < kGroupMixed) {
-                        float2 bd = make_float2(-1.f, -1.f);
-                        if (lane < na) {
-                            const float4 sa = sm.snk[lane];
-                            const float h2f = 2.0f * sa.w;  // = float32(2 h) exactly
-                            const float h2 = h2f * h2f;
-                            const float F = wmax + (fabsf(sa.x) + fabsf(sa.y) + fabsf(sa.z));
-                            const float B = fmaf(F, F, h2) * 0x1p-19f + 1e-30f;
-                            bd = make_float2(h2 - B, h2 + B);
-                        }
-                        sm.band[lane] = bd;
+                        const int i = min(lane, na - 1);
+                        const float4 pa = c.p32[fA + a0 + i];
+                        sm.snk[lane] = make_float4(pa.x, pa.y, pa.z, c.h32[fA + a0 + i]);
                     }
                     __syncwarp();
-                    if (lane < kGroupMixed / 2) {
-                        sm.hi2[lane] = make_float2(sm.band[2 * lane].y, sm.band[2 * lane + 1].y);
-                        sm.lo2[lane] = make_float2(sm.band[2 * lane].x, sm.band[2 * lane + 1].x);
+                    if (lane < kGroupMixed) {
+                        const float4 u = sm.snk[lane & ~1], v = sm.snk[lane | 1];
+                        sm.snk2[lane] = (lane & 1) ? make_float4(u.z, v.z, u.w, v.w) : make_float4(u.x, v.x, u.y, v.y);
+                    }
+                    if (NB) {
+                        g.a0 = fA + a0;
+#pragma unroll
+                        for (int i = 0; i < kGroupMixed; ++i) g.run[i] = sm.grun[gi * kGroupMixed + i];
+                        // neighbour band of each sink particle for this tile (-1: padding slot)
+                        if (lane < kGroupMixed) {
+                            float2 bd = make_float2(-1.f, -1.f);
+                            if (lane < na) {
+                                const float4 pa = c.p32[fA + a0 + lane];
+                                const float h2f = 2.0f * c.h32[fA + a0 + lane];  // = float32(2 h) exactly
+                                const float h2 = h2f * h2f;
+                                const float F = wmax + (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z));
+                                const float B = fmaf(F, F, h2) * 0x1p-19f + 1e-30f;
+                                bd = make_float2(h2 - B, h2 + B);
+                            }
+                            sm.band[lane] = bd;
+                        }
+                        __syncwarp();
+                        if (lane < kGroupMixed / 2) {
+                            sm.hi2[lane] = make_float2(sm.band[2 * lane].y, sm.band[2 * lane + 1].y);
+                            sm.lo2[lane] = make_float2(sm.band[2 * lane].x, sm.band[2 * lane + 1].x);
+                        }
+                    }
+                    __syncwarp();
+                    const float2 st = sm.gacc[gi * 32 + lane];
+                    float rs = st.x, rc = st.y;  // compensated total of value lane mod 4 G (= 4 i + q)
+                    near_tile<kGroupMixed, NB>(c, sm, tl, na, rs, rc, g);
+                    __syncwarp();
+                    sm.gacc[gi * 32 + lane] = make_float2(rs, rc);
+                    if (NB && lane < kGroupMixed) {
+                        int n = g.run[0];
+#pragma unroll
+                        for (int i = 1; i < kGroupMixed; ++i)
+                            if (lane == i) n = g.run[i];
+                        sm.grun[gi * kGroupMixed + lane] = n;
                     }
                     __syncwarp();
                 }
-                near_tile<kGroupMixed, NB>(c, sm, tl, na, rs, rc, g);
-                __syncwarp();
                 if (t0 + kNearTile >= tl.S) break;
             }
-            const double tot = __dadd_rn((double)rs, (double)rc);  // lane l < 4 na: particle l/4, quantity l%4
-            const double q0v = __shfl_sync(0xffffffffu, tot, (4 * lane) & 31);
-            const double q1v = __shfl_sync(0xffffffffu, tot, (4 * lane + 1) & 31);
-            const double q2v = __shfl_sync(0xffffffffu, tot, (4 * lane + 2) & 31);
-            const double q3v = __shfl_sync(0xffffffffu, tot, (4 * lane + 3) & 31);
-            if (lane < na) {
-                const int a = fA + a0 + lane;
-                const float4 pa = c.p32[a];
-                const float d[3] = {pa.x, pa.y, pa.z};
-                // the tile loop included the pair of a with itself: zero force, potential
-                // m_a phi(0) = m_a (-1.4) 2 / (h_a + h_a) computed exactly as the loop did
-                const float ha = c.h32[a];
-                const float self_pot = pa.w * (__fdividef(2.0f, ha + ha) * -1.4f);
-                float Cf[20];
+            for (int gi = 0; gi < ng; ++gi) {
+                const int a0 = A0 + gi * kGroupMixed;
+                const int na = min(kGroupMixed, nA - a0);
+                const float2 st = sm.gacc[gi * 32 + lane];
+                const double tot = __dadd_rn((double)st.x, (double)st.y);  // lane l < 4 na: particle l/4, quantity l%4
+                const double q0v = __shfl_sync(0xffffffffu, tot, (4 * lane) & 31);
+                const double q1v = __shfl_sync(0xffffffffu, tot, (4 * lane + 1) & 31);
+                const double q2v = __shfl_sync(0xffffffffu, tot, (4 * lane + 2) & 31);
+                const double q3v = __shfl_sync(0xffffffffu, tot, (4 * lane + 3) & 31);
+                if (lane < na) {
+                    const int a = fA + a0 + lane;
+                    const float4 pa = c.p32[a];
+                    const float d[3] = {pa.x, pa.y, pa.z};
+                    // the tile loop included the pair of a with itself: zero force, potential
+                    // m_a phi(0) = m_a (-1.4) 2 / (h_a + h_a) computed exactly as the loop did
+                    const float ha = c.h32[a];
+                    const float self_pot = pa.w * (__fdividef(2.0f, ha + ha) * -1.4f);
+                    float Cf[20];
 #pragma unroll
-                for (int i = 0; i < 20; ++i) Cf[i] = c.coef32[(int64_t)s * 20 + i];
-                float phf, af[3];
-                taylor_eval<float>(Cf, d, phf, af);
-                const int o = c.pidx[a];
-                c.acc[3 * (int64_t)o] = q0v + (double)af[0];
-                c.acc[3 * (int64_t)o + 1] = q1v + (double)af[1];
-                c.acc[3 * (int64_t)o + 2] = q2v + (double)af[2];
-                if (c.pot) c.pot[o] = q3v + (double)phf - (double)self_pot;
-            }
-            if (NB && lane < na) {
-                const int a = fA + a0 + lane;
-                int n = g.run[0];
-#pragma unroll
-                for (int i = 1; i < kGroupMixed; ++i)
-                    if (lane == i) n = g.run[i];
-                c.nb_counts[c.pidx[a]] = n;
-                if (n > kNbRowCap) {
-                    const int q = atomicAdd(&c.status[ST_LONGROWS], 1);
-                    if (q < c.cap_long) c.nb_long[q] = make_int2(a, s);
+                    for (int i = 0; i < 20; ++i) Cf[i] = c.coef32[(int64_t)s * 20 + i];
+                    float phf, af[3];
+                    taylor_eval<float>(Cf, d, phf, af);
+                    const int o = c.pidx[a];
+                    c.acc[3 * (int64_t)o] = q0v + (double)af[0];
+                    c.acc[3 * (int64_t)o + 1] = q1v + (double)af[1];
+                    c.acc[3 * (int64_t)o + 2] = q2v + (double)af[2];
+                    if (c.pot) c.pot[o] = q3v + (double)phf - (double)self_pot;
+                    if (NB) {
+                        const int n = sm.grun[gi * kGroupMixed + lane];
+                        c.nb_counts[o] = n;
+                        if (n > kNbRowCap) {
+                            const int q = atomicAdd(&c.status[ST_LONGROWS], 1);
+                            if (q < c.cap_long) c.nb_long[q] = make_int2(a, s);
+                        }
+                    }
                 }
             }
             __syncwarp();
