@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
                 n = 2 * n;
                 continue;
             }
-            while (n & 1) n >>= 1;
-            n += 1;
+            // next node in depth-first order: drop the trailing one bits, then step right
+            n = (n >> (__ffs(~n) - 1)) + 1;
             if (n == 1) break;
         }
         c.near_nr[s] = nr;
