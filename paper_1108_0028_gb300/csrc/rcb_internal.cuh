@@ -273,6 +273,7 @@ struct rcb_tree {
     // backward
     int32_t *tnear_off, *tnear_sink, *tfar_off, *tfar_sink;
     int bwd_valid;
+    int walk_pair;  // walk two sinks per thread (set when the last walk's longest far list exceeded 1024)
     double *adj;  // per-node adjoints
 
     int64_t stats_fallback;

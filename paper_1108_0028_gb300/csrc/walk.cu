@@ -151,6 +151,159 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
     }
 }
 
+// The same walk for two consecutive sinks at once (siblings in label order, whose walks share
+// most nodes): one thread follows the union of the two depth-first walks and loads every node
+// once.  A sink that did not open a node the other opened sits out the node's subtree (skip =
+// that node) and rejoins when the walk leaves it.  Each sink still meets its own nodes in
+// depth-first order, so its lists are the ones its own walk writes.
+struct WSink {
+    int A;
+    float3 rgA, comA, rgAabs, comAabs;
+    float hA;
+    int64_t near_base, far_base;
+    int nr, nnr, nf;
+};
+
+__device__ inline void wsink_init(const WalkCtx &c, int s, WSink &k) {
+    k.A = c.sinks[s];
+    const float4 a32 = c.w32[2 * k.A], b32 = c.w32[2 * k.A + 1];
+    k.rgA = make_float3(a32.x, a32.y, a32.z);
+    k.comA = make_float3(b32.x, b32.y, b32.z);
+    k.hA = __double2float_rn(c.nhnode[k.A]);
+    k.rgAabs = make_float3(fabsf(k.rgA.x), fabsf(k.rgA.y), fabsf(k.rgA.z));
+    k.comAabs = make_float3(fabsf(k.comA.x), fabsf(k.comA.y), fabsf(k.comA.z));
+    k.near_base = (int64_t)s * c.cap_near;
+    k.far_base = (int64_t)s * c.cap_far;
+    k.nr = k.nnr = k.nf = 0;
+}
+
+// The decision for one non-empty node (as in k_walk): 1 near from the front, 2 near from the
+// back, 3 far, 4 open.  The entry is written here.
+__device__ __forceinline__ int wsink_visit(const WalkCtx &c, WSink &k, int n, const float4 &na, const float4 &nb,
+                                           bool is_leaf, int &nfallback) {
+    const float dx = k.rgA.x - na.x, dy = k.rgA.y - na.y, dz = k.rgA.z - na.z;
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    const float rr = k.hA + na.w;
+    const float f = d2 - rr * rr;
+    const float F = sq(k.rgAabs.x + fabsf(na.x)) + sq(k.rgAabs.y + fabsf(na.y)) + sq(k.rgAabs.z + fabsf(na.z)) + rr * rr;
+    const float B = F * 0x1p-20f + 1e-30f;
+    bool reach;
+    if (f < -B) reach = true;
+    else if (f > B) reach = false;
+    else {
+        ++nfallback;
+        const double e2 = dist2_rn(c.nrg[3 * (int64_t)k.A], c.nrg[3 * (int64_t)k.A + 1], c.nrg[3 * (int64_t)k.A + 2],
+                                   c.nrg[3 * (int64_t)n], c.nrg[3 * (int64_t)n + 1], c.nrg[3 * (int64_t)n + 2]);
+        const double r = __dadd_rn(c.nhnode[k.A], c.nhint[n]);
+        reach = e2 < __dmul_rn(r, r);
+    }
+    if (reach) {
+        if (!is_leaf) return 4;
+        if (k.nr + k.nnr < c.cap_near) c.near_list[k.near_base + k.nr] = n;
+        ++k.nr;
+        return 1;
+    }
+    const float ex = k.comA.x - nb.x, ey = k.comA.y - nb.y, ez = k.comA.z - nb.z;
+    const float R2 = ex * ex + ey * ey + ez * ez;
+    const float fm = nb.w * nb.w - c.theta2f * R2;
+    const float Fm = nb.w * nb.w +
+                     c.theta2f * (sq(k.comAabs.x + fabsf(nb.x)) + sq(k.comAabs.y + fabsf(nb.y)) + sq(k.comAabs.z + fabsf(nb.z)));
+    const float Bm = Fm * 0x1p-20f + 1e-30f;
+    bool mac;
+    if (fm < -Bm) mac = true;
+    else if (fm > Bm) mac = false;
+    else {
+        ++nfallback;
+        const double R2d = dist2_rn(c.ncom[3 * (int64_t)k.A], c.ncom[3 * (int64_t)k.A + 1], c.ncom[3 * (int64_t)k.A + 2],
+                                    c.ncom[3 * (int64_t)n], c.ncom[3 * (int64_t)n + 1], c.ncom[3 * (int64_t)n + 2]);
+        const double H = c.nH[n];
+        mac = __dmul_rn(H, H) < __dmul_rn(c.theta2, R2d);
+    }
+    if (mac) {
+        if (k.nf < c.cap_far) c.far_list[k.far_base + k.nf] = n;
+        ++k.nf;
+        return 3;
+    }
+    if (!is_leaf) return 4;
+    if (k.nr + k.nnr < c.cap_near) c.near_list[k.near_base + c.cap_near - 1 - k.nnr] = n;
+    ++k.nnr;
+    return 2;
+}
+
+// m lies in the subtree of a (heap labels)
+__device__ inline bool in_subtree(int m, int a) {
+    const int d = (31 - __clz(m)) - (31 - __clz(a));
+    return d >= 0 && (m >> d) == a;
+}
+
+__global__ void __launch_bounds__(kWalkWarps * 32) k_walk_pair(WalkCtx c) {
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s0 = 2 * t, s1 = 2 * t + 1;
+    const bool v0 = s0 < c.nsinks, v1 = s1 < c.nsinks;
+    WSink k0, k1;
+    int nfallback = 0;
+    bool limit = false;
+    if (v0) wsink_init(c, s0, k0);
+    if (v1) wsink_init(c, s1, k1);
+    if (v0) {
+        int skip0 = 0, skip1 = v1 ? 0 : 1;  // 1: the whole tree (no second sink)
+        const int leaf0 = 1 << c.L;
+        int n = 2;
+        int64_t iter = 0;
+        const int64_t max_iter = 2 * c.nn + 8;
+        while (true) {
+            if (++iter > max_iter) {
+                limit = true;
+                break;
+            }
+            if (skip0 && !in_subtree(n, skip0)) skip0 = 0;
+            if (skip1 && !in_subtree(n, skip1)) skip1 = 0;
+            const float4 na = c.w32[2 * n];
+            if (na.w >= 0.f) {  // non-empty
+                const float4 nb = c.w32[2 * n + 1];
+                const bool is_leaf = n >= leaf0;
+                const int a0 = skip0 ? 0 : wsink_visit(c, k0, n, na, nb, is_leaf, nfallback);
+                const int a1 = skip1 ? 0 : wsink_visit(c, k1, n, na, nb, is_leaf, nfallback);
+                if (a0 == 4 || a1 == 4) {
+                    if (!skip0 && a0 != 4) skip0 = n;
+                    if (!skip1 && a1 != 4) skip1 = n;
+                    n = 2 * n;
+                    continue;
+                }
+            }
+            // next node in depth-first order: drop the trailing one bits, then step right
+            n = (n >> (__ffs(~n) - 1)) + 1;
+            if (n == 1) break;
+        }
+        c.near_nr[s0] = k0.nr;
+        c.near_nn[s0] = k0.nnr;
+        c.far_n[s0] = k0.nf;
+        if (v1) {
+            c.near_nr[s1] = k1.nr;
+            c.near_nn[s1] = k1.nnr;
+            c.far_n[s1] = k1.nf;
+        }
+    }
+    int mn = v0 ? k0.nr + k0.nnr : 0, mf = v0 ? k0.nf : 0;
+    if (v1) {
+        mn = max(mn, k1.nr + k1.nnr);
+        mf = max(mf, k1.nf);
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mf = max(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+        nfallback += __shfl_xor_sync(0xffffffffu, nfallback, o);
+    }
+    const bool anylimit = __any_sync(0xffffffffu, limit);
+    if (lane == 0) {
+        atomicMax(&c.status[ST_MAXNEAR], mn);
+        atomicMax(&c.status[ST_MAXFAR], mf);
+        if (nfallback) atomicAdd(&c.status[ST_FALLBACK], nfallback);
+        if (anylimit) atomicOr(&c.status[ST_ERR], ERRBIT_LIMIT);
+    }
+}
+
 // Per sink: (sink particles) x (particles of all near cells) and x (of reachable cells).
 __global__ void k_pair_counts(const int32_t *sinks, int nsinks, const int32_t *ncount, const int32_t *near_list,
                               const int32_t *near_nr, const int32_t *near_nn, int cap_near,
@@ -221,14 +374,23 @@ int walk_tree(rcb_tree *t) {
         c.near_nn = t->near_nn;
         c.far_n = t->far_n;
         RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_MAXNEAR, 0, 3 * sizeof(int), st));
-        int blocks = (t->nsinks + kWalkWarps * 32 - 1) / (kWalkWarps * 32);
-        if (blocks > 0) k_walk<<<blocks, kWalkWarps * 32, 0, st>>>(c); note_launch();
+        // Long walks (concentrated inputs) share node loads between sibling sinks; short ones keep
+        // one sink per thread for more parallelism.  Both write the same lists.
+        if (t->walk_pair) {
+            const int nthreads = (t->nsinks + 1) / 2;
+            const int blocks = (nthreads + kWalkWarps * 32 - 1) / (kWalkWarps * 32);
+            if (blocks > 0) k_walk_pair<<<blocks, kWalkWarps * 32, 0, st>>>(c); note_launch();
+        } else {
+            const int blocks = (t->nsinks + kWalkWarps * 32 - 1) / (kWalkWarps * 32);
+            if (blocks > 0) k_walk<<<blocks, kWalkWarps * 32, 0, st>>>(c); note_launch();
+        }
         RCB_CUDA_TRY(cudaGetLastError());
         RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status, t->d_status, ST_NWORDS * sizeof(int), cudaMemcpyDeviceToHost, st));
         RCB_CUDA_TRY(cudaStreamSynchronize(st));
         if (t->h_status[ST_ERR] & ERRBIT_LIMIT) return RCB_ERR_LIMIT;
         int need_near = t->h_status[ST_MAXNEAR], need_far = t->h_status[ST_MAXFAR];
         t->stats_fallback = t->h_status[ST_FALLBACK];
+        t->walk_pair = need_far > 1024;
         if (need_near <= t->cap_near && need_far <= t->cap_far) return RCB_OK;
         // grow the per-sink list capacities and walk again
         int cn = std::max(t->cap_near, ((need_near + 31) / 32) * 32 + 32);

@@ -115,3 +115,23 @@ def test_invalid_inputs_rejected():
         with pytest.raises(rcb.RCBError) as e:
             rcb.RCBTree(*_gpu(xx, mm, hh))
         assert e.value.status == rcb.RCB_ERR_ARG
+
+
+def test_paired_walk_writes_the_same_lists():
+    # A concentrated input whose longest far list exceeds 1024 entries: the first build walks one
+    # sink per thread, and the rebuild (same handle) walks two sibling sinks per thread.  The
+    # lists must be identical, entry for entry and in order.
+    import paper_1108_0028_gb300 as rcb
+    N = 65536
+    x, m, h = synth.make_particles("plummer", N, synth.seed_for(6, 1), "loguniform10")
+    tree = rcb.RCBTree(*_gpu(x, m, h), theta=0.5, precision="mixed")
+    assert tree.info()["cap_far"] > 1100  # so the longest far list exceeded 1024
+    first = tree.export_lists()
+    tree.rebuild(*_gpu(x, m, h))
+    second = tree.export_lists()
+    assert first.keys() == second.keys()
+    for k in first:
+        assert np.array_equal(first[k], second[k]), k
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(0.5)
+    assert np.array_equal(tree.export_topology()["leaf_of"], ref.leaf_of())
