@@ -281,6 +281,25 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
     g_acc = 2.0 * acc_b
     tree.gravity_backward(g_acc)
     bwd_ms = staged(lambda: tree.gravity_backward(g_acc), ["backward"])
+    # tree update (Sec. 2.1.8): integrity check, refit and a new walk, when every particle is
+    # still in its ll-cell; positions displaced by 1e-12 (alternating with the originals)
+    gen = torch.Generator(device=xt.device)
+    gen.manual_seed(5)
+    xj = xt + 1e-12 * torch.randn(xt.shape, dtype=xt.dtype, device=xt.device, generator=gen)
+    tree.rebuild(xt, mt, ht)
+    upd = []
+    for i in range(5):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rebuilt = tree.update(xj if i % 2 == 0 else xt, mt, ht, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rebuilt:
+            raise RuntimeError("tree update rebuilt although no particle left its ll-cell")
+        upd.append(e0.elapsed_time(e1))
+    update_ms = statistics.mean(upd)
     L = tree.info()["L"]
     build_bytes = a.n * (72 * L + 56)  # every level reads and writes 36 B per particle, h gathered once
     per_stage = {
@@ -297,6 +316,8 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
         "gravity": {"ms": grav_ms, "mparticles_s": job_throughput(world, a.n, grav_ms), "path": "rcb_gravity alone"},
         "neighbours_gravity_fused": {"ms": fused_ms, "mparticles_s": job_throughput(world, a.n, fused_ms),
                                      "path": "rcb_gravity_neighbours + compaction (the step's path)"},
+        "update": {"ms": update_ms, "mparticles_s": job_throughput(world, a.n, update_ms),
+                   "path": "rcb_update: integrity check, refit, new walk (no particle left its ll-cell)"},
         "gravity_backward": {"ms": bwd_ms, "mparticles_s": job_throughput(world, a.n, bwd_ms),
                              "path": "rcb_gravity_backward on the built tree (lists already transposed)"},
     }

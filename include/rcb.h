@@ -151,6 +151,24 @@ int rcb_gravity_backward(rcb_tree *tree, const double *g_acc, const double *g_po
 int rcb_refit(rcb_tree *tree, const double *x, const double *m, void *stream);
 
 /*
+ * rcb_update -- Sec. 2.1.8 tree update with its integrity check, for the same particles at new
+ *   positions (a time step).  A particle is still in its ll-cell when, at its new position, it
+ *   lies on the side of every ancestor's split plane that it was sorted to (x_axis < split for a
+ *   left child, not less for a right child; only planes with particles on both sides count;
+ *   non-finite coordinates count as outside).
+ *   - every particle inside: the smoothing lengths are replaced, the moments, boxes and radii
+ *     refitted bottom-up (as rcb_refit) and the tree walked again, so the interaction lists
+ *     follow the new positions; the splits stay as built.
+ *   - otherwise: the tree is rebuilt in place (as rcb_build on the same handle, with its
+ *     parameters and allocator).
+ *   x  device, [N][3] float64, original order;  m, h  device, [N] float64
+ *   rebuilt  host, may be NULL: 1 if the tree was rebuilt, 0 if it was updated
+ *   Synchronises `stream`.  Errors: RCB_ERR_ARG (invalid input), RCB_ERR_STATE (no tree), and
+ *   those of rcb_build.
+ */
+int rcb_update(rcb_tree *tree, const double *x, const double *m, const double *h, int32_t *rebuilt, void *stream);
+
+/*
  * rcb_neighbour_offsets_noalloc -- the paper has no counterpart: this is a convenience for
  *   callers that cannot allocate device memory when they need neighbour offsets (for example
  *   code being recorded into a CUDA graph, where cudaMalloc is not allowed, or an application

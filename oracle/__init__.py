@@ -75,6 +75,7 @@ def lib():
                 "orc_direct": (None, [_P, _P, _P, _I64, _P, _I64, _P, _P]),
                 "orc_direct_grad": (None, [_P, _P, _P, _I64, _P, _P, _P, _P]),
                 "orc_refit": (ctypes.c_int, [_P, _P, _P]),
+                "orc_update": (ctypes.c_int, [_P, _P, _P, _P, _P]),
                 "orc_gravity_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
                 "orc_num_threads": (ctypes.c_int, []),
                 "orc_set_num_threads": (None, [ctypes.c_int]),
@@ -301,6 +302,20 @@ class OracleTree:
         r = lib().orc_refit(self._t, _ptr(x), _ptr(m))
         if r != OK:
             raise RuntimeError(f"oracle refit failed: {r}")
+
+    def update(self, x, m, h) -> int:
+        """Sec. 2.1.8 tree update: the number of particles that left their ll-cells at positions
+        x (original order).  When it is zero, h is replaced, the tree refitted and the lists
+        dropped (walk again); otherwise the tree is unchanged (build a new one)."""
+        x, m, h = _f64(x, (-1, 3)), _f64(m), _f64(h)
+        out = np.zeros(1, np.int64)
+        r = lib().orc_update(self._t, _ptr(x), _ptr(m), _ptr(h), _ptr(out))
+        if r != OK:
+            raise RuntimeError(f"oracle update failed: {r}")
+        if out[0] == 0:
+            self.x, self.m, self.h = x, m, h
+            self.walked = False
+        return int(out[0])
 
     def gravity_backward(self, gacc, gpot=None):
         ga = _f64(gacc, (-1, 3))

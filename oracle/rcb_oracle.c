@@ -881,6 +881,41 @@ int orc_refit(orc_tree *t, const double *x, const double *m) {
     return ORC_OK;
 }
 
+/* Tree update with its integrity check (Sec. 2.1.8).  A particle is still in its ll-cell when,
+ * at its new position (original order), it lies on the side of every ancestor's split plane that
+ * it was sorted to: x_axis < split for a left child, not less for a right child.  Only planes
+ * with particles on both sides count: a cell whose other child is empty separates nothing (a
+ * one-particle cell is split through that particle).  A non-finite coordinate counts as
+ * outside.  *outside receives the number of particles that left their
+ * ll-cells.  When it is zero, the smoothing lengths are replaced, the moments, boxes and radii
+ * are refitted (orc_refit) and the interaction lists are dropped, for the caller to walk again;
+ * otherwise the tree is left unchanged and the caller rebuilds. */
+int orc_update(orc_tree *t, const double *x, const double *m, const double *h, int64_t *outside) {
+    int64_t out = 0, leaf0 = (int64_t)1 << t->L;
+    for (int64_t j = 0; j < leaf0; ++j) {
+        int64_t n0 = leaf0 + j;
+        for (int64_t a = t->first[n0]; a < t->first[n0] + t->count[n0]; ++a) {
+            int64_t o = t->perm[a];
+            int ok = isfinite(x[3 * o]) && isfinite(x[3 * o + 1]) && isfinite(x[3 * o + 2]);
+            for (int64_t n = n0; n > 1 && ok; n >>= 1) {
+                int64_t par = n >> 1;
+                if (t->count[n ^ 1] == 0) continue;
+                double v = x[3 * o + t->axis[par]];
+                ok = (n & 1) == 0 ? (v < t->split[par]) : !(v < t->split[par]);
+            }
+            if (!ok) ++out;
+        }
+    }
+    *outside = out;
+    if (out > 0) return ORC_OK;
+    for (int64_t i = 0; i < t->N; ++i)
+        if (!isfinite(h[t->perm[i]]) || !(h[t->perm[i]] > 0.0)) return ORC_ERR_ARG;
+    for (int64_t i = 0; i < t->N; ++i) t->h[i] = h[t->perm[i]];
+    int r = orc_refit(t, x, m);
+    free_lists(t);
+    return r;
+}
+
 /* Vector-Jacobian product of orc_gravity with frozen lists, with respect to positions and
  * masses.  Node moments are the exact functions M = sum m_b, COM = sum m_b x_b / M,
  * Q = sum m_b (3 d d - d^2 I), d = x_b - COM (Eq. 2 reproduces Eq. 1 exactly); because

@@ -1370,6 +1370,89 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
     return RCB_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Tree integrity check (Sec. 2.1.8).  A particle stays in its ll-cell when, at its new position,
+// it lies on the side of every ancestor's split plane that it was sorted to: x_axis < split for a
+// left child, not less for a right child.  Only planes with particles on both sides count (a
+// cell whose other child is empty separates nothing; a one-particle cell is split through that
+// particle).  The ancestors' planes of one sink make a box,
+// lo <= x < hi per axis (lo the largest split among right turns, hi the smallest among left
+// turns; unbounded otherwise); one warp per sink builds it and tests the sink's particles
+// against it.  Non-finite coordinates count as outside.
+
+__global__ void k_integrity(const int32_t *sinks, int nsinks, const int32_t *nfirst, const int32_t *ncount,
+                            const int32_t *naxis, const double *nsplit, const int32_t *pidx, const double *x,
+                            int *outside) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    int nout = 0;
+    for (int s = gw; s < nsinks; s += nw) {
+        const int A = sinks[s];
+        double lo0 = -INFINITY, lo1 = -INFINITY, lo2 = -INFINITY, hi0 = INFINITY, hi1 = INFINITY, hi2 = INFINITY;
+        for (int n = A; n > 1; n >>= 1) {
+            if (ncount[n ^ 1] == 0) continue;
+            const int p = n >> 1, ax = naxis[p];
+            const double sp = nsplit[p];
+            if (n & 1) {  // right child: x_axis >= split
+                if (ax == 0) lo0 = fmax(lo0, sp);
+                else if (ax == 1) lo1 = fmax(lo1, sp);
+                else lo2 = fmax(lo2, sp);
+            } else {      // left child: x_axis < split
+                if (ax == 0) hi0 = fmin(hi0, sp);
+                else if (ax == 1) hi1 = fmin(hi1, sp);
+                else hi2 = fmin(hi2, sp);
+            }
+        }
+        const int f = nfirst[A], cnt = ncount[A];
+        for (int a = f + lane; a < f + cnt; a += 32) {
+            const int64_t o = pidx[a];
+            const double v0 = x[3 * o], v1 = x[3 * o + 1], v2 = x[3 * o + 2];
+            const bool in = v0 >= lo0 && v0 < hi0 && v1 >= lo1 && v1 < hi1 && v2 >= lo2 && v2 < hi2;
+            nout += in ? 0 : 1;
+        }
+    }
+    for (int o = 16; o >= 1; o >>= 1) nout += __shfl_xor_sync(0xffffffffu, nout, o);
+    if (lane == 0 && nout) atomicAdd(outside, nout);
+}
+
+__global__ void k_gather_h(const double *h, int64_t N, const int32_t *pidx, double *ph, int *status) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        const double v = h[pidx[p]];
+        if (!isfinite(v) || !(v > 0.0)) atomicOr(&status[ST_ERR], ERRBIT_ARG);
+        ph[p] = v;
+    }
+}
+
+int integrity_outside(rcb_tree *t, const double *x, int64_t *outside) {
+    if (t->nsinks <= 0) return RCB_ERR_STATE;
+    cudaStream_t st = t->stream;
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, ST_NWORDS * sizeof(int), st));
+    const int nsm = sm_count();
+    const int grid = std::max(1, std::min((t->nsinks + 7) / 8, nsm * 8));
+    k_integrity<<<grid, 256, 0, st>>>(t->sinks, t->nsinks, t->nfirst, t->ncount, t->naxis, t->nsplit, t->pidx, x,
+                                      t->d_status + ST_OUTSIDE); note_launch();
+    RCB_CUDA_TRY(cudaGetLastError());
+    const int rc = read_status(t);
+    if (rc) return rc;
+    *outside = t->h_status[ST_OUTSIDE];
+    return RCB_OK;
+}
+
+// New smoothing lengths (original order) into tree order; the leaf pass derives the float32
+// copies and the radii from them.
+int gather_h(rcb_tree *t, const double *h) {
+    cudaStream_t st = t->stream;
+    RCB_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), st));
+    const int nsm = sm_count();
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((t->N + 255) / 256, (int64_t)nsm * 8));
+    k_gather_h<<<grid, 256, 0, st>>>(h, t->N, t->pidx, t->ph, t->d_status); note_launch();
+    RCB_CUDA_TRY(cudaGetLastError());
+    const int rc = read_status(t);
+    if (rc) return rc;
+    if (t->h_status[ST_ERR] & ERRBIT_ARG) return RCB_ERR_ARG;
+    return RCB_OK;
+}
+
 int refit_tree(rcb_tree *t, const double *x, const double *m) {
     if (t->nsinks <= 0) return RCB_ERR_STATE;
     cudaStream_t st = t->stream;

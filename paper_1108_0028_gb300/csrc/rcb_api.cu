@@ -315,6 +315,30 @@ int rcb_refit(rcb_tree *tree, const double *x, const double *m, void *stream) {
     return refit_tree(tree, x, m);
 }
 
+int rcb_update(rcb_tree *tree, const double *x, const double *m, const double *h, int32_t *rebuilt, void *stream) {
+    if (!tree || !x || !m || !h) return RCB_ERR_ARG;
+    tree->stream = (cudaStream_t)stream;
+    int64_t outside = 0;
+    int rc = rcb::integrity_outside(tree, x, &outside);
+    if (rc) return rc;
+    if (outside == 0) {
+        // every particle is still in its ll-cell: new h, refit bottom-up, new lists
+        if ((rc = rcb::gather_h(tree, h)) != RCB_OK) return rc;
+        if ((rc = rcb::refit_tree(tree, x, m)) != RCB_OK) return rc;
+        if ((rc = rcb::walk_tree(tree)) != RCB_OK) return rc;
+        tree->nb_valid = 0;
+        tree->bwd_valid = 0;
+        tree->near_pairs = tree->cand_pairs = -1;
+        if (rebuilt) *rebuilt = 0;
+        return RCB_OK;
+    }
+    rcb_tree *t = tree;
+    const rcb_params params = tree->params;
+    rc = rcb_build(x, m, h, tree->N, &params, tree->alloc, tree->release, tree->ctx, stream, &t);
+    if (rebuilt) *rebuilt = 1;
+    return rc;
+}
+
 int rcb_set_precision(rcb_tree *tree, int32_t precision) {
     if (!tree || (precision != RCB_FP64 && precision != RCB_MIXED)) return RCB_ERR_ARG;
     tree->params.precision = precision;

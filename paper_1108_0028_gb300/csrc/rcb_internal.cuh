@@ -31,6 +31,7 @@ enum StatusWord {
     ST_NSINKS = 7,     // non-empty ll-cells
     ST_NBFALLBACK = 8, // neighbour decisions taken in FP64
     ST_LONGROWS = 9,   // neighbour rows too long for the in-warp sort
+    ST_OUTSIDE = 10,   // particles outside their ll-cell (tree integrity check)
     ST_NWORDS = 16
 };
 enum ErrBits { ERRBIT_ARG = 1, ERRBIT_LIMIT = 2, ERRBIT_FIXED = 4, ERRBIT_STATE = 8 };
@@ -300,6 +301,8 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h);
 int refit_tree(rcb_tree *t, const double *x, const double *m);
 // walk.cu
 int walk_tree(rcb_tree *t);
+int integrity_outside(rcb_tree *t, const double *x, int64_t *outside);  // build.cu
+int gather_h(rcb_tree *t, const double *h);                             // build.cu
 // neighbours.cu
 int neighbour_counts(rcb_tree *t, int64_t *counts, int *status);  // count pass into caller memory
 int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *needed);

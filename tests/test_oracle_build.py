@@ -216,3 +216,55 @@ def test_degenerate_inputs_build():
     assert nd["count"][1] == 50 and nd["H"][1] == 0.0
     leaf0 = 1 << T.L
     assert sum(nd["count"][leaf0:]) == 50
+
+
+def _route_leaves(nodes, L, x):
+    """Leaf number of every position when routed from the root through the stored splits
+    (x_axis < split to the left child; into the non-empty child where the other is empty, since
+    such a plane separates no particles): an independent statement of the ll-cell membership."""
+    n = np.ones(x.shape[0], np.int64)
+    cnt = nodes["count"]
+    for _ in range(L):
+        ax = nodes["axis"][n]
+        right = ~(x[np.arange(x.shape[0]), ax] < nodes["split"][n])
+        right = np.where(cnt[2 * n] == 0, True, np.where(cnt[2 * n + 1] == 0, False, right))
+        n = 2 * n + right.astype(np.int64)
+    return n - (1 << L)
+
+
+@pytest.mark.parametrize("sigma", [0.0, 1e-3, 3e-2])
+def test_integrity_check_counts_particles_that_left_their_ll_cell(sigma):
+    # Sec. 2.1.8: the update keeps the tree only if no particle crossed its ll-cell's border.  The
+    # count must equal the number of particles whose routed leaf differs from their leaf.
+    N = 3000
+    x, m, h = synth.make_particles("plummer", N, 71, "loguniform10")
+    ref = oracle.OracleTree(x, m, h)
+    x2 = synth.jitter(x, sigma, 72) if sigma > 0 else x.copy()
+    expect = int(np.sum(_route_leaves(ref.nodes(), ref.L, x2) != ref.leaf_of()))
+    if sigma == 0.0:
+        assert expect == 0
+    if sigma == 3e-2:
+        assert expect > 100
+    before = ref.nodes()
+    got = ref.update(x2, m, h)
+    assert got == expect
+    if got > 0:   # the tree is left as it was
+        after = ref.nodes()
+        assert np.array_equal(after["com"], before["com"]) and np.array_equal(after["split"], before["split"])
+
+
+def test_update_inside_equals_refit_with_new_h():
+    # every particle still inside: the update is a refit with the new smoothing lengths (radii
+    # from the new h), the splits unchanged
+    N = 3000
+    x, m, h = synth.make_particles("sphere", N, 73, "loguniform10")
+    x2 = synth.jitter(x, 1e-9, 74)
+    m2 = m * (1.0 + 0.01 * np.random.default_rng(75).random(N))
+    h2 = h * (1.0 + 0.05 * np.random.default_rng(76).random(N))
+    a = oracle.OracleTree(x, m, h)
+    assert a.update(x2, m2, h2) == 0
+    b = oracle.OracleTree(x, m, h2)      # same partition (built at x), radii from h2
+    b.refit(x2, m2)
+    na, nb = a.nodes(), b.nodes()
+    for k in ("split", "axis", "com", "bmin", "bmax", "rg", "hint", "hnode", "Q", "mass"):
+        assert np.array_equal(na[k], nb[k]), k
