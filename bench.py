@@ -300,6 +300,21 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
             raise RuntimeError("tree update rebuilt although no particle left its ll-cell")
         upd.append(e0.elapsed_time(e1))
     update_ms = statistics.mean(upd)
+    # SPH density over the neighbour CSR of the built tree (the first consumer of the lists)
+    tree.rebuild(xt, mt, ht)
+    off_d, idx_d = tree.neighbours()
+    dens = []
+    for _ in range(5):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tree.density(off_d, idx_d, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dens.append(e0.elapsed_time(e1))
+    density_ms = statistics.mean(dens)
+    del off_d, idx_d
     L = tree.info()["L"]
     build_bytes = a.n * (72 * L + 56)  # every level reads and writes 36 B per particle, h gathered once
     per_stage = {
@@ -316,6 +331,8 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
         "gravity": {"ms": grav_ms, "mparticles_s": job_throughput(world, a.n, grav_ms), "path": "rcb_gravity alone"},
         "neighbours_gravity_fused": {"ms": fused_ms, "mparticles_s": job_throughput(world, a.n, fused_ms),
                                      "path": "rcb_gravity_neighbours + compaction (the step's path)"},
+        "density": {"ms": density_ms, "mparticles_s": job_throughput(world, a.n, density_ms),
+                    "path": "rcb_density over the CSR of rcb_neighbours (cubic spline, support 2h)"},
         "update": {"ms": update_ms, "mparticles_s": job_throughput(world, a.n, update_ms),
                    "path": "rcb_update: integrity check, refit, new walk (no particle left its ll-cell)"},
         "gravity_backward": {"ms": bwd_ms, "mparticles_s": job_throughput(world, a.n, bwd_ms),

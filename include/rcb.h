@@ -169,6 +169,21 @@ int rcb_refit(rcb_tree *tree, const double *x, const double *m, void *stream);
 int rcb_update(rcb_tree *tree, const double *x, const double *m, const double *h, int32_t *rebuilt, void *stream);
 
 /*
+ * rcb_density -- SPH density by summation over the neighbour lists (Sec. 2.3: smoothed
+ *   quantities are kernel-weighted sums over the neighbours), with the cubic spline kernel W
+ *   of support 2h the paper uses:
+ *     rho_a = m_a W(0, h_a) + sum_{b in nb(a)} m_b W(|r_a - r_b|, h_a)
+ *   over the tree's current positions, masses and smoothing lengths (those of the last
+ *   rcb_build, rcb_refit or rcb_update).
+ *   offsets, idx  device, the CSR written by rcb_neighbours for this tree (original order)
+ *   rho           device, [N] float64 out, original order
+ *   Pair offsets and W in float32 on a float32 pair split of the positions; the result is
+ *   float64.  Does not synchronise.  Errors: RCB_ERR_ARG, RCB_ERR_ALLOC (scratch of 32 B per
+ *   particle, allocated on first use through the tree's allocator).
+ */
+int rcb_density(rcb_tree *tree, const int64_t *offsets, const int32_t *idx, double *rho, void *stream);
+
+/*
  * rcb_neighbour_offsets_noalloc -- the paper has no counterpart: this is a convenience for
  *   callers that cannot allocate device memory when they need neighbour offsets (for example
  *   code being recorded into a CUDA graph, where cudaMalloc is not allowed, or an application

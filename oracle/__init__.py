@@ -76,6 +76,8 @@ def lib():
                 "orc_direct_grad": (None, [_P, _P, _P, _I64, _P, _P, _P, _P]),
                 "orc_refit": (ctypes.c_int, [_P, _P, _P]),
                 "orc_update": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+                "orc_kernel_W": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+                "orc_density_csr": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
                 "orc_gravity_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
                 "orc_num_threads": (ctypes.c_int, []),
                 "orc_set_num_threads": (None, [ctypes.c_int]),
@@ -154,6 +156,22 @@ def taylor_eval(C, d):
     acc = np.zeros(3)
     lib().orc_taylor_eval(_ptr(C_a), _ptr(d_a), _ptr(phi), _ptr(acc))
     return float(phi[0]), acc
+
+
+def kernel_W(r, h):
+    return lib().orc_kernel_W(float(r), float(h))
+
+
+def density(x, m, h, offsets, idx):
+    """SPH density by summation over neighbour rows (CSR, original order), FP64."""
+    x, m, h = _f64(x, (-1, 3)), _f64(m), _f64(h)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    ix = np.ascontiguousarray(idx, dtype=np.int32)
+    rho = np.zeros(x.shape[0])
+    r = lib().orc_density_csr(x.shape[0], _ptr(x), _ptr(m), _ptr(h), _ptr(off), _ptr(ix), _ptr(rho))
+    if r != OK:
+        raise RuntimeError(f"oracle density failed: {r}")
+    return rho
 
 
 def direct(x, m, h, targets=None):

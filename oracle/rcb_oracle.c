@@ -881,6 +881,35 @@ int orc_refit(orc_tree *t, const double *x, const double *m) {
     return ORC_OK;
 }
 
+/* SPH density by summation over the neighbour lists (Sec. 2.3: smoothed quantities are sums of
+ * kernel-weighted particle properties over the neighbours):
+ *   rho_a = m_a W(0, h_a) + sum_{b in nb(a)} m_b W(r_ab, h_a),
+ * with the cubic spline kernel W the paper uses (Monaghan & Lattanzio 1985, support 2h),
+ *   W(r, h) = (1 - 3/2 q^2 + 3/4 q^3) / (pi h^3)   0 <= q < 1
+ *             (2 - q)^3 / (4 pi h^3)                1 <= q < 2,   q = r / h,
+ * and nb(a) the neighbour rows of orc_neighbours (b != a, r_ab < 2 h_a), original order. */
+double orc_kernel_W(double r, double h) {
+    double q = r / h, w;
+    if (q < 1.0) w = 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+    else if (q < 2.0) w = 0.25 * (2.0 - q) * (2.0 - q) * (2.0 - q);
+    else w = 0.0;
+    return w / (3.14159265358979323846 * h * h * h);
+}
+
+int orc_density_csr(int64_t N, const double *x, const double *m, const double *h, const int64_t *off,
+                    const int32_t *idx, double *rho) {
+    for (int64_t a = 0; a < N; ++a) {
+        double s = m[a] * orc_kernel_W(0.0, h[a]);
+        for (int64_t k = off[a]; k < off[a + 1]; ++k) {
+            int64_t b = idx[k];
+            double dx = x[3 * a] - x[3 * b], dy = x[3 * a + 1] - x[3 * b + 1], dz = x[3 * a + 2] - x[3 * b + 2];
+            s += m[b] * orc_kernel_W(sqrt(dx * dx + dy * dy + dz * dz), h[a]);
+        }
+        rho[a] = s;
+    }
+    return ORC_OK;
+}
+
 /* Tree update with its integrity check (Sec. 2.1.8).  A particle is still in its ll-cell when,
  * at its new position (original order), it lies on the side of every ancestor's split plane that
  * it was sorted to: x_axis < split for a left child, not less for a right child.  Only planes

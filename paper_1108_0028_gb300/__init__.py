@@ -25,7 +25,7 @@ RCB_FP64, RCB_MIXED = 0, 1
 _PRECISION = {"fp64": RCB_FP64, "mixed": RCB_MIXED, RCB_FP64: RCB_FP64, RCB_MIXED: RCB_MIXED}
 
 RCB_FLAG_TIMING = 1
-SYMBOLS = ["rcb_build", "rcb_neighbours", "rcb_gravity", "rcb_gravity_neighbours", "rcb_gravity_backward", "rcb_refit", "rcb_update", "rcb_set_precision",
+SYMBOLS = ["rcb_build", "rcb_neighbours", "rcb_gravity", "rcb_gravity_neighbours", "rcb_gravity_backward", "rcb_refit", "rcb_update", "rcb_density", "rcb_set_precision",
            "rcb_tree_info", "rcb_export_topology", "rcb_export_lists", "rcb_stage_times", "rcb_free", "rcb_strerror",
            "rcb_neighbour_offsets_noalloc"]
 STAGES = ["ingest", "levels", "subtrees", "leaves", "walk", "build", "nb_count", "nb_fill", "nb_sort", "far", "near",
@@ -68,6 +68,7 @@ def lib():
                 "rcb_gravity_backward": (ctypes.c_int, [P, P, P, P, P, P]),
                 "rcb_refit": (ctypes.c_int, [P, P, P, P]),
                 "rcb_update": (ctypes.c_int, [P, P, P, P, P, P]),
+                "rcb_density": (ctypes.c_int, [P, P, P, P, P]),
                 "rcb_set_precision": (ctypes.c_int, [P, I32]),
                 "rcb_tree_info": (ctypes.c_int, [P, P]),
                 "rcb_export_topology": (ctypes.c_int, [P] + [P] * 16 + [P]),
@@ -164,6 +165,10 @@ def rcb_gravity_backward(tree, g_acc, g_pot, g_x, g_m, stream=None):
 
 def rcb_refit(tree, x, m, stream=None):
     _check(lib().rcb_refit(tree, _dptr(x), _dptr(m), _stream_ptr(stream)), "rcb_refit")
+
+
+def rcb_density(tree, offsets, idx, rho, stream=None) -> None:
+    _check(lib().rcb_density(tree, _dptr(offsets), _dptr(idx), _dptr(rho), _stream_ptr(stream)), "rcb_density")
 
 
 def rcb_update(tree, x, m, h, stream=None) -> bool:
@@ -274,6 +279,13 @@ class RCBTree:
 
     def refit(self, x, m, stream=None):
         rcb_refit(self._h, x, m, stream)
+
+    def density(self, offsets, idx, stream=None):
+        """SPH density (float64, original order) over the CSR of neighbours()."""
+        torch = _torch()
+        rho = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        rcb_density(self._h, offsets, idx, rho, stream)
+        return rho
 
     def update(self, x, m, h, stream=None) -> bool:
         """Integrity check, then refit + walk or rebuild (Sec. 2.1.8); True when rebuilt."""

@@ -89,7 +89,8 @@ void for_each_array(rcb_tree *t, F f) {
                   (void **)&t->chunk_part, (void **)&t->sinks, (void **)&t->sink_of_leaf, (void **)&t->near_nr,
                   (void **)&t->near_nn, (void **)&t->far_n, (void **)&t->near_list, (void **)&t->far_list,
                   (void **)&t->coef, (void **)&t->coef32, (void **)&t->nb_count, (void **)&t->nb_long, (void **)&t->nb_rows, (void **)&t->scan_tmp, (void **)&t->tnear_off,
-                  (void **)&t->tnear_sink, (void **)&t->tfar_off, (void **)&t->tfar_sink, (void **)&t->adj};
+                  (void **)&t->tnear_sink, (void **)&t->tfar_off, (void **)&t->tfar_sink, (void **)&t->adj,
+                  (void **)&t->dens_hl};
     for (void **q : p) f(q);
 }
 
@@ -337,6 +338,12 @@ int rcb_update(rcb_tree *tree, const double *x, const double *m, const double *h
     rc = rcb_build(x, m, h, tree->N, &params, tree->alloc, tree->release, tree->ctx, stream, &t);
     if (rebuilt) *rebuilt = 1;
     return rc;
+}
+
+int rcb_density(rcb_tree *tree, const int64_t *offsets, const int32_t *idx, double *rho, void *stream) {
+    if (!tree || !offsets || !idx || !rho) return RCB_ERR_ARG;
+    tree->stream = (cudaStream_t)stream;
+    return rcb::density(tree, offsets, idx, rho);
 }
 
 int rcb_set_precision(rcb_tree *tree, int32_t precision) {

@@ -274,6 +274,7 @@ struct rcb_tree {
     // backward
     int32_t *tnear_off, *tnear_sink, *tfar_off, *tfar_sink;
     int bwd_valid;
+    float4 *dens_hl;  // density scratch: per particle (hi, m) and (lo, 1/h) in float32, original order
     int walk_pair;  // walk two sinks per thread (set when the last walk's longest far list exceeded 1024)
     double *adj;  // per-node adjoints
 
@@ -303,6 +304,7 @@ int refit_tree(rcb_tree *t, const double *x, const double *m);
 int walk_tree(rcb_tree *t);
 int integrity_outside(rcb_tree *t, const double *x, int64_t *outside);  // build.cu
 int gather_h(rcb_tree *t, const double *h);                             // build.cu
+int density(rcb_tree *t, const int64_t *offsets, const int32_t *idx, double *rho);  // density.cu
 // neighbours.cu
 int neighbour_counts(rcb_tree *t, int64_t *counts, int *status);  // count pass into caller memory
 int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *needed);

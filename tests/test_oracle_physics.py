@@ -259,3 +259,47 @@ def test_plummer_analytic_acceleration_and_potential():
         assert abs(ratio.mean() - 1) < 4 * ratio.std() / math.sqrt(n) + 2e-3
         pr = pot[sel] / phi_sh[sel]
         assert abs(pr.mean() - 1) < 4 * pr.std() / math.sqrt(n) + 2e-3
+
+
+# ------------------------------------------------------------------------- SPH density (next-4)
+def test_kernel_W_is_the_normalised_cubic_spline():
+    from scipy.integrate import quad
+    for h in (0.3, 1.0, 2.5):
+        for q in (0.0, 0.2, 0.99, 1.0, 1.5, 1.999, 2.0, 3.0):
+            assert oracle.kernel_W(q * h, h) == pytest.approx(_cubic_spline_W(q * h, h), rel=1e-14, abs=0.0)
+        mass, _ = quad(lambda r: 4 * math.pi * r * r * oracle.kernel_W(r, h), 0.0, 2 * h, points=[h],
+                       epsabs=1e-14, epsrel=1e-13)
+        assert mass == pytest.approx(1.0, rel=1e-12)
+
+
+def test_density_over_neighbour_rows_equals_brute_force():
+    # rho_a = m_a W(0, h_a) + sum over b != a with r_ab < 2 h_a of m_b W(r_ab, h_a): the oracle's
+    # sum over its neighbour CSR against an all-pairs numpy sum
+    N = 2000
+    x, m, h = synth.make_particles("plummer", N, 91, "loguniform10")
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(0.6)
+    off, idx = ref.neighbours()
+    rho = oracle.density(x, m, h, off, idx)
+    d = np.sqrt(((x[:, None, :] - x[None, :, :]) ** 2).sum(-1))
+    q = d / h[:, None]
+    w = np.where(q < 1, 1 - 1.5 * q ** 2 + 0.75 * q ** 3, np.where(q < 2, 0.25 * (2 - q) ** 3, 0.0))
+    w /= np.pi * h[:, None] ** 3
+    brute = (w * m[None, :]).sum(1)      # includes b = a, the self term m_a W(0, h_a)
+    assert np.allclose(rho, brute, rtol=1e-12, atol=0)
+
+
+def test_density_of_a_uniform_sphere_is_its_mean_density():
+    # interior particles of a uniform (uncorrelated) unit sphere of total mass M: the neighbours'
+    # part of the sum has expectation (M / (4/3 pi)) times the kernel's integral, 1; the self
+    # term m_a W(0, h_a) comes on top (about a fifth of the mean with ~50 neighbours)
+    N = 20000
+    x, m, h = synth.make_particles("sphere", N, 92, "equal")
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(0.7)
+    off, idx = ref.neighbours()
+    rho = oracle.density(x, m, h, off, idx)
+    inner = np.linalg.norm(x, axis=1) < 0.6
+    self_term = np.array([m[a] * oracle.kernel_W(0.0, h[a]) for a in range(N)])
+    mean = m.sum() / (4.0 / 3.0 * np.pi)
+    assert abs(np.mean((rho - self_term)[inner]) / mean - 1.0) < 0.02
