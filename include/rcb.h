@@ -39,6 +39,9 @@ extern "C" {
 #define RCB_ERR_STATE (-6)    /* the call needs state the tree does not have */
 
 #define RCB_FLAG_TIMING 1u /* record CUDA events around every stage (see rcb_stage_times) */
+#define RCB_FLAG_CENTRE_OF_NUMBER 2u /* Sec. 2.1.3 variant: cut every cell through its centre of
+                                        number (unit weights) instead of its centre of mass; the
+                                        node moments stay mass-weighted */
 
 #define RCB_FP64 0  /* gravity in FP64 throughout */
 #define RCB_MIXED 1 /* FP32 near field on cell-relative offsets with compensated sums; FP32

@@ -90,7 +90,7 @@ void for_each_array(rcb_tree *t, F f) {
                   (void **)&t->near_nn, (void **)&t->far_n, (void **)&t->near_list, (void **)&t->far_list,
                   (void **)&t->coef, (void **)&t->coef32, (void **)&t->nb_count, (void **)&t->nb_long, (void **)&t->nb_rows, (void **)&t->scan_tmp, (void **)&t->tnear_off,
                   (void **)&t->tnear_sink, (void **)&t->tfar_off, (void **)&t->tfar_sink, (void **)&t->adj,
-                  (void **)&t->dens_hl};
+                  (void **)&t->dens_hl, (void **)&t->ones};
     for (void **q : p) f(q);
 }
 
@@ -206,6 +206,16 @@ int ensure_lists(rcb_tree *t) {
 }
 
 }  // namespace
+__global__ void k_fill_ones(double *v, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = 1.0;
+}
+
+// unit weights for the centre-of-number split
+int fill_ones(double *v, int64_t n, cudaStream_t st) {
+    k_fill_ones<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(v, n); note_launch();
+    return cudaGetLastError() == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
+}
+
 }  // namespace rcb
 
 using namespace rcb;
@@ -231,7 +241,7 @@ int rcb_build(const double *x, const double *m, const double *h, int64_t N, cons
     if (N < 1 || N >= ((int64_t)1 << 31)) return RCB_ERR_ARG;
     if (params->n_ll < 1 || !(params->theta >= 0.0) || !std::isfinite(params->theta)) return RCB_ERR_ARG;
     if (params->precision != RCB_FP64 && params->precision != RCB_MIXED) return RCB_ERR_ARG;
-    if ((params->flags & ~RCB_FLAG_TIMING) != 0) return RCB_ERR_ARG;
+    if ((params->flags & ~(RCB_FLAG_TIMING | RCB_FLAG_CENTRE_OF_NUMBER)) != 0) return RCB_ERR_ARG;
     if ((alloc == nullptr) != (release == nullptr)) return RCB_ERR_ARG;
     const int L = depth_rule(N, params->n_ll);
     if (L > kMaxL) return RCB_ERR_ARG;
@@ -264,7 +274,21 @@ int rcb_build(const double *x, const double *m, const double *h, int64_t N, cons
     int rc = RCB_OK;
     if (t->cap_N == 0) rc = allocate_arrays(t, N, L);
     stage_begin(t, SG_BUILD);
-    if (rc == RCB_OK) rc = build_tree(t, x, m, h);
+    if (rc == RCB_OK) {
+        if (params->flags & RCB_FLAG_CENTRE_OF_NUMBER) {
+            // every cell cut through its centre of number: the partition of unit weights, then the
+            // nodes' mass-weighted moments by a refit (which keeps the splits)
+            if (!t->ones) {
+                t->ones = (double *)dev_alloc(t, (size_t)t->cap_N * sizeof(double));
+                if (!t->ones) rc = RCB_ERR_ALLOC;
+                else rc = fill_ones(t->ones, t->cap_N, t->stream);
+            }
+            if (rc == RCB_OK) rc = build_tree(t, x, t->ones, h);
+            if (rc == RCB_OK) rc = refit_tree(t, x, m);
+        } else {
+            rc = build_tree(t, x, m, h);
+        }
+    }
     if (rc == RCB_OK) rc = ensure_lists(t);
     if (rc == RCB_OK) {
         stage_begin(t, SG_WALK);

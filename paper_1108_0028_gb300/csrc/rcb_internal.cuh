@@ -274,6 +274,7 @@ struct rcb_tree {
     // backward
     int32_t *tnear_off, *tnear_sink, *tfar_off, *tfar_sink;
     int bwd_valid;
+    double *ones;     // unit weights for the centre-of-number split (cap_N)
     float4 *dens_hl;  // density scratch: per particle (hi, m) and (lo, 1/h) in float32, original order
     int walk_pair;  // walk two sinks per thread (set when the last walk's longest far list exceeded 1024)
     double *adj;  // per-node adjoints

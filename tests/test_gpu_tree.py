@@ -135,3 +135,63 @@ def test_paired_walk_writes_the_same_lists():
     ref = oracle.OracleTree(x, m, h)
     ref.walk(0.5)
     assert np.array_equal(tree.export_topology()["leaf_of"], ref.leaf_of())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_centre_of_number_split(precision):
+    # Sec. 2.1.3 variant: every cell cut through its centre of number.  The oracle's counterpart
+    # is the tree of unit weights, refitted with the real masses (the refit keeps the splits).
+    import paper_1108_0028_gb300 as rcb
+    N = 6000
+    x, m, h = synth.make_particles("plummer", N, synth.seed_for(6, 2), "loguniform10")
+    ref = oracle.OracleTree(x, np.ones(N), h)
+    ref.refit(x, m)
+    ref.walk(0.6)
+    tree = rcb.RCBTree(*_gpu(x, m, h), theta=0.6, precision=precision, split="number")
+    g, o = tree.export_topology(), ref.nodes()
+    assert np.array_equal(g["leaf_of"], ref.leaf_of())
+    inner = o["count"][: 1 << ref.L] > 0
+    inner[0] = False
+    assert np.array_equal(g["split"][: 1 << ref.L][inner].view(np.int64), o["split"][: 1 << ref.L][inner].view(np.int64))
+    live = o["count"] > 0
+    live[0] = False
+    for k in ("com", "bmin", "bmax", "rg", "hint", "mass"):
+        assert np.array_equal(g[k][live].view(np.int64), o[k][live].view(np.int64)), k
+    gl, ol = tree.export_lists(), ref.lists()
+    for j in range(ref.nleaves):
+        a, b = gl["far_off"][j], gl["far_off"][j + 1]
+        c, d = ol["far_off"][j], ol["far_off"][j + 1]
+        assert sorted(gl["far_ids"][a:b].tolist()) == sorted(ol["far_ids"][c:d].tolist()), j
+        a, b = gl["near_off"][j], gl["near_off"][j + 1]
+        c, d = ol["near_off"][j], ol["near_off"][j + 1]
+        assert sorted(gl["near_ids"][a:b].tolist()) == sorted(ol["near_ids"][c:d].tolist()), j
+    ro, ri = ref.neighbours()
+    go, gi = tree.neighbours()
+    assert np.array_equal(go.cpu().numpy(), ro) and np.array_equal(gi.cpu().numpy(), ri)
+    oa, _ = ref.gravity()
+    ga, _ = tree.gravity()
+    e = np.linalg.norm(ga.cpu().numpy() - oa, axis=1) / np.linalg.norm(oa, axis=1)
+    assert np.sqrt(np.mean(e * e)) < (1e-10 if precision == "fp64" else 2e-6)
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.7])
+def test_split_variants_force_accuracy_on_plummer(theta):
+    # The paper prefers the centre-of-mass split because it bounds the truncation error of
+    # "renegade" particles (Sec. 2.1.3).  Both variants against the direct sum on a Plummer
+    # sphere with a 10x mass range; the printed errors are the measurement.
+    import paper_1108_0028_gb300 as rcb
+    N = 65536
+    x, m, h = synth.make_particles("plummer", N, synth.seed_for(6, 3), "loguniform10")
+    targets = np.random.default_rng(5).choice(N, 2000, replace=False)
+    da, _ = oracle.direct(x, m, h, targets)
+    out = {}
+    for split in ("mass", "number"):
+        tree = rcb.RCBTree(*_gpu(x, m, h), theta=theta, precision="fp64", split=split)
+        ga, _ = tree.gravity()
+        e = np.linalg.norm(ga.cpu().numpy()[targets] - da, axis=1) / np.linalg.norm(da, axis=1)
+        out[split] = (float(np.sqrt(np.mean(e * e))), float(np.quantile(e, 0.999)), float(e.max()),
+                      tree.info()["far_total"], tree.info()["near_pairs"])
+    print(f"theta {theta}: " + "; ".join(f"{k}: rms {v[0]:.3e} p99.9 {v[1]:.3e} max {v[2]:.3e} far {v[3]} "
+                                         f"near pairs {v[4]}" for k, v in out.items()))
+    for v in out.values():
+        assert v[0] < 1e-2

@@ -268,3 +268,20 @@ def test_update_inside_equals_refit_with_new_h():
     na, nb = a.nodes(), b.nodes()
     for k in ("split", "axis", "com", "bmin", "bmax", "rg", "hint", "hnode", "Q", "mass"):
         assert np.array_equal(na[k], nb[k]), k
+
+
+def test_unit_weight_splits_are_centres_of_number():
+    # the centre-of-number variant (Sec. 2.1.3): with unit weights every split is the cell's mean
+    # coordinate along the cut axis (exact rational mean, within one ulp of the fixed-point grid)
+    N = 2000
+    x, _, h = synth.make_particles("plummer", N, 77, "equal")
+    ref = oracle.OracleTree(x, np.ones(N), h)
+    nd, perm = ref.nodes(), ref.perm()
+    for c in range(1, 1 << ref.L):
+        f, n = nd["first"][c], nd["count"][c]
+        if n == 0:
+            continue
+        ax = nd["axis"][c]
+        vals = x[perm[f:f + n], ax]
+        exact = float(sum(Fraction(v) for v in vals) / n)
+        assert abs(nd["split"][c] - exact) <= 2 * np.spacing(abs(exact)), c
