@@ -201,6 +201,8 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
     import numpy as np
     import torch
 
+    import paper_1108_0028_gb300 as rcb
+
     # FP64 form on the same tree (gravity only differs), and the mixed form's error against it
     acc_m, pot_m = tree.gravity()
     tree.set_precision("fp64")
@@ -315,6 +317,29 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
         dens.append(e0.elapsed_time(e1))
     density_ms = statistics.mean(dens)
     del off_d, idx_d
+    # MAC-only near lists (the Sec. 2.5 variant): gravity alone on such a tree, its near pairs and
+    # its force difference from the conservative lists of the headline tree
+    tree.rebuild(xt, mt, ht)
+    acc_std, _ = tree.gravity()
+    acc_std = acc_std.clone()
+    near_pairs_std = tree.info()["near_pairs"]
+    mac_tree = rcb.RCBTree(xt, mt, ht, n_ll=N_LL, theta=a.theta, precision="mixed", timing=True,
+                           mac_only=True)
+    mac_ms = []
+    for _ in range(5):
+        flush.zero_()
+        torch.cuda.synchronize()
+        acc_mac, _ = mac_tree.gravity()
+        st = mac_tree.stage_times()
+        mac_ms.append(st["far"] + st["near"])
+    dmac = torch.linalg.norm(acc_mac - acc_std, dim=1) / torch.linalg.norm(acc_std, dim=1)
+    mac_info = mac_tree.info()
+    mac_only = {"ms": statistics.mean(mac_ms), "mparticles_s": job_throughput(world, a.n, statistics.mean(mac_ms)),
+                "near_pairs": mac_info["near_pairs"], "near_pairs_conservative": near_pairs_std,
+                "rms_rel_diff_vs_conservative": float(torch.sqrt(torch.mean(dmac * dmac))),
+                "path": "rcb_gravity on a tree built with RCB_FLAG_MAC_ONLY (near lists from the MAC alone)"}
+    mac_tree.free()
+    del acc_mac, acc_std, dmac
     L = tree.info()["L"]
     build_bytes = a.n * (72 * L + 56)  # every level reads and writes 36 B per particle, h gathered once
     per_stage = {
@@ -331,6 +356,7 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
         "gravity": {"ms": grav_ms, "mparticles_s": job_throughput(world, a.n, grav_ms), "path": "rcb_gravity alone"},
         "neighbours_gravity_fused": {"ms": fused_ms, "mparticles_s": job_throughput(world, a.n, fused_ms),
                                      "path": "rcb_gravity_neighbours + compaction (the step's path)"},
+        "gravity_mac_only": mac_only,
         "density": {"ms": density_ms, "mparticles_s": job_throughput(world, a.n, density_ms),
                     "path": "rcb_density over the CSR of rcb_neighbours (cubic spline, support 2h)"},
         "update": {"ms": update_ms, "mparticles_s": job_throughput(world, a.n, update_ms),

@@ -42,6 +42,11 @@ extern "C" {
 #define RCB_FLAG_CENTRE_OF_NUMBER 2u /* Sec. 2.1.3 variant: cut every cell through its centre of
                                         number (unit weights) instead of its centre of mass; the
                                         node moments stay mass-weighted */
+#define RCB_FLAG_MAC_ONLY 4u /* Sec. 2.5 variant: near lists from the MAC alone (no reachability
+                                override), so gravity sees shorter near lists; neighbour
+                                candidates come from a reachability walk of their own, and
+                                rcb_gravity_neighbours runs gravity and the neighbour count as
+                                two passes */
 
 #define RCB_FP64 0  /* gravity in FP64 throughout */
 #define RCB_MIXED 1 /* FP32 near field on cell-relative offsets with compensated sums; FP32

@@ -76,6 +76,7 @@ def lib():
                 "orc_direct_grad": (None, [_P, _P, _P, _I64, _P, _P, _P, _P]),
                 "orc_refit": (ctypes.c_int, [_P, _P, _P]),
                 "orc_update": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+                "orc_walk_mac_only": (ctypes.c_int, [_P, ctypes.c_double]),
                 "orc_kernel_W": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
                 "orc_density_csr": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
                 "orc_gravity_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -276,7 +277,17 @@ class OracleTree:
             out[perm[f:f + c]] = j
         return out
 
-    def walk(self, theta: float, sinks=None) -> None:
+    def walk(self, theta: float, sinks=None, mac_only: bool = False) -> None:
+        """mac_only: near lists from the MAC alone (Sec. 2.5 variant); every sink is walked and the
+        lists hold no neighbour candidates."""
+        if mac_only:
+            if sinks is not None:
+                raise ValueError("the MAC-only walk covers every sink")
+            r = lib().orc_walk_mac_only(self._t, float(theta))
+            if r != OK:
+                raise RuntimeError(f"oracle walk failed: {r}")
+            self.walked = True
+            return
         s = None if sinks is None else np.ascontiguousarray(sinks, dtype=np.int32)
         r = lib().orc_walk(self._t, float(theta), _ptr(s), -1 if s is None else s.shape[0])
         if r != OK:

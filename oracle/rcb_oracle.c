@@ -453,7 +453,9 @@ static int vpush(vec_t *v, int32_t id, uint8_t flag) {
     return ORC_OK;
 }
 
-static int walk_sink(const orc_tree *t, int64_t A, double theta2, vec_t *near, vec_t *far) {
+/* mac_only: the variant of Sec. 2.5 without the reachability override (near lists from the MAC
+ * alone); its near lists carry no neighbour candidates. */
+static int walk_sink(const orc_tree *t, int64_t A, double theta2, int mac_only, vec_t *near, vec_t *far) {
     int64_t leaf0 = (int64_t)1 << t->L;
     int64_t n = 2;
     while (n != 1) {
@@ -462,7 +464,7 @@ static int walk_sink(const orc_tree *t, int64_t A, double theta2, vec_t *near, v
             int is_leaf = n >= leaf0;
             double d2 = dist2(t->rg[0][A], t->rg[1][A], t->rg[2][A], t->rg[0][n], t->rg[1][n], t->rg[2][n]);
             double rr = t->hnode[A] + t->hint[n];
-            if (d2 < rr * rr) {
+            if (!mac_only && d2 < rr * rr) {
                 /* Sec. 2.3.1 reachable: never accepted by the MAC (Sec. 2.4.1). */
                 if (is_leaf) { if (vpush(near, (int32_t)n, 1)) return ORC_ERR_ALLOC; }
                 else descend = 1;
@@ -482,7 +484,18 @@ static int walk_sink(const orc_tree *t, int64_t A, double theta2, vec_t *near, v
     return ORC_OK;
 }
 
+static int walk_mode(orc_tree *t, double theta, const int32_t *sinks, int64_t nsinks, int mac_only);
+
 int orc_walk(orc_tree *t, double theta, const int32_t *sinks, int64_t nsinks) {
+    return walk_mode(t, theta, sinks, nsinks, 0);
+}
+
+/* The MAC-only walk (Sec. 2.5): every sink, near lists without the reachability override. */
+int orc_walk_mac_only(orc_tree *t, double theta) {
+    return walk_mode(t, theta, NULL, -1, 1);
+}
+
+static int walk_mode(orc_tree *t, double theta, const int32_t *sinks, int64_t nsinks, int mac_only) {
     if (!(theta >= 0.0) || !isfinite(theta)) return ORC_ERR_ARG;
     free_lists(t);
     int64_t nl = (int64_t)1 << t->L, leaf0 = nl;
@@ -508,7 +521,7 @@ int orc_walk(orc_tree *t, double theta, const int32_t *sinks, int64_t nsinks) {
     for (int64_t j = 0; j < nl; ++j) {
         if (!t->walked_leaf[j]) continue;
         vec_t near = {0}, far = {0};
-        int e = walk_sink(t, leaf0 + j, theta2, &near, &far);
+        int e = walk_sink(t, leaf0 + j, theta2, mac_only, &near, &far);
         if (e) {
 #pragma omp atomic write
             err = e;

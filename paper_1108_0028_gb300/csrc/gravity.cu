@@ -939,8 +939,8 @@ int gravity_impl(rcb_tree *t, double *acc, double *pot, bool nb) {
 int gravity(rcb_tree *t, double *acc, double *pot) { return gravity_impl(t, acc, pot, false); }
 
 int gravity_neighbours(rcb_tree *t, double *acc, double *pot) {
-    if (t->params.precision != RCB_MIXED) {
-        // FP64 form: the two passes run separately
+    if (t->params.precision != RCB_MIXED || (t->params.flags & RCB_FLAG_MAC_ONLY)) {
+        // FP64 form, or MAC-only near lists that do not hold every candidate: two passes
         const int rc = gravity_impl(t, acc, pot, false);
         if (rc) return rc;
         return count_neighbours(t);

@@ -427,9 +427,12 @@ NbCtx make_nbctx(rcb_tree *t) {
     NbCtx c;
     c.nsinks = t->nsinks;
     c.sinks = t->sinks;
-    c.near_list = t->near_list;
-    c.near_nr = t->near_nr;
-    c.cap_near = t->cap_near;
+    // candidates: the reachable leaves at the front of the near rows, or the candidate rows of a
+    // MAC-only tree
+    const bool mac_only = (t->params.flags & RCB_FLAG_MAC_ONLY) != 0;
+    c.near_list = mac_only ? t->cand_list : t->near_list;
+    c.near_nr = mac_only ? t->cand_n : t->near_nr;
+    c.cap_near = mac_only ? t->cap_cand : t->cap_near;
     c.nfirst = t->nfirst;
     c.ncount = t->ncount;
     c.ncom = t->ncom;

@@ -90,7 +90,8 @@ void for_each_array(rcb_tree *t, F f) {
                   (void **)&t->near_nn, (void **)&t->far_n, (void **)&t->near_list, (void **)&t->far_list,
                   (void **)&t->coef, (void **)&t->coef32, (void **)&t->nb_count, (void **)&t->nb_long, (void **)&t->nb_rows, (void **)&t->scan_tmp, (void **)&t->tnear_off,
                   (void **)&t->tnear_sink, (void **)&t->tfar_off, (void **)&t->tfar_sink, (void **)&t->adj,
-                  (void **)&t->dens_hl, (void **)&t->ones};
+                  (void **)&t->dens_hl, (void **)&t->ones, (void **)&t->cand_list, (void **)&t->cand_far,
+                  (void **)&t->cand_n};
     for (void **q : p) f(q);
 }
 
@@ -241,7 +242,7 @@ int rcb_build(const double *x, const double *m, const double *h, int64_t N, cons
     if (N < 1 || N >= ((int64_t)1 << 31)) return RCB_ERR_ARG;
     if (params->n_ll < 1 || !(params->theta >= 0.0) || !std::isfinite(params->theta)) return RCB_ERR_ARG;
     if (params->precision != RCB_FP64 && params->precision != RCB_MIXED) return RCB_ERR_ARG;
-    if ((params->flags & ~(RCB_FLAG_TIMING | RCB_FLAG_CENTRE_OF_NUMBER)) != 0) return RCB_ERR_ARG;
+    if ((params->flags & ~(RCB_FLAG_TIMING | RCB_FLAG_CENTRE_OF_NUMBER | RCB_FLAG_MAC_ONLY)) != 0) return RCB_ERR_ARG;
     if ((alloc == nullptr) != (release == nullptr)) return RCB_ERR_ARG;
     const int L = depth_rule(N, params->n_ll);
     if (L > kMaxL) return RCB_ERR_ARG;

@@ -275,6 +275,10 @@ struct rcb_tree {
     int32_t *tnear_off, *tnear_sink, *tfar_off, *tfar_sink;
     int bwd_valid;
     double *ones;     // unit weights for the centre-of-number split (cap_N)
+    // neighbour candidates of a MAC-only tree: reachable leaves per sink (front of the rows)
+    int32_t *cand_list, *cand_far, *cand_n;  // cand_n: [3][nleaves] counts (front, back, far)
+    int cap_cand;
+    int64_t cap_lists_cand;
     float4 *dens_hl;  // density scratch: per particle (hi, m) and (lo, 1/h) in float32, original order
     int walk_pair;  // walk two sinks per thread (set when the last walk's longest far list exceeded 1024)
     double *adj;  // per-node adjoints

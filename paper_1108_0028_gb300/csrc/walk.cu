@@ -42,6 +42,11 @@ struct WalkCtx {
 
 __device__ inline float sq(float v) { return v * v; }
 
+// MODE 0: the walk above.  MODE 1: MAC-only near lists (the variant of Sec. 2.5 without the
+// reachability override): MAC -> far, otherwise leaf -> near (from the back), internal -> open.
+// MODE 2: neighbour candidates only: reachable leaves -> near (from the front), reachable
+// internal nodes opened, the rest skipped; no far list.
+template <int MODE>
 __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -80,7 +85,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
                 const float F = sq(rgAabs.x + fabsf(na.x)) + sq(rgAabs.y + fabsf(na.y)) + sq(rgAabs.z + fabsf(na.z)) + rr * rr;
                 const float B = F * 0x1p-20f + 1e-30f;
                 bool reach;
-                if (f < -B) reach = true;
+                if (MODE == 1) reach = false;
+                else if (f < -B) reach = true;
                 else if (f > B) reach = false;
                 else {
                     ++nfallback;
@@ -96,7 +102,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
                     } else {
                         open = true;
                     }
-                } else {
+                } else if (MODE != 2) {
                     const float ex = comA.x - nb.x, ey = comA.y - nb.y, ez = comA.z - nb.z;
                     const float R2 = ex * ex + ey * ey + ez * ez;
                     const float fm = nb.w * nb.w - c.theta2f * R2;
@@ -349,7 +355,10 @@ int count_pairs(rcb_tree *t) {
     return RCB_OK;
 }
 
-int walk_tree(rcb_tree *t) {
+// The walk into one set of per-sink lists, growing their capacities until every sink fits.
+static int walk_into(rcb_tree *t, int mode, int32_t *&near_list, int32_t *&far_list, int32_t *near_nr,
+                     int32_t *near_nn, int32_t *far_n, int &cap_near, int &cap_far, int64_t &cap_lists_near,
+                     int64_t &cap_lists_far) {
     cudaStream_t st = t->stream;
     WalkCtx c;
     c.L = t->L;
@@ -366,46 +375,81 @@ int walk_tree(rcb_tree *t) {
     c.nsinks = t->nsinks;
     c.status = t->d_status;
     for (int attempt = 0; attempt < 3; ++attempt) {
-        c.cap_near = t->cap_near;
-        c.cap_far = t->cap_far;
-        c.near_list = t->near_list;
-        c.far_list = t->far_list;
-        c.near_nr = t->near_nr;
-        c.near_nn = t->near_nn;
-        c.far_n = t->far_n;
+        c.cap_near = cap_near;
+        c.cap_far = cap_far;
+        c.near_list = near_list;
+        c.far_list = far_list;
+        c.near_nr = near_nr;
+        c.near_nn = near_nn;
+        c.far_n = far_n;
         RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_MAXNEAR, 0, 3 * sizeof(int), st));
-        // Long walks (concentrated inputs) share node loads between sibling sinks; short ones keep
-        // one sink per thread for more parallelism.  Both write the same lists.
-        if (t->walk_pair) {
+        const int blocks = (t->nsinks + kWalkWarps * 32 - 1) / (kWalkWarps * 32);
+        if (mode == 0 && t->walk_pair) {
+            // Long walks (concentrated inputs) share node loads between sibling sinks; short ones
+            // keep one sink per thread for more parallelism.  Both write the same lists.
             const int nthreads = (t->nsinks + 1) / 2;
-            const int blocks = (nthreads + kWalkWarps * 32 - 1) / (kWalkWarps * 32);
-            if (blocks > 0) k_walk_pair<<<blocks, kWalkWarps * 32, 0, st>>>(c); note_launch();
-        } else {
-            const int blocks = (t->nsinks + kWalkWarps * 32 - 1) / (kWalkWarps * 32);
-            if (blocks > 0) k_walk<<<blocks, kWalkWarps * 32, 0, st>>>(c); note_launch();
+            const int bp = (nthreads + kWalkWarps * 32 - 1) / (kWalkWarps * 32);
+            if (bp > 0) k_walk_pair<<<bp, kWalkWarps * 32, 0, st>>>(c); note_launch();
+        } else if (blocks > 0) {
+            if (mode == 0) k_walk<0><<<blocks, kWalkWarps * 32, 0, st>>>(c);
+            else if (mode == 1) k_walk<1><<<blocks, kWalkWarps * 32, 0, st>>>(c);
+            else k_walk<2><<<blocks, kWalkWarps * 32, 0, st>>>(c);
+            note_launch();
         }
         RCB_CUDA_TRY(cudaGetLastError());
         RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status, t->d_status, ST_NWORDS * sizeof(int), cudaMemcpyDeviceToHost, st));
         RCB_CUDA_TRY(cudaStreamSynchronize(st));
         if (t->h_status[ST_ERR] & ERRBIT_LIMIT) return RCB_ERR_LIMIT;
         int need_near = t->h_status[ST_MAXNEAR], need_far = t->h_status[ST_MAXFAR];
-        t->stats_fallback = t->h_status[ST_FALLBACK];
-        t->walk_pair = need_far > 1024;
-        if (need_near <= t->cap_near && need_far <= t->cap_far) return RCB_OK;
+        if (mode != 2) t->stats_fallback = t->h_status[ST_FALLBACK];
+        if (mode == 0) t->walk_pair = need_far > 1024;
+        if (need_near <= cap_near && need_far <= cap_far) return RCB_OK;
         // grow the per-sink list capacities and walk again
-        int cn = std::max(t->cap_near, ((need_near + 31) / 32) * 32 + 32);
-        int cf = std::max(t->cap_far, ((need_far + 31) / 32) * 32 + 32);
-        dev_free(t, t->near_list);
-        dev_free(t, t->far_list);
-        t->near_list = (int32_t *)dev_alloc(t, (size_t)t->nsinks * cn * sizeof(int32_t) + 16);
-        t->far_list = (int32_t *)dev_alloc(t, (size_t)t->nsinks * cf * sizeof(int32_t) + 16);
-        if (!t->near_list || !t->far_list) return RCB_ERR_ALLOC;
-        t->cap_near = cn;
-        t->cap_far = cf;
-        t->cap_lists_near = (int64_t)t->nsinks * cn;
-        t->cap_lists_far = (int64_t)t->nsinks * cf;
+        int cn = std::max(cap_near, ((need_near + 31) / 32) * 32 + 32);
+        int cf = std::max(cap_far, ((need_far + 31) / 32) * 32 + 32);
+        dev_free(t, near_list);
+        dev_free(t, far_list);
+        near_list = (int32_t *)dev_alloc(t, (size_t)t->nsinks * cn * sizeof(int32_t) + 16);
+        far_list = (int32_t *)dev_alloc(t, (size_t)t->nsinks * cf * sizeof(int32_t) + 16);
+        if (!near_list || !far_list) return RCB_ERR_ALLOC;
+        cap_near = cn;
+        cap_far = cf;
+        cap_lists_near = (int64_t)t->nsinks * cn;
+        cap_lists_far = (int64_t)t->nsinks * cf;
     }
     return RCB_ERR_LIMIT;
+}
+
+// The walks of a build or update: the lists gravity uses (standard, or MAC-only with
+// RCB_FLAG_MAC_ONLY) and, for MAC-only lists, the neighbour candidates from a walk of their own.
+int walk_tree(rcb_tree *t) {
+    if (!(t->params.flags & RCB_FLAG_MAC_ONLY))
+        return walk_into(t, 0, t->near_list, t->far_list, t->near_nr, t->near_nn, t->far_n, t->cap_near, t->cap_far,
+                         t->cap_lists_near, t->cap_lists_far);
+    int rc = walk_into(t, 1, t->near_list, t->far_list, t->near_nr, t->near_nn, t->far_n, t->cap_near, t->cap_far,
+                       t->cap_lists_near, t->cap_lists_far);
+    if (rc) return rc;
+    if (!t->cand_n) {
+        t->cand_n = (int32_t *)dev_alloc(t, 3 * (size_t)std::max<int64_t>(t->nleaves, 1) * sizeof(int32_t));
+        if (!t->cand_n) return RCB_ERR_ALLOC;
+        t->cap_cand = 0;
+    }
+    if (!t->cand_list) {
+        t->cap_cand = 64;
+        t->cap_lists_cand = (int64_t)t->nsinks * t->cap_cand;
+        t->cand_list = (int32_t *)dev_alloc(t, (size_t)t->cap_lists_cand * sizeof(int32_t) + 16);
+        t->cand_far = (int32_t *)dev_alloc(t, 16);
+        if (!t->cand_list || !t->cand_far) return RCB_ERR_ALLOC;
+    } else if ((int64_t)t->nsinks * t->cap_cand > t->cap_lists_cand) {
+        dev_free(t, t->cand_list);
+        t->cap_lists_cand = (int64_t)t->nsinks * t->cap_cand;
+        t->cand_list = (int32_t *)dev_alloc(t, (size_t)t->cap_lists_cand * sizeof(int32_t) + 16);
+        if (!t->cand_list) return RCB_ERR_ALLOC;
+    }
+    int cap_far0 = 0;
+    int64_t far_lists0 = 0;
+    return walk_into(t, 2, t->cand_list, t->cand_far, t->cand_n, t->cand_n + t->nleaves, t->cand_n + 2 * t->nleaves,
+                     t->cap_cand, cap_far0, t->cap_lists_cand, far_lists0);
 }
 
 }  // namespace rcb

@@ -195,3 +195,40 @@ def test_split_variants_force_accuracy_on_plummer(theta):
                                          f"near pairs {v[4]}" for k, v in out.items()))
     for v in out.values():
         assert v[0] < 1e-2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_mac_only_near_lists(precision):
+    # Sec. 2.5 variant: the MAC alone builds the near lists (no reachability override).  Gravity
+    # lists and forces equal the oracle's MAC-only walk; the neighbour lists are unchanged (their
+    # candidates come from a reachability walk of their own).
+    import paper_1108_0028_gb300 as rcb
+    N = 6000
+    x, m, h = synth.make_particles("plummer", N, synth.seed_for(6, 4), "loguniform10")
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(0.6, mac_only=True)
+    tree = rcb.RCBTree(*_gpu(x, m, h), theta=0.6, precision=precision, mac_only=True)
+    gl, ol = tree.export_lists(), ref.lists()
+    for j in range(ref.nleaves):
+        a, b = gl["near_off"][j], gl["near_off"][j + 1]
+        c, d = ol["near_off"][j], ol["near_off"][j + 1]
+        assert sorted(zip(gl["near_ids"][a:b].tolist(), gl["near_reach"][a:b].tolist())) == \
+            sorted(zip(ol["near_ids"][c:d].tolist(), ol["near_reach"][c:d].tolist())), j
+        a, b = gl["far_off"][j], gl["far_off"][j + 1]
+        c, d = ol["far_off"][j], ol["far_off"][j + 1]
+        assert sorted(gl["far_ids"][a:b].tolist()) == sorted(ol["far_ids"][c:d].tolist()), j
+    ro, ri = oracle.brute_neighbours(x, h)
+    go, gi = tree.neighbours()
+    assert np.array_equal(go.cpu().numpy(), ro) and np.array_equal(gi.cpu().numpy(), ri)
+    oa, op = ref.gravity()
+    ga, gp, fo, fi = tree.gravity_neighbours()
+    assert np.array_equal(fo.cpu().numpy(), ro) and np.array_equal(fi.cpu().numpy(), ri)
+    e = np.linalg.norm(ga.cpu().numpy() - oa, axis=1) / np.linalg.norm(oa, axis=1)
+    assert np.sqrt(np.mean(e * e)) < (1e-10 if precision == "fp64" else 2e-6)
+    # shorter near lists than the conservative walk
+    std = rcb.RCBTree(*_gpu(x, m, h), theta=0.6, precision=precision)
+    assert tree.info()["near_total"] < std.info()["near_total"]
+    # an update keeps the variant (both walks again)
+    assert not tree.update(*_gpu(x, m, h))
+    go2, gi2 = tree.neighbours()
+    assert np.array_equal(go2.cpu().numpy(), ro) and np.array_equal(gi2.cpu().numpy(), ri)
