@@ -678,6 +678,7 @@ __device__ inline void pair_grad32(float dx, float dy, float dz, float hsum, flo
 
 constexpr int kMTile = 384;   // staged particles per warp (mixed)
 constexpr int kMGroup = 8;    // own particles per pass (mixed)
+constexpr int kMSuper = 3;    // groups of own particles sharing one staged tile
 
 // Per-warp staging.  SIDE 0 (sources b): a = (x, y, z, m_b), hb = h_b.  SIDE 1 (sink particles a):
 // a = (x, y, z, h_a), v = (dL/da_a, dL/dPhi_a).  Positions relative to the own cell's centre of mass.
@@ -686,7 +687,9 @@ struct BNearSmem {
     float4 v[kMTile];
     float hb[kMTile];
     int32_t id[kMTile];
-    static constexpr size_t bytes = (size_t)kMTile * (2 * sizeof(float4) + sizeof(float) + sizeof(int32_t));
+    float2 gacc[kMSuper][32];  // the groups' compensated lane totals while another group runs
+    static constexpr size_t bytes =
+        (size_t)kMTile * (2 * sizeof(float4) + sizeof(float) + sizeof(int32_t)) + kMSuper * 32 * sizeof(float2);
 };
 
 // Stage slots [t0, t0 + kMTile) of the concatenated cells; one lane per slot.
@@ -744,9 +747,12 @@ __device__ int stage_cells_mixed(const BCtx &c, int ncells, CellAt cell_at, int6
 
 // SIDE 0: sink side, a in the sink, b over the near cells: gxs[a] += g.
 // SIDE 1: source side, b in a leaf, a over the sink particles listing it: gxs[b] -= g, gms[b] += gm.
-// Per tile the float32 sums fold into compensated (sum, error) pairs; lanes reduce at the end.
+// Up to kMSuper groups of own particles share each staged tile (the tile loop runs outside the
+// group loop).  Per tile and group the float32 sums are reduce-scattered across lanes with
+// compensation and folded into the group's (sum, error) pair per lane, which waits in shared
+// memory while another group runs.
 template <int SIDE>
-__global__ void __launch_bounds__(kBW * 32, 2) k_bwd_near_mixed(BCtx c) {
+__global__ void __launch_bounds__(kBW * 32, 3) k_bwd_near_mixed(BCtx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     BNearSmem &sm = *reinterpret_cast<BNearSmem *>(smem_raw + (size_t)w * BNearSmem::bytes);
@@ -778,94 +784,102 @@ __global__ void __launch_bounds__(kBW * 32, 2) k_bwd_near_mixed(BCtx c) {
         for (int k = lane; k < ncells; k += 32) S += c.ncount[cell_at(k)];
         for (int o = 16; o >= 1; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
         const int f = c.nfirst[own], n = c.ncount[own];
-        for (int p0 = 0; p0 < n; p0 += kMGroup) {
-            const int np = min(kMGroup, n - p0);
-            float ox[kMGroup], oy[kMGroup], oz[kMGroup], oh[kMGroup], om[kMGroup], ovx[kMGroup], ovy[kMGroup],
-                ovz[kMGroup], ow[kMGroup];
-            int oid[kMGroup];
-#pragma unroll
-            for (int i = 0; i < kMGroup; ++i) {
-                const int p = f + p0 + min(i, np - 1);
-                const float4 pp = c.p32[p];
-                ox[i] = pp.x;
-                oy[i] = pp.y;
-                oz[i] = pp.z;
-                om[i] = pp.w;
-                oh[i] = c.h32[p];
-                if (SIDE == 0) {
-                    const float4 gv = c.gv32[p];
-                    ovx[i] = gv.x;
-                    ovy[i] = gv.y;
-                    ovz[i] = gv.z;
-                    ow[i] = gv.w;
-                }
-                oid[i] = i < np ? p : -1;
-            }
-            float cs[NQ * kMGroup], ce[NQ * kMGroup];
-#pragma unroll
-            for (int i = 0; i < NQ * kMGroup; ++i) cs[i] = ce[i] = 0.f;
+        for (int P0 = 0; P0 < n; P0 += kMSuper * kMGroup) {
+            const int ng = min(kMSuper, (n - P0 + kMGroup - 1) / kMGroup);
+            for (int gi = 0; gi < ng; ++gi) sm.gacc[gi][lane] = make_float2(0.f, 0.f);
             for (int64_t t0 = 0; t0 < S; t0 += kMTile) {
                 const int ns = stage_cells_mixed<SIDE>(c, ncells, cell_at, t0, cO, sm);
-                float acc[NQ * kMGroup];
+                for (int gi = 0; gi < ng; ++gi) {
+                    const int p0 = P0 + gi * kMGroup;
+                    const int np = min(kMGroup, n - p0);
+                    float ox[kMGroup], oy[kMGroup], oz[kMGroup], oh[kMGroup], om[kMGroup], ovx[kMGroup], ovy[kMGroup],
+                        ovz[kMGroup], ow[kMGroup];
+                    int oid[kMGroup];
 #pragma unroll
-                for (int i = 0; i < NQ * kMGroup; ++i) acc[i] = 0.f;
-                for (int j = lane; j < ns; j += 32) {
-                    const float4 ja = sm.a[j];
-                    const int jid = sm.id[j];
-                    if (SIDE == 0) {
-                        const float jh = sm.hb[j];
-#pragma unroll
-                        for (int i = 0; i < kMGroup; ++i) {
-                            if (i > 0 && i >= np) break;  // padding of a short group (warp-uniform)
-                            float gx, gy, gz, gmv;
-                            pair_grad32(ox[i] - ja.x, oy[i] - ja.y, oz[i] - ja.z, oh[i] + jh, ja.w, ovx[i], ovy[i],
-                                        ovz[i], ow[i], gx, gy, gz, gmv);
-                            if (jid != oid[i]) {
-                                acc[3 * i] += gx;
-                                acc[3 * i + 1] += gy;
-                                acc[3 * i + 2] += gz;
-                            }
+                    for (int i = 0; i < kMGroup; ++i) {
+                        const int p = f + p0 + min(i, np - 1);
+                        const float4 pp = c.p32[p];
+                        ox[i] = pp.x;
+                        oy[i] = pp.y;
+                        oz[i] = pp.z;
+                        om[i] = pp.w;
+                        oh[i] = c.h32[p];
+                        if (SIDE == 0) {
+                            const float4 gv = c.gv32[p];
+                            ovx[i] = gv.x;
+                            ovy[i] = gv.y;
+                            ovz[i] = gv.z;
+                            ow[i] = gv.w;
                         }
-                    } else {
-                        const float4 jv = sm.v[j];
+                        oid[i] = i < np ? p : -1;
+                    }
+                    float acc[32];
 #pragma unroll
-                        for (int i = 0; i < kMGroup; ++i) {
-                            if (i > 0 && i >= np) break;  // padding of a short group (warp-uniform)
-                            float gx, gy, gz, gmv;
-                            pair_grad32(ja.x - ox[i], ja.y - oy[i], ja.z - oz[i], ja.w + oh[i], om[i], jv.x, jv.y, jv.z,
-                                        jv.w, gx, gy, gz, gmv);
-                            if (jid != oid[i]) {
-                                acc[4 * i] -= gx;
-                                acc[4 * i + 1] -= gy;
-                                acc[4 * i + 2] -= gz;
-                                acc[4 * i + 3] += gmv;
+                    for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+                    for (int j = lane; j < ns; j += 32) {
+                        const float4 ja = sm.a[j];
+                        const int jid = sm.id[j];
+                        if (SIDE == 0) {
+                            const float jh = sm.hb[j];
+#pragma unroll
+                            for (int i = 0; i < kMGroup; ++i) {
+                                if (i > 0 && i >= np) break;  // padding of a short group (warp-uniform)
+                                float gx, gy, gz, gmv;
+                                pair_grad32(ox[i] - ja.x, oy[i] - ja.y, oz[i] - ja.z, oh[i] + jh, ja.w, ovx[i], ovy[i],
+                                            ovz[i], ow[i], gx, gy, gz, gmv);
+                                if (jid != oid[i]) {
+                                    acc[NQ * i] += gx;
+                                    acc[NQ * i + 1] += gy;
+                                    acc[NQ * i + 2] += gz;
+                                }
+                            }
+                        } else {
+                            const float4 jv = sm.v[j];
+#pragma unroll
+                            for (int i = 0; i < kMGroup; ++i) {
+                                if (i > 0 && i >= np) break;  // padding of a short group (warp-uniform)
+                                float gx, gy, gz, gmv;
+                                pair_grad32(ja.x - ox[i], ja.y - oy[i], ja.z - oz[i], ja.w + oh[i], om[i], jv.x, jv.y, jv.z,
+                                            jv.w, gx, gy, gz, gmv);
+                                if (jid != oid[i]) {
+                                    acc[NQ * i] -= gx;
+                                    acc[NQ * i + 1] -= gy;
+                                    acc[NQ * i + 2] -= gz;
+                                    acc[NQ * i + 3] += gmv;
+                                }
                             }
                         }
                     }
-                }
+                    // lane l ends with quantity l (of NQ * kMGroup <= 32) of this tile, then folds it in
+                    float E[32];
 #pragma unroll
-                for (int i = 0; i < NQ * kMGroup; ++i) comp_add(cs[i], ce[i], acc[i]);
+                    for (int i = 0; i < 32; ++i) E[i] = 0.f;
+                    reduce_scatter_df<32>(acc, E);
+                    float2 st = sm.gacc[gi][lane];
+                    float t, e;
+                    two_sum(st.x, acc[0], t, e);
+                    st.x = t;
+                    st.y = __fadd_rn(__fadd_rn(st.y, E[0]), e);
+                    sm.gacc[gi][lane] = st;
+                }
                 __syncwarp();
             }
-            // lanes reduce; lane l ends with quantity l (of NQ * kMGroup <= 32)
-            float V[32], E[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                V[i] = i < NQ * kMGroup ? cs[i] : 0.f;
-                E[i] = i < NQ * kMGroup ? ce[i] : 0.f;
+            for (int gi = 0; gi < ng; ++gi) {
+                const int p0 = P0 + gi * kMGroup;
+                const int np = min(kMGroup, n - p0);
+                const float2 st = sm.gacc[gi][lane];
+                const double tot = (double)st.x + (double)st.y;
+                if (lane < NQ * np) {
+                    const int i = lane / NQ, qq = lane - NQ * i;
+                    const int p = f + p0 + i;
+                    if (qq < 3)
+                        c.gxs[3 * (int64_t)p + qq] += tot;
+                    else
+                        c.gms[p] += tot;
+                }
             }
-            reduce_scatter_df<32>(V, E);
-            const double tot = (double)V[0] + (double)E[0];
-            if (lane < NQ * np) {
-                const int i = lane / NQ, qq = lane - NQ * i;
-                const int p = f + p0 + i;
-                if (qq < 3)
-                    c.gxs[3 * (int64_t)p + qq] += tot;
-                else
-                    c.gms[p] += tot;
-            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
