@@ -318,10 +318,44 @@ __device__ inline void warp_sort(int32_t (&v)[R]) {
     }
 }
 
+// The same network on each half-warp separately: 16 lanes x R keys per segment (shuffle
+// distances below 16 stay inside a half-warp), so two rows of up to 16 R entries sort at once.
+template <int R>
+__device__ inline void halfwarp_sort(int32_t (&v)[R]) {
+    const int hl = threadIdx.x & 15;
+#pragma unroll
+    for (int k = 2; k <= 16 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 16) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int p = r ^ (j >> 4);
+                    if (p > r) {
+                        const bool up = ((r * 16 + hl) & k) == 0;
+                        const int32_t x = v[r], y = v[p];
+                        v[r] = up ? min(x, y) : max(x, y);
+                        v[p] = up ? max(x, y) : min(x, y);
+                    }
+                }
+            } else {
+                const bool lower = (hl & j) == 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int32_t y = __shfl_xor_sync(kFull, v[r], j);
+                    const bool up = ((r * 16 + hl) & k) == 0;
+                    v[r] = (lower == up) ? min(v[r], y) : max(v[r], y);
+                }
+            }
+        }
+    }
+}
+
 // A warp takes 32 consecutive particles (sorted indices): their permutation entries and offsets
-// are loaded once, coalesced; then row by row the slot entries are mapped to original indices,
-// sorted in registers and written at the row's offset, the next row's entries being gathered
-// before the current row is sorted.  Rows longer than kRowCap are written by k_nb_long.
+// are loaded once, coalesced; then two rows at a time the slot entries are mapped to original
+// indices, sorted in registers (one row per half-warp when both have at most 64 entries, else
+// one row at a time over the warp) and written at the row's offset.  Rows longer than kRowCap
+// are written by k_nb_long.
 __device__ inline void load_row(const int32_t *rows, const int32_t *pidx, int64_t a, int n, int32_t v[4]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -345,29 +379,57 @@ __global__ void __launch_bounds__(256) k_nb_compact(const int32_t *rows, const i
             nl = (int)(offsets[r + 1] - ol);
         }
         const int cnt = (int)(N - base < 32 ? N - base : 32);
-        int32_t cur[4], nxt[4];
-        load_row(rows, pidx, base, __shfl_sync(0xffffffffu, nl, 0), cur);
-        for (int i = 0; i < cnt; ++i) {
-            if (i + 1 < cnt) load_row(rows, pidx, base + i + 1, __shfl_sync(0xffffffffu, nl, i + 1), nxt);
-            const int n = __shfl_sync(0xffffffffu, nl, i);
-            const int64_t o = __shfl_sync(0xffffffffu, ol, i);
-            if (n <= 32) {
-                int32_t v[1] = {cur[0]};
-                warp_sort<1>(v);
-                if (lane < n) idx[o + lane] = v[0];
-            } else if (n <= 64) {
-                int32_t v[2] = {cur[0], cur[1]};
-                warp_sort<2>(v);
-                idx[o + lane] = v[0];
-                if (lane + 32 < n) idx[o + lane + 32] = v[1];
-            } else if (n <= kRowCap) {
-                warp_sort<4>(cur);
+        const int half = lane >> 4, hl = lane & 15;
+        for (int i = 0; i < cnt; i += 2) {
+            const int n0 = __shfl_sync(0xffffffffu, nl, i);
+            const int n1 = i + 1 < cnt ? __shfl_sync(0xffffffffu, nl, i + 1) : 0;
+            const int64_t o0 = __shfl_sync(0xffffffffu, ol, i);
+            const int64_t o1 = __shfl_sync(0xffffffffu, ol, min(i + 1, cnt - 1));
+            if (n0 <= 64 && n1 <= 64) {
+                // two rows at once, one per half-warp: up to 16 R entries each
+                const int n = half ? n1 : n0;
+                const int64_t a = base + i + half, o = half ? o1 : o0;
+                int32_t v[4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (r * 32 + lane < n) idx[o + r * 32 + lane] = cur[r];
+                for (int r = 0; r < 4; ++r) {
+                    const int q = r * 16 + hl;
+                    v[r] = (q < n) ? pidx[rows[a * kRowCap + q]] : INT32_MAX;
+                }
+                if (n0 <= 32 && n1 <= 32) {
+                    int32_t w2[2] = {v[0], v[1]};
+                    halfwarp_sort<2>(w2);
+                    if (hl < n) idx[o + hl] = w2[0];
+                    if (16 + hl < n) idx[o + 16 + hl] = w2[1];
+                } else {
+                    halfwarp_sort<4>(v);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (r * 16 + hl < n) idx[o + r * 16 + hl] = v[r];
+                }
+                continue;
             }
+            // otherwise one row at a time over the whole warp
+            for (int u = 0; u < 2 && i + u < cnt; ++u) {
+                const int n = u ? n1 : n0;
+                const int64_t o = u ? o1 : o0;
+                int32_t cur[4];
+                load_row(rows, pidx, base + i + u, n, cur);
+                if (n <= 32) {
+                    int32_t v[1] = {cur[0]};
+                    warp_sort<1>(v);
+                    if (lane < n) idx[o + lane] = v[0];
+                } else if (n <= 64) {
+                    int32_t v[2] = {cur[0], cur[1]};
+                    warp_sort<2>(v);
+                    idx[o + lane] = v[0];
+                    if (lane + 32 < n) idx[o + lane + 32] = v[1];
+                } else if (n <= kRowCap) {
+                    warp_sort<4>(cur);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) cur[r] = nxt[r];
+                    for (int r = 0; r < 4; ++r)
+                        if (r * 32 + lane < n) idx[o + r * 32 + lane] = cur[r];
+                }
+            }
         }
     }
 }
