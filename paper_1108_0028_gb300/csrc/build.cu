@@ -1176,7 +1176,8 @@ int sm_count() {
 }
 
 int read_status(rcb_tree *t) {
-    RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status, t->d_status, ST_NWORDS * sizeof(int), cudaMemcpyDeviceToHost, t->stream));
+    const int rc = copy_words(t->h_status_dev, t->d_status, ST_NWORDS, t->stream);
+    if (rc) return rc;
     RCB_CUDA_TRY(cudaStreamSynchronize(t->stream));
     return RCB_OK;
 }
@@ -1278,8 +1279,8 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
             nbig_bound = std::min<int64_t>(2 * nbig_bound, big_cap);
         }
         RCB_CUDA_TRY(cudaGetLastError());
-        RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status + ST_NWORDS, t->d_nbig + level, sizeof(int32_t),
-                                     cudaMemcpyDeviceToHost, st));
+        rc = copy_words(t->h_status_dev + ST_NWORDS, t->d_nbig + level, 1, st);
+        if (rc) return rc;
         rc = read_status(t);
         if (rc) return rc;
         if (t->h_status[ST_ERR] & ERRBIT_STATE) return RCB_ERR_LIMIT;

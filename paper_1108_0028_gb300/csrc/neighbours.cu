@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <climits>
 
 #include "rcb_internal.cuh"
@@ -553,10 +554,12 @@ int scan_neighbour_counts(rcb_tree *t) {
 
 int fetch_neighbour_total(rcb_tree *t) {
     cudaStream_t st = t->stream;
-    RCB_CUDA_TRY(cudaMemcpyAsync(&t->nb_total, t->nb_count + t->N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status + ST_NBFALLBACK, t->d_status + ST_NBFALLBACK, 2 * sizeof(int),
-                                 cudaMemcpyDeviceToHost, st));
+    // the total (int64, 8-byte aligned slot of the pinned buffer) and two status words
+    int rc = copy_words(t->h_status_dev + ST_NWORDS + 2, t->nb_count + t->N, 2, st);
+    if (!rc) rc = copy_words(t->h_status_dev + ST_NBFALLBACK, t->d_status + ST_NBFALLBACK, 2, st);
+    if (rc) return rc;
     RCB_CUDA_TRY(cudaStreamSynchronize(st));
+    std::memcpy(&t->nb_total, t->h_status + ST_NWORDS + 2, sizeof(int64_t));
     t->nb_nlong = std::min(t->h_status[ST_LONGROWS], (int)t->N);
     t->nb_valid = 1;
     return RCB_OK;
@@ -584,7 +587,8 @@ int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, in
     const int nsm = sm_count_nb();
     int rc = count_neighbours(t);
     if (rc) return rc;
-    RCB_CUDA_TRY(cudaMemcpyAsync(offsets, t->nb_count, (t->N + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    rc = copy_words(offsets, t->nb_count, 2 * (t->N + 1), st);
+    if (rc) return rc;
     *needed = t->nb_total;
     if (!idx) {
         RCB_CUDA_TRY(cudaStreamSynchronize(st));

@@ -207,6 +207,18 @@ int ensure_lists(rcb_tree *t) {
 }
 
 }  // namespace
+__global__ void k_copy_words(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+int copy_words(void *dst, const void *src, int64_t nwords, cudaStream_t st) {
+    if (nwords <= 0) return RCB_OK;
+    const int grid = (int)std::min<int64_t>((nwords + 255) / 256, 4096);
+    k_copy_words<<<grid, 256, 0, st>>>((const uint32_t *)src, (uint32_t *)dst, nwords); note_launch();
+    return cudaGetLastError() == cudaSuccess ? RCB_OK : RCB_ERR_CUDA;
+}
+
 __global__ void k_fill_ones(double *v, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = 1.0;
 }
@@ -254,6 +266,11 @@ int rcb_build(const double *x, const double *m, const double *h, int64_t N, cons
         if (!t) return RCB_ERR_ALLOC;
         std::memset((void *)t, 0, sizeof(rcb_tree));
         if (cudaMallocHost((void **)&t->h_status, 2 * ST_NWORDS * sizeof(int)) != cudaSuccess) {
+            delete t;
+            return RCB_ERR_CUDA;
+        }
+        if (cudaHostGetDevicePointer((void **)&t->h_status_dev, t->h_status, 0) != cudaSuccess) {
+            cudaFreeHost(t->h_status);
             delete t;
             return RCB_ERR_CUDA;
         }

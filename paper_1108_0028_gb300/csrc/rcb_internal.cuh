@@ -213,6 +213,7 @@ struct rcb_tree {
     // status
     int *d_status;  // [ST_NWORDS]
     int *h_status;  // pinned mirror ([ST_NWORDS + 16])
+    int *h_status_dev;  // the same pinned buffer as the device sees it (written by kernels)
     int *d_E;       // [4] fixed-point exponents E_x, E_y, E_z, E_m
     int32_t *d_nbig;  // [kMaxL + 2] large cells per level of the level passes
     unsigned long long *d_maxbits;  // [4] bit patterns of max |m x_d| and max m
@@ -309,6 +310,9 @@ int refit_tree(rcb_tree *t, const double *x, const double *m);
 int walk_tree(rcb_tree *t);
 int integrity_outside(rcb_tree *t, const double *x, int64_t *outside);  // build.cu
 int gather_h(rcb_tree *t, const double *h);                             // build.cu
+// nwords 32-bit words from src to dst by a kernel on st (no copy engine: small readbacks into the
+// pinned status buffer and device copies do not queue behind the caller's large transfers)
+int copy_words(void *dst, const void *src, int64_t nwords, cudaStream_t st);  // rcb_api.cu
 int density(rcb_tree *t, const int64_t *offsets, const int32_t *idx, double *rho);  // density.cu
 // neighbours.cu
 int neighbour_counts(rcb_tree *t, int64_t *counts, int *status);  // count pass into caller memory

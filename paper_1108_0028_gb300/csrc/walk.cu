@@ -397,7 +397,10 @@ static int walk_into(rcb_tree *t, int mode, int32_t *&near_list, int32_t *&far_l
             note_launch();
         }
         RCB_CUDA_TRY(cudaGetLastError());
-        RCB_CUDA_TRY(cudaMemcpyAsync(t->h_status, t->d_status, ST_NWORDS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        {
+            const int rc = copy_words(t->h_status_dev, t->d_status, ST_NWORDS, st);
+            if (rc) return rc;
+        }
         RCB_CUDA_TRY(cudaStreamSynchronize(st));
         if (t->h_status[ST_ERR] & ERRBIT_LIMIT) return RCB_ERR_LIMIT;
         int need_near = t->h_status[ST_MAXNEAR], need_far = t->h_status[ST_MAXFAR];
