@@ -187,6 +187,41 @@ def test_walk_covers_every_particle_exactly_once(plummer4096):
             assert nd["H"][n] < 0.7 * R * (1 + 1e-12)
 
 
+def test_mac_only_walk(plummer4096):
+    # The Sec. 2.5 variant (no reachability override): theta = 0 is still direct summation; for
+    # every sink the far nodes and near cells cover each particle exactly once, every far node
+    # passes the MAC, the near cells carry no candidate flag, and they are a subset of the
+    # conservative walk's near cells (a leaf whose ancestors all fail the MAC is visited and kept
+    # near by both walks).
+    x, m, h, T = plummer4096
+    T.walk(0.0, mac_only=True)
+    acc, _ = T.gravity()
+    ad, _ = oracle.direct(x, m, h)
+    assert (np.linalg.norm(acc - ad, axis=1) / np.linalg.norm(ad, axis=1)).max() < 1e-12
+    T.walk(0.7)
+    std = T.lists()
+    T.walk(0.7, mac_only=True)
+    mac = T.lists()
+    nd = T.nodes()
+    leaf0 = 1 << T.L
+    assert mac["near_ids"].size < std["near_ids"].size
+    assert not mac["near_reach"].any()
+    for j in range(T.nleaves):
+        if nd["count"][leaf0 + j] == 0:
+            continue
+        near = mac["near_ids"][mac["near_off"][j]:mac["near_off"][j + 1]]
+        far = mac["far_ids"][mac["far_off"][j]:mac["far_off"][j + 1]]
+        cover = np.zeros(T.N, np.int64)
+        for n in list(near) + list(far):
+            cover[nd["first"][n]:nd["first"][n] + nd["count"][n]] += 1
+        assert np.all(cover == 1)
+        A = leaf0 + j
+        for n in far:
+            R = np.linalg.norm(nd["com"][A] - nd["com"][n])
+            assert nd["H"][n] < 0.7 * R * (1 + 1e-12)
+        assert set(near.tolist()) <= set(std["near_ids"][std["near_off"][j]:std["near_off"][j + 1]].tolist())
+
+
 def test_hand_built_two_clusters():
     # two tight clusters 100 apart, 8 particles each: N = 16 gives L = 1 (16/2 < 12); the root
     # splits on x through the COM; each leaf is near to itself and far to the other.
