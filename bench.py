@@ -265,10 +265,12 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
     # timed region, which ends when the last results are on the host.
     S, Cin, Cout = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     xin = [(torch.empty_like(xt), torch.empty_like(mt), torch.empty_like(ht)) for _ in range(2)]
-    outh = [(torch.empty(off0.shape, dtype=off0.dtype).pin_memory(), torch.empty(idx0.shape, dtype=idx0.dtype).pin_memory(),
-             torch.empty(acc0.shape, dtype=acc0.dtype).pin_memory(), torch.empty(pot0.shape, dtype=pot0.dtype).pin_memory())
-            for _ in range(2)]
+    # results on the device and on the host, two of each, allocated once
+    outd = [(torch.empty_like(off0), torch.empty(max(idx0.numel(), 1) + (1 << 20), dtype=idx0.dtype, device=xt.device),
+             torch.empty_like(acc0), torch.empty_like(pot0)) for _ in range(2)]
+    outh = [tuple(torch.empty(d_.shape, dtype=d_.dtype).pin_memory() for d_ in o) for o in outd]
     in_ev = [torch.cuda.Event(), torch.cuda.Event()]
+    out_free = [torch.cuda.Event(), torch.cuda.Event()]  # a buffer's copy to the host has finished
     del off0, idx0, acc0, pot0
 
     def copy_in(b):
@@ -280,30 +282,38 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
     K = max(3, a.steps // 2)
     flush.zero_()
     copy_in(0)
+    for b in range(2):
+        out_free[b].record(Cout)
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(S)
+    nidx = 0
     for k in range(K):
         b = k % 2
+        offd, idxd, accd, potd = outd[b]
         S.wait_event(in_ev[b])
-        with torch.cuda.stream(S):
-            tree.rebuild(*xin[b], stream=S)
-            if k + 1 < K:
-                copy_in(1 - b)  # the other buffer's build finished before this one began
-            acc, pot, off, idx = tree.gravity_neighbours(stream=S)
-            done = torch.cuda.Event()
-            done.record(S)
+        tree.rebuild(*xin[b], stream=S)
+        if k + 1 < K:
+            copy_in(1 - b)  # the other buffer's build finished before this one began
+        S.wait_event(out_free[b])
+        rcb.rcb_gravity_neighbours(tree.handle, accd, potd, offd, S)
+        st_, nidx = rcb.rcb_neighbours(tree.handle, offd, idxd, idxd.numel(), S)
+        if st_ != 0:
+            raise RuntimeError(f"rcb_neighbours failed: {st_}")
+        done = torch.cuda.Event()
+        done.record(S)
         Cout.wait_event(done)
         with torch.cuda.stream(Cout):
-            for h_, d_ in zip(outh[b], (off, idx, acc, pot)):
-                h_.view(-1)[:d_.numel()].copy_(d_.view(-1), non_blocking=True)
-                d_.record_stream(Cout)
+            for h_, d_, n_ in zip(outh[b], outd[b], (offd.numel(), nidx, accd.numel(), potd.numel())):
+                h_.view(-1)[:n_].copy_(d_.view(-1)[:n_], non_blocking=True)
+            out_free[b].record(Cout)
     last = torch.cuda.Event()
     last.record(Cout)
     S.wait_event(last)
     e1.record(S)
     torch.cuda.synchronize()
+    idx = outd[0][1][:nidx]
     ems = max_over_ranks(e0.elapsed_time(e1) / K, dist, xt.device)
     h2d = (x.nbytes + m.nbytes + h.nbytes)
     d2h = offh.numel() * 8 + idx_total_bytes(idx) + acch.numel() * 8 + poth.numel() * 8
