@@ -53,6 +53,7 @@ def lib():
             sig = {
                 "orc_depth": (ctypes.c_int, [_I64, ctypes.c_int32]),
                 "orc_build": (_P, [_P, _P, _P, _I64, ctypes.c_int32, _P]),
+                "orc_build_split": (_P, [_P, _P, _P, _I64, ctypes.c_int32, ctypes.c_int, _P]),
                 "orc_free": (None, [_P]),
                 "orc_info": (None, [_P, _P]),
                 "orc_export_nodes": (None, [_P] + [_P] * 14),
@@ -213,13 +214,19 @@ def brute_neighbours(x, h):
 class OracleTree:
     """The oracle's RCB tree (Sec. 2.1) with walk, neighbours, gravity and gradients."""
 
-    def __init__(self, x, m, h, n_ll: int = 12):
+    def __init__(self, x, m, h, n_ll: int = 12, split: str = "mass"):
+        """split: "mass" cuts every cell through its centre of mass (CMS, Sec. 2.1.3), "median"
+        through the median position along the longest side (the MPS variant of the same
+        section)."""
+        if split not in ("mass", "median"):
+            raise ValueError("split must be 'mass' or 'median'")
         self.x = _f64(x, (-1, 3))
         self.m = _f64(m)
         self.h = _f64(h)
         self.N = self.x.shape[0]
         st = ctypes.c_int(0)
-        self._t = lib().orc_build(_ptr(self.x), _ptr(self.m), _ptr(self.h), self.N, int(n_ll), ctypes.byref(st))
+        self._t = lib().orc_build_split(_ptr(self.x), _ptr(self.m), _ptr(self.h), self.N, int(n_ll),
+                                        1 if split == "median" else 0, ctypes.byref(st))
         if not self._t:
             raise ValueError(f"oracle build failed with status {st.value}")
         info = np.zeros(8, dtype=np.int64)

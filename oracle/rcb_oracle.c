@@ -9,7 +9,8 @@
  *
  * Every step follows the paper in its own order and notation:
  *   Sec. 2.1.1  depth rule: split until the mean ll-cell occupancy drops below N_ll
- *   Sec. 2.1.3  split the longest side through the centre of mass (CMS)
+ *   Sec. 2.1.3  split the longest side through the centre of mass (CMS); variant: through the
+ *               median position (MPS)
  *   Sec. 2.1.4  quick-sort-like in-place partition of each cell's index range
  *   Sec. 2.1.5  heap labels: root 1, children 2n and 2n+1, level k spans 2^k .. 2^(k+1)-1
  *   Sec. 2.1.6  Eq. 1 (ll-cell quadrupoles) and Eq. 2 (shift-up to parents)
@@ -47,6 +48,7 @@
 typedef __int128 i128;
 
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_ALLOC = -2, ORC_ERR_CAPACITY = -3, ORC_ERR_STATE = -4 };
+enum { ORC_SPLIT_CMS = 0, ORC_SPLIT_MPS = 1 };
 
 /* ------------------------------------------------------------------------------------------ */
 /* Tree storage.  Node labels follow Sec. 2.1.5: nodes 1 .. 2^(L+1)-1; arrays are sized 2^(L+1)
@@ -295,9 +297,37 @@ static int fixed_point(orc_tree *t) {
     return ORC_OK;
 }
 
+static int cmp_double(const void *a, const void *b) {
+    double u = *(const double *)a, v = *(const double *)b;
+    return (u > v) - (u < v);
+}
+
+/* Sec. 2.1.3, the median position split (MPS): the coordinate of rank floor(cnt/2), counted from
+ * 0 in ascending order, of the cell's particles along the axis.  With distinct coordinates the
+ * cut x < s leaves floor(cnt/2) particles on the left and the rest on the right; particles tied
+ * with the median coordinate all go right. */
+static double median_position(const orc_tree *t, int64_t f, int64_t cnt, int ax) {
+    double *v = malloc(sizeof(double) * (size_t)cnt);
+    if (!v) return NAN;
+    for (int64_t i = 0; i < cnt; ++i) v[i] = t->x[ax][f + i];
+    qsort(v, (size_t)cnt, sizeof(double), cmp_double);
+    double s = v[cnt / 2];
+    free(v);
+    return s;
+}
+
+orc_tree *orc_build_split(const double *x, const double *m, const double *h, int64_t N, int32_t n_ll,
+                          int split_mode, int *status);
+
 orc_tree *orc_build(const double *x, const double *m, const double *h, int64_t N, int32_t n_ll, int *status) {
+    return orc_build_split(x, m, h, N, n_ll, ORC_SPLIT_CMS, status);
+}
+
+orc_tree *orc_build_split(const double *x, const double *m, const double *h, int64_t N, int32_t n_ll,
+                          int split_mode, int *status) {
     *status = ORC_ERR_ARG;
     if (N < 1 || N >= ((int64_t)1 << 31) || n_ll < 1) return NULL;
+    if (split_mode != ORC_SPLIT_CMS && split_mode != ORC_SPLIT_MPS) return NULL;
     for (int64_t i = 0; i < N; ++i) {
         if (!isfinite(x[3 * i]) || !isfinite(x[3 * i + 1]) || !isfinite(x[3 * i + 2])) return NULL;
         if (!isfinite(m[i]) || !(m[i] > 0.0) || !isfinite(h[i]) || !(h[i] > 0.0)) return NULL;
@@ -327,13 +357,19 @@ orc_tree *orc_build(const double *x, const double *m, const double *h, int64_t N
             double s = 0.0;
             int64_t nleft = 0;
             if (cnt > 0) {
-                /* Sec. 2.1.3: the longest side (ties -> lowest axis), cut through the CMS. */
+                /* Sec. 2.1.3: the longest side (ties -> lowest axis), cut through the CMS, or
+                 * through the median position for the MPS variant. */
                 double best = -1.0;
                 for (int d = 0; d < 3; ++d) {
                     double ext = t->bmax[d][c] - t->bmin[d][c];
                     if (ext > best) { best = ext; ax = d; }
                 }
-                s = t->com[ax][c];
+                if (split_mode == ORC_SPLIT_MPS) {
+                    s = median_position(t, f, cnt, ax);
+                    if (isnan(s)) { orc_free(t); *status = ORC_ERR_ALLOC; return NULL; }
+                } else {
+                    s = t->com[ax][c];
+                }
                 /* Sec. 2.1.4: one pass; smaller coordinates to the front, the rest to the back. */
                 int64_t i = f, j = f + cnt - 1;
                 while (i <= j) {

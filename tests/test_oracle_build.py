@@ -285,3 +285,73 @@ def test_unit_weight_splits_are_centres_of_number():
         vals = x[perm[f:f + n], ax]
         exact = float(sum(Fraction(v) for v in vals) / n)
         assert abs(nd["split"][c] - exact) <= 2 * np.spacing(abs(exact)), c
+
+
+def _check_median_cells(x, T, distinct):
+    # Sec. 2.1.3, the median position split: every cell is cut along its longest side at the
+    # order statistic of rank floor(n/2) of its coordinates, i.e. #(x < s) <= n // 2 < #(x <= s),
+    # and s is a coordinate of the cell (the smallest of the right child).  With distinct
+    # coordinates the daughters hold exactly floor(n/2) and ceil(n/2) particles.
+    nd, perm = T.nodes(), T.perm()
+    for n in range(1, 1 << T.L):
+        f, c = nd["first"][n], nd["count"][n]
+        if c == 0:
+            continue
+        pts = x[perm[f:f + c]]
+        ax = int(np.argmax(pts.max(0) - pts.min(0)))
+        assert nd["axis"][n] == ax
+        s = nd["split"][n]
+        v = pts[:, ax]
+        below, upto = int(np.sum(v < s)), int(np.sum(v <= s))
+        assert below <= c // 2 < upto, n
+        cl, cr = nd["count"][2 * n], nd["count"][2 * n + 1]
+        assert cl == below and cl + cr == c
+        assert np.all(x[perm[f:f + cl], ax] < s)
+        right = x[perm[f + cl:f + c], ax]
+        assert np.all(right >= s) and right.min() == s
+        if distinct:
+            assert cl == c // 2 and cr == c - c // 2
+
+
+@pytest.mark.parametrize("kind,N", [("plummer", 3000), ("sphere", 2049), ("cube", 13)])
+def test_median_split_is_the_order_statistic(kind, N):
+    x, m, h = synth.make_particles(kind, N, 78, "loguniform10")
+    assert all(len(np.unique(x[:, d])) == N for d in range(3))
+    T = oracle.OracleTree(x, m, h, split="median")
+    _check_median_cells(x, T, distinct=True)
+
+
+def test_median_split_with_tied_coordinates():
+    # a lattice: many particles share each coordinate; the cut still sits at the order statistic
+    g = np.arange(12, dtype=np.float64)
+    x = np.stack(np.meshgrid(g, g, g[:9], indexing="ij"), -1).reshape(-1, 3)
+    N = x.shape[0]
+    T = oracle.OracleTree(x, np.ones(N), np.full(N, 0.7), split="median")
+    _check_median_cells(x, T, distinct=False)
+
+
+def test_median_split_balances_every_leaf():
+    # N = 12 * 2^8 particles at N_ll = 12 give L = 9 and 512 ll-cells of exactly 6 particles each
+    N = 3072
+    x, m, h = synth.make_particles("plummer", N, 79, "loguniform10")
+    T = oracle.OracleTree(x, m, h, split="median")
+    assert T.L == 9
+    nd = T.nodes()
+    assert np.all(nd["count"][1 << 9:] == 6)
+    # the centre-of-mass split of the same set is not balanced
+    assert not np.all(oracle.OracleTree(x, m, h).nodes()["count"][1 << 9:] == 6)
+
+
+def test_median_split_tree_update_and_refit():
+    # the integrity check and the refit use the stored planes, whatever chose them
+    N = 3000
+    x, m, h = synth.make_particles("sphere", N, 80, "loguniform10")
+    a = oracle.OracleTree(x, m, h, split="median")
+    before = a.nodes()
+    assert a.update(x, m, h) == 0
+    after = a.nodes()
+    for k in ("split", "axis", "count", "com", "Q"):
+        assert np.array_equal(before[k], after[k]), k
+    x2 = synth.jitter(x, 3e-2, 81)
+    expect = int(np.sum(_route_leaves(a.nodes(), a.L, x2) != a.leaf_of()))
+    assert expect > 0 and a.update(x2, m, h) == expect
