@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--kind", default="sphere")
     p.add_argument("--mass", default="loguniform10")
     p.add_argument("--theta", type=float, default=0.7)
+    p.add_argument("--split", choices=["mass", "number", "median"], default="mass",
+                   help="cut of the headline tree (Sec. 2.1.3): centre of mass, centre of number, median")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-sinks", type=int, default=256)
     p.add_argument("--headline-only", action="store_true",
@@ -70,7 +72,7 @@ def workload_name(a):
 
 def bench_config(a, world):
     """The `config` object of the JSON line (both arms)."""
-    return {"workload": workload_name(a), "N": a.n, "theta": a.theta, "n_ll": N_LL, "form": "mixed",
+    return {"workload": workload_name(a), "N": a.n, "theta": a.theta, "n_ll": N_LL, "form": "mixed", "split": a.split,
             "parallelism": f"replicas x{world}",
             "l2": "inputs (164 MB) exceed L2 and a 256 MB buffer is written between timed steps"}
 
@@ -403,7 +405,37 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
                 "rms_rel_diff_vs_conservative": float(torch.sqrt(torch.mean(dmac * dmac))),
                 "path": "rcb_gravity on a tree built with RCB_FLAG_MAC_ONLY (near lists from the MAC alone)"}
     mac_tree.free()
-    del acc_mac, acc_std, dmac
+    del acc_mac, dmac
+    # the split variants of Sec. 2.1.3 on the same input (centre of number, median position):
+    # construction, walk and gravity by the library's stage events, list sizes, and the force
+    # difference from the centre-of-mass tree
+    std_info = tree.info()
+    split_variants = {"mass": {"near_pairs": near_pairs_std, "far_total": std_info["far_total"]}}
+    for split in ("number", "median"):
+        vt = rcb.RCBTree(xt, mt, ht, n_ll=N_LL, theta=a.theta, precision="mixed", timing=True, split=split)
+        b_ms, w_ms, g_ms = [], [], []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            vt.rebuild(xt, mt, ht)
+            st = vt.stage_times()
+            b_ms.append(st["build"])
+            w_ms.append(st["walk"])
+            flush.zero_()
+            torch.cuda.synchronize()
+            acc_v, _ = vt.gravity()
+            st = vt.stage_times()
+            g_ms.append(st["far"] + st["near"])
+        dv = torch.linalg.norm(acc_v - acc_std, dim=1) / torch.linalg.norm(acc_std, dim=1)
+        vinfo = vt.info()
+        split_variants[split] = {
+            "construction_ms": statistics.mean(b_ms) - statistics.mean(w_ms), "walk_ms": statistics.mean(w_ms),
+            "gravity_ms": statistics.mean(g_ms), "near_pairs": vinfo["near_pairs"], "far_total": vinfo["far_total"],
+            "rms_rel_diff_vs_mass_split": float(torch.sqrt(torch.mean(dv * dv))),
+            "p999_rel_diff_vs_mass_split": float(torch.quantile(dv[:: max(1, dv.numel() // 1000000)].float(), 0.999))}
+        vt.free()
+        del acc_v, dv
+    del acc_std
     L = tree.info()["L"]
     build_bytes = a.n * (72 * L + 56)  # every level reads and writes 36 B per particle, h gathered once
     per_stage = {
@@ -421,6 +453,7 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
         "neighbours_gravity_fused": {"ms": fused_ms, "mparticles_s": job_throughput(world, a.n, fused_ms),
                                      "path": "rcb_gravity_neighbours + compaction (the step's path)"},
         "gravity_mac_only": mac_only,
+        "split_variants": split_variants,
         "density": {"ms": density_ms, "mparticles_s": job_throughput(world, a.n, density_ms),
                     "path": "rcb_density over the CSR of rcb_neighbours (cubic spline, support 2h)"},
         "update": {"ms": update_ms, "mparticles_s": job_throughput(world, a.n, update_ms),
@@ -457,7 +490,7 @@ def run_ours(a, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    tree = rcb.RCBTree(xt, mt, ht, n_ll=N_LL, theta=a.theta, precision="mixed", timing=True)
+    tree = rcb.RCBTree(xt, mt, ht, n_ll=N_LL, theta=a.theta, precision="mixed", timing=True, split=a.split)
 
     def step():
         tree.rebuild(xt, mt, ht)

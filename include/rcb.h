@@ -48,6 +48,13 @@ extern "C" {
                                 rcb_gravity_neighbours runs gravity and the neighbour count as
                                 two passes */
 
+#define RCB_FLAG_MEDIAN_SPLIT 8u /* Sec. 2.1.3 variant: cut every cell at the median position along
+                                    its longest side (the coordinate of rank floor(n/2) of its n
+                                    particles; x < split goes left, so particles tied with the
+                                    median all go right), giving daughters of floor(n/2) and
+                                    ceil(n/2) particles when coordinates are distinct; excludes
+                                    RCB_FLAG_CENTRE_OF_NUMBER (RCB_ERR_ARG) */
+
 #define RCB_FP64 0  /* gravity in FP64 throughout */
 #define RCB_MIXED 1 /* FP32 near field on cell-relative offsets with compensated sums; FP32
                        multipole tensors; Taylor coefficients accumulated with compensation
@@ -60,7 +67,7 @@ typedef struct {
                           N < n_ll * 2^L (Table 1) */
     int32_t precision; /* RCB_FP64 or RCB_MIXED: form used by rcb_gravity and the backward */
     double theta;      /* opening angle of the geometric MAC, Eq. 4 (theta = 0: direct sum) */
-    uint32_t flags;    /* 0 or RCB_FLAG_TIMING */
+    uint32_t flags;    /* 0 or an OR of the RCB_FLAG_* bits above */
     uint32_t reserved;
 } rcb_params;
 

@@ -27,6 +27,8 @@ _PRECISION = {"fp64": RCB_FP64, "mixed": RCB_MIXED, RCB_FP64: RCB_FP64, RCB_MIXE
 RCB_FLAG_TIMING = 1
 RCB_FLAG_CENTRE_OF_NUMBER = 2
 RCB_FLAG_MAC_ONLY = 4
+RCB_FLAG_MEDIAN_SPLIT = 8
+_SPLIT_FLAG = {"mass": 0, "number": RCB_FLAG_CENTRE_OF_NUMBER, "median": RCB_FLAG_MEDIAN_SPLIT}
 SYMBOLS = ["rcb_build", "rcb_neighbours", "rcb_gravity", "rcb_gravity_neighbours", "rcb_gravity_backward", "rcb_refit", "rcb_update", "rcb_density", "rcb_set_precision",
            "rcb_tree_info", "rcb_export_topology", "rcb_export_lists", "rcb_stage_times", "rcb_free", "rcb_strerror",
            "rcb_neighbour_offsets_noalloc"]
@@ -211,15 +213,15 @@ class RCBTree:
     def __init__(self, x, m, h, n_ll: int = 12, theta: float = 0.7, precision="mixed", stream=None,
                  timing: bool = False, split: str = "mass", mac_only: bool = False):
         """split: "mass" cuts every cell through its centre of mass (Sec. 2.1.3), "number" through
-        its centre of number (unit weights; node moments stay mass-weighted).  mac_only: near
-        lists from the MAC alone (Sec. 2.5 variant), neighbour candidates from a walk of their
-        own."""
-        if split not in ("mass", "number"):
-            raise ValueError(f"split must be 'mass' or 'number', not {split!r}")
+        its centre of number (unit weights; node moments stay mass-weighted), "median" at the
+        median position along the longest side (the MPS variant: daughters of floor(n/2) and
+        ceil(n/2) particles).  mac_only: near lists from the MAC alone (Sec. 2.5 variant),
+        neighbour candidates from a walk of their own."""
+        if split not in _SPLIT_FLAG:
+            raise ValueError(f"split must be 'mass', 'number' or 'median', not {split!r}")
         self._h = None
         self.n_ll, self.theta, self.precision = n_ll, theta, precision
-        self.flags = (RCB_FLAG_TIMING if timing else 0) | (RCB_FLAG_CENTRE_OF_NUMBER if split == "number" else 0) | \
-            (RCB_FLAG_MAC_ONLY if mac_only else 0)
+        self.flags = (RCB_FLAG_TIMING if timing else 0) | _SPLIT_FLAG[split] | (RCB_FLAG_MAC_ONLY if mac_only else 0)
         self._h = rcb_build(x, m, h, n_ll, theta, precision, None, stream, self.flags)
         self.N = x.shape[0]
         self.device = x.device

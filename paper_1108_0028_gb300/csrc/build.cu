@@ -11,6 +11,9 @@
 //   subtree     one CTA per queued root loads its <= kTcta records into shared memory and
 //               splits them level by level down to L (flags, block scan, stable move, exact
 //               children reductions), then writes the particles in tree order.
+//   median      (median position split only) before a level pass, the key of rank floor(n/2)
+//               along each large cell's axis by an exact radix selection, and in the subtree
+//               kernel by counting ranks in shared memory; it replaces the centre-of-mass split
 //   leaves      per non-empty ll-cell: Eq. 1 quadrupole, radii h_node_int and h_node, float32
 //               cell-relative copies; then an arrival-counter climb computes every parent by
 //               Eq. 2 as soon as both of its children are done.
@@ -94,6 +97,7 @@ __device__ void red_block(Red &r, Red *scratch) {
 
 struct Ctx {  // device-side view of the tree arrays used by the build kernels
     int L;
+    int mps;  // median position split instead of the centre-of-mass split
     int64_t capN;
     int64_t cap_big, cap_roots;
     int *status;
@@ -536,6 +540,108 @@ __global__ void __launch_bounds__(kChunkThreads)
 }
 
 // ------------------------------------------------------------------------------------------
+// Median position split of the large cells of one level (Sec. 2.1.3 variant).  The split key is
+// the order statistic of rank floor(n/2) of the cell's keys along its axis, found by an exact
+// radix selection: eight rounds of one 8-bit digit each, from the most significant.  In a round
+// every chunk histograms the digit of those keys that match the prefix chosen so far (k_mps_hist),
+// then one warp per cell finds the digit whose bin holds the rank still sought (k_mps_pick).
+// Keys are dkey with the sign bit flipped, so that unsigned order is coordinate order.
+
+constexpr int kMpsBins = 256;
+
+__device__ inline unsigned long long mps_ukey(double v) {
+    return (unsigned long long)dkey(v) ^ 0x8000000000000000ull;
+}
+
+__global__ void __launch_bounds__(kChunkThreads)
+    k_mps_hist(Ctx c, const int4 *chunks, const int *nchunks_ptr, const double *__restrict__ bx,
+               const double *__restrict__ by, const double *__restrict__ bz, const unsigned long long *prefix,
+               int shift, int32_t *hist) {
+    __shared__ int32_t h[kMpsBins];
+    const int nchunks = *nchunks_ptr;
+    const bool first_round = shift >= 56;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        for (int i = threadIdx.x; i < kMpsBins; i += blockDim.x) h[i] = 0;
+        __syncthreads();
+        const int4 cd = chunks[ch];
+        const int node = cd.x, start = cd.y, cnt = cd.z, cell = cd.w;
+        const int ax = c.naxis[node];
+        const double *b = ax == 0 ? bx : (ax == 1 ? by : bz);
+        const unsigned long long high = first_round ? 0ull : prefix[cell] >> (shift + 8);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const unsigned long long u = mps_ukey(b[start + i]);
+            if (first_round || (u >> (shift + 8)) == high) atomicAdd(&h[(u >> shift) & (kMpsBins - 1)], 1);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kMpsBins; i += blockDim.x)
+            if (h[i]) atomicAdd(&hist[(int64_t)cell * kMpsBins + i], h[i]);
+        __syncthreads();
+    }
+}
+
+// One warp per large cell: the digit holding the sought rank; clears the cell's bins for the next
+// round.  After the last round the prefix is the split key.
+__global__ void k_mps_pick(Ctx c, const int32_t *big, const int32_t *nbig_ptr, int shift, int32_t *hist,
+                           unsigned long long *prefix, int32_t *rank) {
+    const int nbig = *nbig_ptr;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = gw; i < nbig; i += nw) {
+        const int node = big[i];
+        int r = shift >= 56 ? c.ncount[node] / 2 : rank[i];
+        unsigned long long pre = shift >= 56 ? 0ull : prefix[i];
+        int32_t *hc = hist + (int64_t)i * kMpsBins;
+        int v[kMpsBins / 32];
+        int tot = 0;
+#pragma unroll
+        for (int k = 0; k < kMpsBins / 32; ++k) {
+            v[k] = hc[(kMpsBins / 32) * lane + k];
+            hc[(kMpsBins / 32) * lane + k] = 0;
+            tot += v[k];
+        }
+        int incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int excl = incl - tot;
+        const bool mine = r >= excl && r < incl;
+        const unsigned ball = __ballot_sync(0xffffffffu, mine);
+        if (ball == 0u) {  // the histogram does not hold the rank: inconsistent state, report
+            if (lane == 0) atomicOr(&c.status[ST_ERR], ERRBIT_STATE);
+            continue;
+        }
+        int digit = 0, before = 0;
+        if (mine) {
+            int acc = excl;
+#pragma unroll
+            for (int k = 0; k < kMpsBins / 32; ++k) {
+                if (r < acc + v[k]) {
+                    digit = (kMpsBins / 32) * lane + k;
+                    before = acc;
+                    break;
+                }
+                acc += v[k];
+            }
+        }
+        const int src = __ffs(ball) - 1;
+        digit = __shfl_sync(0xffffffffu, digit, src);
+        before = __shfl_sync(0xffffffffu, before, src);
+        r -= before;
+        pre |= (unsigned long long)digit << shift;
+        if (lane == 0) {
+            rank[i] = r;
+            prefix[i] = pre;
+            if (shift == 0) {
+                const int64_t key = (int64_t)(pre ^ 0x8000000000000000ull);
+                c.nsplitkey[node] = key;
+                c.nsplit[node] = dkey_inv(key);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Subtrees in shared memory.
 
 struct SubtreeSmem {
@@ -595,6 +701,31 @@ struct Bufs {
     const int32_t *idx[2];
 };
 
+// Median position split of every cell of order `cur` (all of them internal): each particle's rank
+// along its cell's axis, ties broken by position; the particle of rank floor(n/2) writes its key
+// as the cell's split (exactly one per cell).
+__device__ void subtree_median(const Ctx &c, SubtreeSmem &s, int cur, int n) {
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int ci = s.cellOf[cur][p];
+        const int f = s.cfirst[cur][ci], cn = s.ccount[cur][ci];
+        const int ax = s.caxis[ci];
+        const double *coord = ax == 0 ? s.x : (ax == 1 ? s.y : s.z);
+        const int64_t kp = dkey(coord[s.perm[cur][p]]);
+        int below = 0;
+        for (int q = f; q < f + cn; ++q) {
+            const int64_t kq = dkey(coord[s.perm[cur][q]]);
+            below += (kq < kp) || (kq == kp && q < p);
+        }
+        if (below == cn / 2) {
+            const int node = s.cnode[cur][ci];
+            s.csplit[ci] = kp;
+            c.nsplitkey[node] = kp;
+            c.nsplit[node] = dkey_inv(kp);
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kCtaThreads, 2)
     k_subtree(Ctx c, const int32_t *roots, const int *nroots_ptr, Bufs B, const double *__restrict__ m_in,
               const double *__restrict__ h_in, double *__restrict__ px, double *__restrict__ py,
@@ -646,6 +777,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
             s.nkids = 1;
         }
         __syncthreads();
+        if (c.mps) subtree_median(c, s, 0, n);
         int cur = 0;
         int K = 1;
         for (int level = k0; level < c.L; ++level) {
@@ -774,6 +906,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
             __syncthreads();
             cur = nxt;
             K = K2;
+            if (c.mps && level + 1 < c.L) subtree_median(c, s, cur, n);
         }
         // write the particles in tree order
         for (int p = tid; p < n; p += nt) {
@@ -1144,6 +1277,7 @@ __global__ void k_refit_cells(Ctx c, const int32_t *sinks, int nsinks, const dou
 Ctx make_ctx(rcb_tree *t) {
     Ctx c;
     c.L = t->L;
+    c.mps = (t->params.flags & RCB_FLAG_MEDIAN_SPLIT) ? 1 : 0;
     c.capN = t->cap_N;
     c.cap_big = t->cap_N / (kTcta + 1) + 2;
     c.cap_roots = t->cap_roots;
@@ -1254,6 +1388,10 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
     // launches levels in batches with upper-bound grids and synchronises once per batch.
     int nbig = t->h_status[ST_NBIG];
     int level = 0;
+    if (c.mps) {
+        if (!t->mps_hist || !t->mps_prefix || !t->mps_rank) return RCB_ERR_STATE;
+        RCB_CUDA_TRY(cudaMemsetAsync(t->mps_hist, 0, (size_t)c.cap_big * kMpsBins * sizeof(int32_t), st));
+    }
     ChunkPart *parts = reinterpret_cast<ChunkPart *>(t->chunk_part);
     const int64_t big_cap = N / (kTcta + 1) + 2;
     constexpr int kBatch = 4;
@@ -1266,6 +1404,16 @@ int build_tree(rcb_tree *t, const double *x, const double *m, const double *h) {
             k_chunk_plan<<<1, 1024, 0, st>>>(t->big_list[cur], t->d_nbig + level, t->nfirst, t->ncount,
                                              t->cell_chunk0, t->chunks, t->d_status); note_launch();
             const int g = (int)std::min<int64_t>(bound, (int64_t)nsm * 8);
+            if (c.mps) {
+                const int gp = (int)std::max<int64_t>(1, (nbig_bound * 32 + 255) / 256);
+                for (int shift = 56; shift >= 0; shift -= 8) {
+                    k_mps_hist<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, t->bx[cur],
+                                                            t->by[cur], t->bz[cur], t->mps_prefix, shift,
+                                                            t->mps_hist); note_launch();
+                    k_mps_pick<<<gp, 256, 0, st>>>(c, t->big_list[cur], t->d_nbig + level, shift, t->mps_hist,
+                                                   t->mps_prefix, t->mps_rank); note_launch();
+                }
+            }
             k_level_reduce<<<g, kChunkThreads, 0, st>>>(c, t->chunks, t->d_status + ST_NCHUNKS, t->bx[cur],
                                                         t->by[cur], t->bz[cur], t->bP[cur], parts); note_launch();
             const int gf = (int)std::max<int64_t>(1, (nbig_bound * 32 + 255) / 256);

@@ -91,7 +91,7 @@ void for_each_array(rcb_tree *t, F f) {
                   (void **)&t->coef, (void **)&t->coef32, (void **)&t->nb_count, (void **)&t->nb_long, (void **)&t->nb_rows, (void **)&t->scan_tmp, (void **)&t->tnear_off,
                   (void **)&t->tnear_sink, (void **)&t->tfar_off, (void **)&t->tfar_sink, (void **)&t->adj,
                   (void **)&t->dens_hl, (void **)&t->ones, (void **)&t->cand_list, (void **)&t->cand_far,
-                  (void **)&t->cand_n};
+                  (void **)&t->cand_n, (void **)&t->mps_hist, (void **)&t->mps_prefix, (void **)&t->mps_rank};
     for (void **q : p) f(q);
 }
 
@@ -254,7 +254,9 @@ int rcb_build(const double *x, const double *m, const double *h, int64_t N, cons
     if (N < 1 || N >= ((int64_t)1 << 31)) return RCB_ERR_ARG;
     if (params->n_ll < 1 || !(params->theta >= 0.0) || !std::isfinite(params->theta)) return RCB_ERR_ARG;
     if (params->precision != RCB_FP64 && params->precision != RCB_MIXED) return RCB_ERR_ARG;
-    if ((params->flags & ~(RCB_FLAG_TIMING | RCB_FLAG_CENTRE_OF_NUMBER | RCB_FLAG_MAC_ONLY)) != 0) return RCB_ERR_ARG;
+    if ((params->flags & ~(RCB_FLAG_TIMING | RCB_FLAG_CENTRE_OF_NUMBER | RCB_FLAG_MAC_ONLY | RCB_FLAG_MEDIAN_SPLIT)) != 0)
+        return RCB_ERR_ARG;
+    if ((params->flags & RCB_FLAG_CENTRE_OF_NUMBER) && (params->flags & RCB_FLAG_MEDIAN_SPLIT)) return RCB_ERR_ARG;
     if ((alloc == nullptr) != (release == nullptr)) return RCB_ERR_ARG;
     const int L = depth_rule(N, params->n_ll);
     if (L > kMaxL) return RCB_ERR_ARG;
@@ -304,7 +306,14 @@ int rcb_build(const double *x, const double *m, const double *h, int64_t N, cons
             if (rc == RCB_OK) rc = build_tree(t, x, t->ones, h);
             if (rc == RCB_OK) rc = refit_tree(t, x, m);
         } else {
-            rc = build_tree(t, x, m, h);
+            if ((params->flags & RCB_FLAG_MEDIAN_SPLIT) && !t->mps_hist) {
+                const int64_t cap_big = t->cap_N / (kTcta + 1) + 2;
+                t->mps_hist = (int32_t *)dev_alloc(t, (size_t)cap_big * 256 * sizeof(int32_t));
+                t->mps_prefix = (unsigned long long *)dev_alloc(t, (size_t)cap_big * sizeof(unsigned long long));
+                t->mps_rank = (int32_t *)dev_alloc(t, (size_t)cap_big * sizeof(int32_t));
+                if (!t->mps_hist || !t->mps_prefix || !t->mps_rank) rc = RCB_ERR_ALLOC;
+            }
+            if (rc == RCB_OK) rc = build_tree(t, x, m, h);
         }
     }
     if (rc == RCB_OK) rc = ensure_lists(t);

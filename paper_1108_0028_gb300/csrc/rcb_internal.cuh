@@ -276,6 +276,11 @@ struct rcb_tree {
     int32_t *tnear_off, *tnear_sink, *tfar_off, *tfar_sink;
     int bwd_valid;
     double *ones;     // unit weights for the centre-of-number split (cap_N)
+    // median position split: per large cell of a level, a 256-bin digit histogram, the key prefix
+    // chosen so far and the rank still sought (cap_N / (kTcta + 1) + 2 cells)
+    int32_t *mps_hist;
+    unsigned long long *mps_prefix;
+    int32_t *mps_rank;
     // neighbour candidates of a MAC-only tree: reachable leaves per sink (front of the rows)
     int32_t *cand_list, *cand_far, *cand_n;  // cand_n: [3][nleaves] counts (front, back, far)
     int cap_cand;

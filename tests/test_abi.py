@@ -48,6 +48,11 @@ def test_strerror_and_argument_checks_need_no_gpu(libpath):
     assert lib.rcb_build(one, one, one, 10, ctypes.byref(bad), None, None, None, None, ctypes.byref(h)) == -1
     assert lib.rcb_build(one, one, one, 0, ctypes.byref(p), None, None, None, None, ctypes.byref(h)) == -1
     assert lib.rcb_build(one, one, one, 1 << 31, ctypes.byref(p), None, None, None, None, ctypes.byref(h)) == -1
+    # unknown flag bits, and the two alternative splits together, are rejected
+    bad = rcb.rcb_params(12, 1, 0.5, 16, 0)
+    assert lib.rcb_build(one, one, one, 10, ctypes.byref(bad), None, None, None, None, ctypes.byref(h)) == -1
+    bad = rcb.rcb_params(12, 1, 0.5, rcb.RCB_FLAG_CENTRE_OF_NUMBER | rcb.RCB_FLAG_MEDIAN_SPLIT, 0)
+    assert lib.rcb_build(one, one, one, 10, ctypes.byref(bad), None, None, None, None, ctypes.byref(h)) == -1
     assert lib.rcb_gravity(None, None, None, None) == -1
     assert lib.rcb_set_precision(None, 0) == -1
     lib.rcb_free(None)
@@ -59,3 +64,11 @@ def test_binding_refuses_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(rcb, "_lib", None)
     with pytest.raises(RuntimeError):
         rcb.lib()
+
+
+def test_flag_values_match_the_header():
+    import paper_1108_0028_gb300 as rcb
+    src = open(os.path.join(ROOT, "include", "rcb.h")).read()
+    found = {k: int(v) for k, v in re.findall(r"#define (RCB_FLAG_[A-Z_]+) (\d+)u", src)}
+    assert found == {k: getattr(rcb, k) for k in found}
+    assert set(found) == {"RCB_FLAG_TIMING", "RCB_FLAG_CENTRE_OF_NUMBER", "RCB_FLAG_MAC_ONLY", "RCB_FLAG_MEDIAN_SPLIT"}
