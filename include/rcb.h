@@ -84,7 +84,8 @@ typedef struct rcb_tree rcb_tree;
 /*
  * rcb_build -- Sec. 2.1 tree build and Sec. 2.2-2.4.1 interaction lists.
  *   Splits the root cell level by level through each cell's centre of mass along its longest
- *   side (Sec. 2.1.3), partitioning each cell's particles in place (Sec. 2.1.4), down to level
+ *   side (Sec. 2.1.3; or through its centre of number, or at its median position, as the
+ *   RCB_FLAG_* split bits select), partitioning each cell's particles (Sec. 2.1.4), down to level
  *   L; computes per node mass, centre of mass, tight bounding box, geometric centre, size,
  *   traceless quadrupole (Eq. 1, shifted up by Eq. 2), h_node and h_node_int (Sec. 2.3.1);
  *   then walks the tree once per non-empty lowest-level cell (sink) from node 2 and stores its
@@ -98,8 +99,12 @@ typedef struct rcb_tree rcb_tree;
  *   tree    host, in/out: *tree == NULL builds a new tree; a tree from an earlier call is
  *           rebuilt in place, reusing its memory where the sizes allow.
  *   The inputs are copied; the caller may change or free them after the call returns.
+ *   The split variants allocate extra memory: N float64 unit weights for the centre-of-number
+ *   split; 1 KB of digit histograms per cell larger than 1024 particles (at most N / 1025 + 2
+ *   cells) for the median split.
  *   Synchronises `stream` (the list capacities are read back).  Errors: RCB_ERR_ARG (invalid
- *   input; *tree unchanged if it was NULL), RCB_ERR_ALLOC, RCB_ERR_CUDA, RCB_ERR_LIMIT.
+ *   input, an unknown flag bit or both split bits; *tree unchanged if it was NULL),
+ *   RCB_ERR_ALLOC, RCB_ERR_CUDA, RCB_ERR_LIMIT.
  */
 int rcb_build(const double *x, const double *m, const double *h, int64_t N, const rcb_params *params,
               rcb_alloc_fn alloc, rcb_free_fn release, void *ctx, void *stream, rcb_tree **tree);
