@@ -355,3 +355,19 @@ def test_median_split_tree_update_and_refit():
     x2 = synth.jitter(x, 3e-2, 81)
     expect = int(np.sum(_route_leaves(a.nodes(), a.L, x2) != a.leaf_of()))
     assert expect > 0 and a.update(x2, m, h) == expect
+
+
+def test_median_split_tree_gives_direct_sum_and_brute_neighbours():
+    # any partition must reproduce the direct sum at theta = 0 (Sec. 2.4.1) and the brute-force
+    # neighbour lists (Sec. 2.3): the median tree's moments, radii and lists cover every particle
+    N = 1500
+    x, m, h = synth.make_particles("plummer", N, 82, "loguniform10")
+    T = oracle.OracleTree(x, m, h, split="median")
+    T.walk(0.0)
+    acc, pot = T.gravity()
+    ad, pd = oracle.direct(x, m, h)
+    assert np.max(np.linalg.norm(acc - ad, axis=1) / np.linalg.norm(ad, axis=1)) < 1e-12
+    assert np.abs(pot - pd).max() < 1e-12 * np.abs(pd).max()
+    to, ti = T.neighbours()
+    bo, bi = oracle.brute_neighbours(x, h)
+    assert np.array_equal(to, bo) and np.array_equal(ti, bi)
