@@ -371,3 +371,110 @@ def test_median_split_tree_gives_direct_sum_and_brute_neighbours():
     to, ti = T.neighbours()
     bo, bi = oracle.brute_neighbours(x, h)
     assert np.array_equal(to, bo) and np.array_equal(ti, bi)
+
+
+def _fixed_exact(x, m):
+    """Fixed-point integers of the exact centre of mass, restated from the definition (p = RN(m x),
+    E with max|p| < 2^E, P = RN(p 2^(62 - E)), half to even) with Python's exact arithmetic."""
+    p = m[:, None] * x
+    E = [math.frexp(float(np.abs(p[:, d]).max()))[1] for d in range(3)]
+    Em = math.frexp(float(m.max()))[1]
+    P = np.empty((len(m), 4), dtype=object)
+    for i in range(len(m)):
+        P[i, 0] = round(Fraction(float(m[i])) * Fraction(2) ** (62 - Em))
+        for d in range(3):
+            P[i, 1 + d] = round(Fraction(float(p[i, d])) * Fraction(2) ** (62 - E[d]))
+    return P, E, Em
+
+
+def _check_nodes_against_particles(x, m, h, T):
+    """Every node of T against brute force over its own particle set (positions x, masses m and
+    smoothing lengths h in original order): exact integer sums, mass and centre of mass, the tight
+    box, r_g and H (Sec. 2.1.3, Eq. 4), the quadrupole of Eq. 1 summed directly, and the radii of
+    Sec. 2.3.1 (exact for ll-cells, enclosing for internal nodes)."""
+    nd, perm = T.nodes(), T.perm()
+    P, E, Em = _fixed_exact(x, m)
+    leaf0 = 1 << T.L
+    for n in range(1, 2 << T.L):
+        f, c = nd["first"][n], nd["count"][n]
+        if c == 0:
+            continue
+        idx = perm[f:f + c]
+        Ms = int(sum(P[idx, 0]))
+        assert _i128(nd["sums"][n, 0]) == Ms, n
+        M = math.ldexp(float(Ms), Em - 62)
+        assert nd["mass"][n] == M, n
+        for d in range(3):
+            S = int(sum(P[idx, 1 + d]))
+            assert _i128(nd["sums"][n, 1 + d]) == S, n
+            assert nd["com"][n, d] == math.ldexp(float(S), E[d] - 62) / M, n
+        pts = x[idx]
+        lo, hi = pts.min(0), pts.max(0)
+        assert np.array_equal(nd["bmin"][n], lo) and np.array_equal(nd["bmax"][n], hi), n
+        assert np.array_equal(nd["rg"][n], 0.5 * (lo + hi)), n
+        assert nd["H"][n] == (hi - lo).max(), n
+        d = pts - nd["com"][n]
+        d2 = np.einsum("ki,ki->k", d, d)
+        Qf = 3 * np.einsum("k,ki,kj->ij", m[idx], d, d) - np.eye(3) * np.sum(m[idx] * d2)
+        q6 = np.array([Qf[0, 0], Qf[0, 1], Qf[0, 2], Qf[1, 1], Qf[1, 2], Qf[2, 2]])
+        assert np.max(np.abs(nd["Q"][n] - q6)) <= 1e-11 * (np.sum(m[idx] * d2) + 1e-300), n
+        dv = pts - nd["rg"][n]
+        dist = np.sqrt((dv[:, 0] * dv[:, 0] + dv[:, 1] * dv[:, 1]) + dv[:, 2] * dv[:, 2])
+        if n >= leaf0:
+            assert nd["hint"][n] == dist.max(), n
+            assert nd["hnode"][n] == np.max(dist + 2.0 * h[idx]), n
+        else:
+            assert nd["hint"][n] >= dist.max() * (1 - 1e-15), n
+
+
+def test_node_check_holds_on_a_fresh_build(small_tree):
+    x, m, h, T = small_tree
+    _check_nodes_against_particles(x, m, h, T)
+
+
+def test_refit_recomputes_every_node_from_the_moved_particles():
+    # Sec. 2.1.8 refit with the structure frozen: positions moved far enough that every box,
+    # centre, radius and moment changes, masses changed; each node must equal brute force over
+    # its (unchanged) particle set at the new positions and masses, as on a fresh build
+    N = 2500
+    x, m, h = synth.make_particles("plummer", N, 83, "loguniform10")
+    T = oracle.OracleTree(x, m, h)
+    before = T.nodes()
+    x2 = synth.jitter(x, 1e-3, 84)
+    m2 = m * (1.0 + 0.5 * np.random.default_rng(85).random(N))
+    T.refit(x2, m2)
+    after = T.nodes()
+    for k in ("bmin", "bmax", "rg", "H", "hint", "hnode", "com", "Q", "mass"):
+        assert not np.array_equal(before[k], after[k]), k   # a stale field would pass unnoticed
+    assert np.array_equal(before["split"], after["split"]) and np.array_equal(before["count"], after["count"])
+    _check_nodes_against_particles(x2, m2, h, T)
+
+
+def test_update_inside_recomputes_every_node_and_walks_to_exact_results():
+    # Sec. 2.1.8 update with every particle still inside its ll-cell: new positions, masses and
+    # smoothing lengths; every node equals brute force at the new state, and the tree walked again
+    # gives the brute-force neighbour lists (Sec. 2.3) and, at theta = 0, the direct sum (Sec. 2.4.1)
+    N = 2500
+    x, m, h = synth.make_particles("sphere", N, 86, "loguniform10")
+    T = oracle.OracleTree(x, m, h)
+    x2 = synth.jitter(x, 1e-9, 87)
+    m2 = m * (1.0 + 0.3 * np.random.default_rng(88).random(N))
+    h2 = h * (1.0 + 0.2 * np.random.default_rng(89).random(N))
+    before = T.nodes()
+    assert T.update(x2, m2, h2) == 0
+    after = T.nodes()
+    for k in ("bmin", "bmax", "hint", "hnode", "com", "Q"):
+        assert not np.array_equal(before[k], after[k]), k
+    _check_nodes_against_particles(x2, m2, h2, T)
+    T.walk(0.0)
+    to, ti = T.neighbours()
+    bo, bi = oracle.brute_neighbours(x2, h2)
+    assert np.array_equal(to, bo) and np.array_equal(ti, bi)
+    acc, pot = T.gravity()
+    ad, pd = oracle.direct(x2, m2, h2)
+    assert np.max(np.linalg.norm(acc - ad, axis=1) / np.linalg.norm(ad, axis=1)) < 1e-12
+    assert np.abs(pot - pd).max() < 1e-12 * np.abs(pd).max()
+    # and at theta = 0.7 the neighbour lists still equal brute force
+    T.walk(0.7)
+    to, ti = T.neighbours()
+    assert np.array_equal(to, bo) and np.array_equal(ti, bi)
