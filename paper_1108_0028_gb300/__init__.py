@@ -377,3 +377,33 @@ def rcb_gravity_fn(x, m, h, n_ll: int = 12, theta: float = 0.7, precision="mixed
     if _gravity_fn is None:
         _gravity_fn = _make_gravity_fn()
     return _gravity_fn.apply(x, m, h, n_ll, theta, precision)
+
+
+def alu_rates(sms: int, iters: int = 4096) -> dict:
+    """Measured arithmetic rates of the current GPU from the probe library ``libpeak.so``
+    (``peak/alu_rate.cu``): FP32 FMA, paired FP32 FMA, MUFU reciprocal square root (tera-operations
+    per second, FMA = 2 flops) and FP64 FMA.  Best of three runs of each probe on ``sms`` x 4
+    blocks of 256 threads.  A diagnostic of the benchmark; it changes no device setting."""
+    import torch
+
+    path = os.path.join(_HERE, "libpeak.so")
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1108_0028_gb300.build()")
+    L = ctypes.CDLL(path)
+    L.alu_rate_run.restype = ctypes.c_double
+    L.alu_rate_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.POINTER(ctypes.c_double)]
+    blocks, threads = 4 * sms, 256
+    out = torch.empty(blocks * threads, dtype=torch.float32, device="cuda")
+    res = {}
+    for which, name, it in ((0, "ffma_tflops", iters), (1, "ffma2_tflops", iters), (2, "rsqrt_tops", iters // 4),
+                            (3, "dfma_tflops", max(1, iters // 64))):
+        best = 0.0
+        for _ in range(4):   # the first run is a warm-up
+            ops = ctypes.c_double(0.0)
+            ms = L.alu_rate_run(which, blocks, threads, it, ctypes.c_void_p(out.data_ptr()), ctypes.byref(ops))
+            if ms <= 0:
+                raise RuntimeError("ALU rate probe failed")
+            best = max(best, ops.value / (ms * 1e-3) / 1e12)
+        res[name] = round(best, 3)
+    return res

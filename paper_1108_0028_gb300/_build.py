@@ -15,6 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librcb.so")
+PEAK_SRC = os.path.join(HERE, "peak", "alu_rate.cu")
+PEAK_LIB = os.path.join(HERE, "libpeak.so")  # arithmetic-rate probe of the benchmark (not part of the C ABI)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 # float32-heavy kernels: flush subnormals and use the hardware reciprocal / square-root
@@ -65,6 +67,12 @@ def build(verbose: bool = False, force: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(LIB + ".tmp", LIB)
+    if force or not os.path.exists(PEAK_LIB) or os.path.getmtime(PEAK_LIB) < os.path.getmtime(PEAK_SRC):
+        cmd = [nvcc] + ARCH + ["-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "-o", PEAK_LIB + ".tmp", PEAK_SRC]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {PEAK_SRC}:\n{r.stderr}")
+        os.replace(PEAK_LIB + ".tmp", PEAK_LIB)
     return LIB
 
 

@@ -57,11 +57,8 @@ struct GCtx {
     double *coef;
     float *coef32;
     double *acc, *pot;
-    // neighbour search fused into the mixed near field
+    // neighbour counts fused into the mixed near field
     int64_t *nb_counts;  // [N] by original index
-    int32_t *nb_rows;    // [N][kNbRowCap] by sorted index
-    int2 *nb_long;
-    int cap_long;
     int *status;
 };
 
@@ -229,67 +226,73 @@ __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_
     return staged;
 }
 
+// ------------------------------------------------------------------------------ mixed near field
+// One warp per sink.  The sources (the particles of the sink's near cells) are staged once per
+// tile in shared memory; the warp's lanes then take (sink particle i, source stream j) pairs:
+// with P sink particles in the pass, S = 32 / P streams, lane l holds particle i = l mod P and
+// walks the source pairs k = j, j + S, ... (j = l / P).  Every lane evaluates two sources at once
+// with paired float32 instructions (each half rounds as the scalar operation would) and keeps
+// its own totals, so nothing crosses lanes until the sink is finished.  Sources are stored by
+// pairs and negated, (-x_2k, -x_2k+1, -y_2k, -y_2k+1), (-z.., -m..), (h.., sorted index..), so
+// that every paired operand arrives from one shared-memory load.
+constexpr int kNearWarps = 8;   // warps per block
+constexpr int kNearMinBlocks = 2;
+constexpr int kNearTile = 256;  // staged source slots per warp (even)
+constexpr int kNearPad = 4;     // slots kept free for padding the regions to even length
+constexpr int kFoldIters = 16;  // source pairs summed in float32 before a compensated fold
 
-constexpr int kNearWarps = 8;     // warps per block of the mixed near kernel
-constexpr int kNearTile = 512;    // staged sources per warp
-constexpr int kNbChunks = kNearTile / 32;  // 32-source chunks of a tile
-constexpr int kSuper = 3;                   // groups of sink particles sharing one staged tile
-
-// Shared memory of one warp of the mixed near kernel.  With the neighbour search (NB) it also
-// holds each source's sorted index (bitwise complement for sources of non-candidate cells) and
-// each sink particle's float32 neighbour band.
-template <bool NB>
+// Shared memory of one warp: per source pair k, A[k], B[k], C[k] (see above), and the slot of
+// each sink particle of the pass in the current tile (-1 if not staged there).
 struct NearSmem {
-    static constexpr size_t bytes =
-        kNearTile * (sizeof(float4) + sizeof(float)) + 2 * kGroupMixed * sizeof(float4) +
-        kSuper * 32 * sizeof(float2) + (NB ? kSuper * kGroupMixed * sizeof(int) : 0) +
-        (NB ? kNearTile * sizeof(int32_t) + kGroupMixed * sizeof(float2) + kGroupMixed * sizeof(float2) +
-                  kNbChunks * kGroupMixed * sizeof(unsigned)
-            : 0);
-    float4 *src;    // (d_b relative to the sink's centre of mass, m_b)
-    float *hs;      // h_b
-    float4 *snk;    // (d_a, h_a) of the current group
-    float4 *snk2;   // the same by pairs (i, i + 1): (x_i, x_i+1, y_i, y_i+1), (z_i, z_i+1, h_i, h_i+1)
-    float2 *hi2;    // NB: upper band edges by pairs
-    float2 *lo2;    // NB: lower band edges by pairs
-    int32_t *sidx;  // NB
-    float2 *band;   // NB: per sink particle (2h)^2 -+ B
-    unsigned *mamb; // NB: [chunk][sink particle] sources inside the band (float64 decides)
-    float2 *gacc;   // [group][lane] the lanes' compensated totals of the groups sharing a tile
-    int *grun;      // NB: [group][sink particle] neighbours found so far
+    static constexpr size_t bytes = (size_t)(kNearTile / 2) * 3 * sizeof(float4) + 32 * sizeof(int);
+    float4 *A, *B, *C;
+    int *self;
     __device__ NearSmem(unsigned char *p) {
-        src = reinterpret_cast<float4 *>(p);
-        hs = reinterpret_cast<float *>(src + kNearTile);
-        snk = reinterpret_cast<float4 *>(hs + kNearTile);
-        snk2 = snk + kGroupMixed;
-        band = reinterpret_cast<float2 *>(snk2 + kGroupMixed);
-        hi2 = band + (NB ? kGroupMixed : 0);
-        lo2 = hi2 + (NB ? kGroupMixed / 2 : 0);
-        sidx = reinterpret_cast<int32_t *>(lo2 + (NB ? kGroupMixed / 2 : 0));
-        mamb = reinterpret_cast<unsigned *>(sidx + (NB ? kNearTile : 0));
-        gacc = reinterpret_cast<float2 *>(mamb + (NB ? kNbChunks * kGroupMixed : 0));
-        grun = reinterpret_cast<int *>(gacc + kSuper * 32);
+        A = reinterpret_cast<float4 *>(p);
+        B = A + kNearTile / 2;
+        C = B + kNearTile / 2;
+        self = reinterpret_cast<int *>(C + kNearTile / 2);
+    }
+    // store source slot s: offset d (from the sink's centre of mass), mass, h, sorted index
+    __device__ __forceinline__ void put(int s, float dx, float dy, float dz, float m, float h, int idx) const {
+        float *a = reinterpret_cast<float *>(A + (s >> 1)), *b = reinterpret_cast<float *>(B + (s >> 1));
+        float *cc = reinterpret_cast<float *>(C + (s >> 1));
+        const int u = s & 1;
+        a[u] = -dx;
+        a[2 + u] = -dy;
+        b[u] = -dz;
+        b[2 + u] = -m;
+        cc[u] = h;
+        cc[2 + u] = __int_as_float(idx);
     }
 };
 
-// Staged tile: the close sources at [0, nclose) of src/hs (and sidx), the far ones at
-// [kNearTile - nfar, kNearTile) (see below).
-struct NearTile {
-    int nclose, nfar;
-    int64_t S;  // all sources of the sink
+// Where the next tile starts: position t0 of the concatenated source sequence (cells in list
+// order: the reachable ones, then the others) lies in the batch of up to 32 near cells that
+// begins at list entry k0, whose first particle is at position pos.
+struct NearCursor {
+    int k0;
+    int64_t pos, t0;
 };
 
-// Stage sources [t0, t0 + kNearTile) of the sink's near cells.  For 32 cells at a time, lanes
-// first describe the cells (first particle, count, centre-of-mass offset), then take one slot
-// each (two slot chunks per round, so both gathers are in flight together), find the slot's
-// cell, form the particle's float32 offset from the sink's centre of mass and store it with
-// its mass and h, close sources from the front of the tile and far ones from the back.  The
+// One staged tile: close sources in slots [0, nclose), of which [0, ncc) come from neighbour
+// candidates (reachable cells), far sources in [kNearTile - nfar, kNearTile); all three counts
+// are even (padding slots hold a massless source far away).
+struct NearTile {
+    int nclose, ncc, nfar;
+    bool last;  // no sources beyond this tile
+};
+
+// Stage the next tile of sink s (cell A, sorted particles [fA, fA + nA), this pass the P
+// particles from a0).  For 32 cells at a time lanes describe the cells (first particle, count,
+// centre-of-mass offset); then every lane takes two slots per round (both gathers in flight
+// together), finds the slot's cell, forms the particle's float32 offset from the sink's centre of
+// mass and stores it, close sources from the front of the tile and far ones from the back.  The
 // cell offset o is the double-float difference of the two centres of mass: it differs from the
 // float64 difference by at most 2u |dCOM| + 3 2^-48 (|COM_A|_1 + |COM_B|_1) per component
-// (u = 2^-24; the second term is the double-float representation).  With NB the sorted index is
-// kept (bitwise complement for sources of non-candidate cells) and wmax gets the tile's largest
-// w = |o|_1 + |d_b|_1 + 2^-20 (|COM_A|_1 + |COM_B|_1): the last term makes the representation
-// error's share of the d^2 error at most 6 2^-28 F, well inside the neighbour band.
+// (u = 2^-24).  With NB, wmax gets the tile's largest w = |o|_1 + |d_b|_1 + 2^-20 (|COM_A|_1 +
+// |COM_B|_1) over candidate sources: the last term makes the representation error's share of
+// the d^2 error at most 6 2^-28 F, well inside the neighbour band.
 //
 // Far sources: with R_A the largest |d_a| and H_A the largest h_a of the sink's particles, a
 // source b with |d_b| > (R_A + X_b)(1 + 2^-10) has r_ab >= |d_b| - |d_a| > X_b for every sink
@@ -298,40 +301,42 @@ struct NearTile {
 // sphere (r < 2 h_a).  The 2^-10 margin is far above the float32 rounding of the test, of q and
 // of the neighbour filter.
 template <bool NB>
-__device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int nr, int64_t t0, const NearSmem<NB> &sm,
-                                     float RA, float HA, float &wmax) {
+__device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0, int P, int nlist, int nr,
+                                     NearCursor &cur, const NearSmem &sm, float RA, float HA, float &wmax) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)s * c.cap_near;
-    const float2 a0 = c.ncomdf[3 * (int64_t)A], a1 = c.ncomdf[3 * (int64_t)A + 1], a2 = c.ncomdf[3 * (int64_t)A + 2];
-    const float aabs = fabsf(a0.x) + fabsf(a1.x) + fabsf(a2.x);
-    int64_t pos = 0;
+    const float2 a0f = c.ncomdf[3 * (int64_t)A], a1f = c.ncomdf[3 * (int64_t)A + 1], a2f = c.ncomdf[3 * (int64_t)A + 2];
+    const float aabs = fabsf(a0f.x) + fabsf(a1f.x) + fabsf(a2f.x);
+    const int64_t t0 = cur.t0;
+    const int64_t tend = t0 + (kNearTile - kNearPad);
+    sm.self[lane] = -1;
+    __syncwarp();
     float wl = 0.f;
-    int nclose = 0, nfar = 0;
-    for (int k0 = 0; k0 < nlist; k0 += 32) {
-        const int k = k0 + lane;
+    int nclose = 0, nfar = 0, ncc = -1;
+    bool full = false;
+    while (cur.k0 < nlist) {
+        const int kend = cur.k0 < nr ? nr : nlist;  // the batch stays within one of the two parts
+        const int k = cur.k0 + lane;
         int f = 0, n = 0;
         float ox = 0.f, oy = 0.f, oz = 0.f, ow = 0.f;
-        const bool inside = pos < t0 + kNearTile;  // cells beyond the tile are only counted
-        if (k < nlist) {
-            const int B = near_entry(c, base, nr, k);
-            n = c.ncount[B];
-        }
-        if (k < nlist && inside) {
+        if (k < kend) {
             const int B = near_entry(c, base, nr, k);
             f = c.nfirst[B];
+            n = c.ncount[B];
             const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1],
                          b2 = c.ncomdf[3 * (int64_t)B + 2];
-            ox = (b0.x - a0.x) + (b0.y - a0.y);
-            oy = (b1.x - a1.x) + (b1.y - a1.y);
-            oz = (b2.x - a2.x) + (b2.y - a2.y);
+            ox = (b0.x - a0f.x) + (b0.y - a0f.y);
+            oy = (b1.x - a1f.x) + (b1.y - a1f.y);
+            oz = (b2.x - a2f.x) + (b2.y - a2f.y);
             if (NB) ow = 0x1p-20f * (aabs + (fabsf(b0.x) + fabsf(b1.x) + fabsf(b2.x)));
         }
+        const bool cand = cur.k0 < nr;
         const int excl = warp_excl_scan(n);
         const int total = __shfl_sync(0xffffffffu, excl + n, 31);
-        const int64_t lo = pos > t0 ? pos : t0;
-        const int64_t hi = pos + total < t0 + kNearTile ? pos + total : t0 + kNearTile;
-        for (int64_t j0 = lo; j0 < hi; j0 += 64) {
+        const int64_t pos = cur.pos;
+        const int64_t hi = pos + total < tend ? pos + total : tend;
+        for (int64_t j0 = pos > t0 ? pos : t0; j0 < hi; j0 += 64) {
             int b[2], cl[2];
             float cx[2], cy[2], cz[2], cw[2];
             bool act[2];
@@ -359,8 +364,8 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
             }
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const float4 v = make_float4(cx[u] + pb[u].x, cy[u] + pb[u].y, cz[u] + pb[u].z, pb[u].w);
-                const float d2 = fmaf(v.z, v.z, fmaf(v.y, v.y, v.x * v.x));
+                const float vx = cx[u] + pb[u].x, vy = cy[u] + pb[u].y, vz = cz[u] + pb[u].z;
+                const float d2 = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
                 const float X = NB ? fmaxf(HA + hb[u], HA + HA) : HA + hb[u];
                 const float R = (RA + X) * (1.0f + 0x1p-10f);
                 const bool far = d2 > R * R;
@@ -368,232 +373,232 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int nlist, int
                 const unsigned mf = __ballot_sync(0xffffffffu, act[u] && far);
                 if (act[u]) {
                     const int at = far ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt);
-                    sm.src[at] = v;
-                    sm.hs[at] = hb[u];
+                    sm.put(at, vx, vy, vz, pb[u].w, hb[u], b[u]);
                     if (NB) {
-                        sm.sidx[at] = k0 + cl[u] < nr ? b[u] : ~b[u];
-                        wl = fmaxf(wl, (fabsf(cx[u]) + fabsf(cy[u]) + fabsf(cz[u])) + fabsf(pb[u].x) + fabsf(pb[u].y) +
-                                           fabsf(pb[u].z) + cw[u]);
+                        if (cand)
+                            wl = fmaxf(wl, (fabsf(cx[u]) + fabsf(cy[u]) + fabsf(cz[u])) + fabsf(pb[u].x) +
+                                               fabsf(pb[u].y) + fabsf(pb[u].z) + cw[u]);
+                        const int i = b[u] - fA - a0;  // a sink particle of this pass?
+                        if (i >= 0 && i < P) sm.self[i] = at;
                     }
                 }
                 nclose += __popc(mc);
                 nfar += __popc(mf);
             }
         }
-        pos += total;
+        if (pos + total > tend) {  // the tile is full: the next one continues inside this batch
+            full = true;
+            cur.t0 = tend;
+            break;
+        }
+        cur.pos = pos + total;
+        cur.k0 = min(cur.k0 + 32, kend);
+        if (cur.k0 == nr && ncc < 0) {  // all candidates staged: pad the candidate part to even
+            if (nclose & 1) {
+                if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1);
+                ++nclose;
+            }
+            ncc = nclose;
+        }
+    }
+    if (!full) cur.t0 = cur.pos;
+    if (ncc < 0) ncc = cur.k0 < nr ? nclose : 0;
+    if (ncc & 1) {  // the tile ended inside the candidates
+        if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1);
+        ++nclose;
+        ++ncc;
+    }
+    if (nclose & 1) {
+        if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1);
+        ++nclose;
+    }
+    if (nfar & 1) {
+        if (lane == 0) sm.put(kNearTile - 1 - nfar, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1);
+        ++nfar;
     }
     if (NB) {
         for (int o = 16; o >= 1; o >>= 1) wl = fmaxf(wl, __shfl_xor_sync(0xffffffffu, wl, o));
         wmax = wl;
     }
     __syncwarp();
-    return NearTile{nclose, nfar, pos};
+    return NearTile{nclose, ncc, nfar, !full};
 }
 
-// Neighbour-search state of one group of sink particles.
-struct NbGroup {
-    int a0;                 // sorted index of the group's first sink particle
-    int run[kGroupMixed];   // neighbours of sink particle i found so far (the same in every lane)
-    int nfb;                // float64 decisions taken (per lane)
+// Lane state of the mixed near field: the lane's sink particle (float32 offset from the sink's
+// centre of mass and h, each twice), its neighbour band, and its sums.  In[q] collects quantity q
+// (a_x, a_y, a_z, phi) over two sources at a time; (sum, comp) is the compensated total.
+struct NearLane {
+    float2 xa, ya, za, ha;
+    float h2, B;   // (2 h_a)^2 and the half width of the neighbour band
+    float2 In[4];
+    float sum[4], comp[4];
+    int cnt;  // neighbours counted
+    int nfb;  // float64 neighbour decisions taken
 };
 
-// Append the sources of mask m (bits = lanes of chunk k) to sink particle i's row: the lanes
-// whose bit is set write consecutive slots.  The order inside a row is free (the compaction
-// sorts each row).
-__device__ __forceinline__ void nb_append(const GCtx &c, int a, int &run, unsigned m, int sb) {
-    const int lane = threadIdx.x & 31;
-    if ((m >> lane) & 1u) {
-        const int p = run + __popc(m & ((1u << lane) - 1u));
-        if (p < kNbRowCap) c.nb_rows[(int64_t)a * kNbRowCap + p] = sb;
-    }
-    run += __popc(m);
-}
-
-// Sources inside a sink particle's float32 band (mamb, recorded by the close loop per chunk and
-// sink particle) are settled by the float64 test, every lane of the chunk at once, and appended.
-template <int G>
-__device__ inline void settle_band(const GCtx &c, const NearSmem<true> &sm, int nchunks, int na, NbGroup &g) {
-    const int lane = threadIdx.x & 31;
-    for (int e0 = 0; e0 < nchunks * G; e0 += 32) {
-        const int e = e0 + lane;
-        unsigned todo = __ballot_sync(0xffffffffu, e < nchunks * G && (e % G) < na && sm.mamb[e] != 0u);
-        while (todo) {
-            const int ee = e0 + __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int k = ee / G, i = ee % G;
-            const unsigned amb = sm.mamb[ee];
-            const int a = g.a0 + i;
-            const int sb = sm.sidx[32 * k + lane];
-            bool nb = false;
-            if (((amb >> lane) & 1u) && sb != a) {
-                const double s2 = __dmul_rn(2.0, c.ph[a]);
-                nb = dist2_rn(c.px[a], c.py[a], c.pz[a], c.px[sb], c.py[sb], c.pz[sb]) < __dmul_rn(s2, s2);
-                ++g.nfb;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, nb);
+__device__ __forceinline__ void near_fold(NearLane &L) {
 #pragma unroll
-            for (int q = 0; q < G; ++q)
-                if (q == i) nb_append(c, a, g.run[q], m, sb);
-        }
+    for (int q = 0; q < 4; ++q) {
+        comp_add(L.sum[q], L.comp[q], __fadd_rn(L.In[q].x, L.In[q].y));
+        L.In[q] = make_float2(0.f, 0.f);
     }
 }
 
-// The pair loops of one staged tile for G sink particles (snk[0, G)), folded into the lane's
-// compensated total (rs, rc) of value (lane mod 4 G) = 4 i + q.  With NB the close loop also
-// tests every candidate pair (a, b) for |r_a - r_b| < 2 h_a (float32 d^2 against the band of
-// sink particle i, one ballot per band edge) and records the masks from which emit_neighbours
-// settles the in-band pairs in float64 and appends b's sorted index to a's row of slots.
-template <int G, bool NB>
-__device__ inline void near_tile(const GCtx &c, const NearSmem<NB> &sm, const NearTile &tl, int na, float &rs,
-                                 float &rc, NbGroup &g) {
-    const int nclose = tl.nclose;
-    const int npair = (na + 1) >> 1;  // sink particle pairs holding a real particle (warp-uniform)
-    static_assert(G % 2 == 0, "sink particles go by pairs");
-    const int lane = threadIdx.x & 31;
-    // In[q][p]: quantity q (a_x, a_y, a_z, phi) of sink particles 2p and 2p + 1.  Every pair
-    // term below is computed for two sink particles at once with paired float32 instructions
-    // (each half rounds exactly as the scalar operation would).
-    float2 In[4][G / 2];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < G / 2; ++p) In[q][p] = make_float2(0.f, 0.f);
-    // far sources: every pair outside its kernel support, Newtonian only
-    for (int q0 = kNearTile - tl.nfar; q0 < kNearTile; q0 += 32) {
-        const int j = q0 + lane;
-        // padding lanes: a massless source far away (finite r, zero contribution)
-        const float4 b = j < kNearTile ? sm.src[j] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-        const float2 nbx = make_float2(-b.x, -b.x), nby = make_float2(-b.y, -b.y), nbz = make_float2(-b.z, -b.z);
-        const float2 nbm = make_float2(-b.w, -b.w);
-#pragma unroll
-        for (int p = 0; p < G / 2; ++p) {
-            if (p > 0 && p >= npair) break;  // padding pairs of a short group
-            const float4 sxy = sm.snk2[2 * p], szh = sm.snk2[2 * p + 1];
-            const float2 dx = __fadd2_rn(make_float2(sxy.x, sxy.y), nbx);
-            const float2 dy = __fadd2_rn(make_float2(sxy.z, sxy.w), nby);
-            const float2 dz = __fadd2_rn(make_float2(szh.x, szh.y), nbz);
-            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            const float2 rinv = make_float2(rsqrtf(fmaxf(r2.x, 1e-30f)), rsqrtf(fmaxf(r2.y, 1e-30f)));
-            const float2 nw = __fmul2_rn(nbm, __fmul2_rn(__fmul2_rn(rinv, rinv), rinv));  // -m_b / r^3
-            In[0][p] = __ffma2_rn(nw, dx, In[0][p]);
-            In[1][p] = __ffma2_rn(nw, dy, In[1][p]);
-            In[2][p] = __ffma2_rn(nw, dz, In[2][p]);
-            In[3][p] = __ffma2_rn(nbm, rinv, In[3][p]);
-        }
-    }
-    // close sources: the full kernel-softened pair
-    const float2 k05 = make_float2(0.5f, 0.5f), km12 = make_float2(-1.2f, -1.2f), k43 = make_float2(4.0f / 3.0f, 4.0f / 3.0f);
-    const float2 k01 = make_float2(0.1f, 0.1f), km03 = make_float2(-0.3f, -0.3f), k23 = make_float2(2.0f / 3.0f, 2.0f / 3.0f);
-    const float2 km14 = make_float2(-1.4f, -1.4f), km16 = make_float2(-1.0f / 6.0f, -1.0f / 6.0f);
-    const float2 k12 = make_float2(1.2f, 1.2f), km3 = make_float2(-3.0f, -3.0f), k83 = make_float2(8.0f / 3.0f, 8.0f / 3.0f);
-    const float2 km115 = make_float2(-1.0f / 15.0f, -1.0f / 15.0f), km130 = make_float2(-1.0f / 30.0f, -1.0f / 30.0f);
-    const float2 k03 = make_float2(0.3f, 0.3f), km1 = make_float2(-1.0f, -1.0f), km16b = make_float2(-1.6f, -1.6f);
-    const float2 k115 = make_float2(1.0f / 15.0f, 1.0f / 15.0f);
-    for (int q0 = 0; q0 < nclose; q0 += 32) {
-        const int j = q0 + lane;
-        float4 b = make_float4(1e18f, 1e18f, 1e18f, 0.f);
-        float hb = 1.f;
-        int sb = -1;
-        if (j < nclose) {
-            b = sm.src[j];
-            hb = sm.hs[j];
-            if (NB) sb = sm.sidx[j];
-        }
-        const unsigned cand = NB ? __ballot_sync(0xffffffffu, sb >= 0) : 0u;  // candidate-cell sources
-        const int kc = q0 >> 5;                                                  // chunk of the tile
-        const bool own = NB && __any_sync(0xffffffffu, sb >= g.a0 && sb < g.a0 + G);  // holds group particles
-        const float2 nbx = make_float2(-b.x, -b.x), nby = make_float2(-b.y, -b.y), nbz = make_float2(-b.z, -b.z);
-        const float2 bm = make_float2(b.w, b.w), nbm = make_float2(-b.w, -b.w), hb2 = make_float2(hb, hb);
-#pragma unroll
-        for (int p = 0; p < G / 2; ++p) {
-            if (p > 0 && p >= npair) break;  // padding pairs of a short group
-            // sink particles 2p and 2p + 1 against this lane's source (the self pair has r = 0:
-            // zero force; its potential m_a phi(0) is removed in the epilogue)
-            const float4 sxy = sm.snk2[2 * p], szh = sm.snk2[2 * p + 1];
-            const float2 dx = __fadd2_rn(make_float2(sxy.x, sxy.y), nbx);
-            const float2 dy = __fadd2_rn(make_float2(sxy.z, sxy.w), nby);
-            const float2 dz = __fadd2_rn(make_float2(szh.x, szh.y), nbz);
-            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            const float2 rinv = make_float2(rsqrtf(fmaxf(r2.x, 1e-30f)), rsqrtf(fmaxf(r2.y, 1e-30f)));
-            const float2 r = __fmul2_rn(r2, rinv);
-            const float2 hsum = __fadd2_rn(make_float2(szh.z, szh.w), hb2);
-            const float2 hinv = make_float2(__fdividef(2.0f, hsum.x), __fdividef(2.0f, hsum.y));
-            const float2 q = __fmul2_rn(r, hinv);
-            const float2 q2 = __fmul2_rn(q, q);
-            const float2 rinv3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
-            // Eq. 10 as S/r and its potential: q < 1, 1 <= q < 2, q >= 2
-            const float2 h3 = __fmul2_rn(__fmul2_rn(hinv, hinv), hinv);
-            const float2 s1 = __fmul2_rn(h3, __ffma2_rn(q2, __ffma2_rn(k05, q, km12), k43));
-            const float2 p1 = __fmul2_rn(hinv, __ffma2_rn(q2, __ffma2_rn(q2, __ffma2_rn(k01, q, km03), k23), km14));
-            const float2 s2v = __ffma2_rn(h3, __ffma2_rn(q, __ffma2_rn(q, __ffma2_rn(km16, q, k12), km3), k83),
-                                          __fmul2_rn(km115, rinv3));
-            const float2 p2v =
-                __ffma2_rn(hinv, __ffma2_rn(q2, __ffma2_rn(q, __ffma2_rn(q, __ffma2_rn(km130, q, k03), km1), k43), km16b),
-                           __fmul2_rn(k115, rinv));
-            const float2 sr = make_float2(q.x < 1.0f ? s1.x : (q.x < 2.0f ? s2v.x : rinv3.x),
-                                          q.y < 1.0f ? s1.y : (q.y < 2.0f ? s2v.y : rinv3.y));
-            const float2 ph = make_float2(q.x < 1.0f ? p1.x : (q.x < 2.0f ? p2v.x : -rinv.x),
-                                          q.y < 1.0f ? p1.y : (q.y < 2.0f ? p2v.y : -rinv.y));
-            const float2 nw = __fmul2_rn(nbm, sr);
-            In[0][p] = __ffma2_rn(nw, dx, In[0][p]);
-            In[1][p] = __ffma2_rn(nw, dy, In[1][p]);
-            In[2][p] = __ffma2_rn(nw, dz, In[2][p]);
-            In[3][p] = __ffma2_rn(bm, ph, In[3][p]);
-            if (NB) {
-                // neighbour test of sink particles 2p and 2p + 1 against this chunk: sources below
-                // the band are appended now, those inside it are recorded for settle_band; a
-                // particle is not its own neighbour
-                const float2 hi = sm.hi2[p], lo = sm.lo2[p];
-                unsigned l0 = __ballot_sync(0xffffffffu, r2.x < lo.x) & cand;
-                const unsigned h0 = __ballot_sync(0xffffffffu, r2.x <= hi.x) & cand;
-                unsigned l1 = __ballot_sync(0xffffffffu, r2.y < lo.y) & cand;
-                const unsigned h1 = __ballot_sync(0xffffffffu, r2.y <= hi.y) & cand;
-                if (lane == 0) {
-                    sm.mamb[kc * G + 2 * p] = h0 & ~l0;
-                    sm.mamb[kc * G + 2 * p + 1] = h1 & ~l1;
-                }
-                if (own) {
-                    l0 &= ~__ballot_sync(0xffffffffu, sb == g.a0 + 2 * p);
-                    l1 &= ~__ballot_sync(0xffffffffu, sb == g.a0 + 2 * p + 1);
-                }
-                nb_append(c, g.a0 + 2 * p, g.run[2 * p], l0, sb);
-                nb_append(c, g.a0 + 2 * p + 1, g.run[2 * p + 1], l1, sb);
-            }
-        }
-    }
-    if constexpr (NB) {
-        __syncwarp();
-        settle_band<G>(c, sm, (nclose + 31) >> 5, na, g);
-    }
-    // fold this tile: compensated reduce-scatter across lanes, then into (rs, rc)
-    float Vs[4 * G], Vc[4 * G];
-#pragma unroll
-    for (int i = 0; i < G; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            Vs[4 * i + q] = (i & 1) ? In[q][i / 2].y : In[q][i / 2].x;
-            Vc[4 * i + q] = 0.f;
-        }
-    reduce_scatter_df<4 * G>(Vs, Vc);
-    float t, e;
-    two_sum(rs, Vs[0], t, e);
-    rs = t;
-    rc = __fadd_rn(__fadd_rn(rc, Vc[0]), e);
+__device__ __forceinline__ float2 near_r2(const NearLane &L, const float4 a, const float4 b, float2 &dx, float2 &dy,
+                                         float2 &dz) {
+    dx = __fadd2_rn(L.xa, make_float2(a.x, a.y));
+    dy = __fadd2_rn(L.ya, make_float2(a.z, a.w));
+    dz = __fadd2_rn(L.za, make_float2(b.x, b.y));
+    return __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
 }
 
-// Mixed near field; with NB also the neighbour search of Sec. 2.3 on the same staged sources
-// (counts to nb_counts by original index, rows of kNbRowCap slots to nb_rows, longer rows
-// queued).  The float32 neighbour filter compares d^2 with (2h)^2 -+ B,
-// B = 2^-19 ((W + |d_a|_1)^2 + (2h)^2) + 1e-30, W the tile's largest w (see stage_near_mixed):
-// the input and offset roundings, the squares and sums and the roundings of (2h)^2 -+ B stay
-// below 16 u F, half of B; inside the band the float64 test (the definition) decides.
+// Far sources: every pair outside the kernel support, Newtonian only (r > 0 always).
+__device__ __forceinline__ void near_pair_newton(NearLane &L, const float4 a, const float4 b) {
+    float2 dx, dy, dz;
+    const float2 r2 = near_r2(L, a, b, dx, dy, dz);
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 nm = make_float2(b.z, b.w);                                      // -m_b
+    const float2 nw = __fmul2_rn(nm, __fmul2_rn(__fmul2_rn(rinv, rinv), rinv));  // -m_b / r^3
+    L.In[0] = __ffma2_rn(nw, dx, L.In[0]);
+    L.In[1] = __ffma2_rn(nw, dy, L.In[1]);
+    L.In[2] = __ffma2_rn(nw, dz, L.In[2]);
+    L.In[3] = __ffma2_rn(nm, rinv, L.In[3]);  // m_b phi, phi = -1/r
+}
+
+// Close sources: the full kernel-softened pair of Eq. 10 with its potential (branch-free, the
+// branch of each half selected by its q); -phi is evaluated, so that the stored -m_b multiplies
+// it.  Returns r^2 of both pairs.  The pair of a particle with itself has r = 0: zero force,
+// potential m_a phi(0) (removed in the epilogue).
+__device__ __forceinline__ float2 near_pair_close(NearLane &L, const float4 a, const float4 b, const float4 cc) {
+    float2 dx, dy, dz;
+    const float2 r2 = near_r2(L, a, b, dx, dy, dz);
+    const float2 rinv = make_float2(rsqrtf(fmaxf(r2.x, 1e-30f)), rsqrtf(fmaxf(r2.y, 1e-30f)));
+    const float2 r = __fmul2_rn(r2, rinv);
+    const float2 hsum = __fadd2_rn(L.ha, make_float2(cc.x, cc.y));
+    const float2 hinv = make_float2(__fdividef(2.0f, hsum.x), __fdividef(2.0f, hsum.y));
+    const float2 q = __fmul2_rn(r, hinv);
+    const float2 q2 = __fmul2_rn(q, q);
+    const float2 rinv3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
+    const float2 h3 = __fmul2_rn(__fmul2_rn(hinv, hinv), hinv);
+    // S/r:  q < 1:      h^-3 (4/3 - 6/5 q^2 + 1/2 q^3)
+    //       1 <= q < 2: h^-3 (8/3 - 3 q + 6/5 q^2 - 1/6 q^3) - 1/(15 r^3)
+    const float2 s1 = __fmul2_rn(h3, __ffma2_rn(q2, __ffma2_rn(make_float2(0.5f, 0.5f), q, make_float2(-1.2f, -1.2f)),
+                                                make_float2(4.0f / 3.0f, 4.0f / 3.0f)));
+    const float2 s2 = __ffma2_rn(
+        h3,
+        __ffma2_rn(q,
+                   __ffma2_rn(q, __ffma2_rn(make_float2(-1.0f / 6.0f, -1.0f / 6.0f), q, make_float2(1.2f, 1.2f)),
+                              make_float2(-3.0f, -3.0f)),
+                   make_float2(8.0f / 3.0f, 8.0f / 3.0f)),
+        __fmul2_rn(make_float2(-1.0f / 15.0f, -1.0f / 15.0f), rinv3));
+    // -phi: q < 1:      h^-1 (7/5 - 2/3 q^2 + 3/10 q^4 - 1/10 q^5)
+    //       1 <= q < 2: h^-1 (8/5 - 4/3 q^2 + q^3 - 3/10 q^4 + 1/30 q^5) - 1/(15 r)
+    const float2 p1 = __fmul2_rn(
+        hinv, __ffma2_rn(q2,
+                         __ffma2_rn(q2, __ffma2_rn(make_float2(-0.1f, -0.1f), q, make_float2(0.3f, 0.3f)),
+                                    make_float2(-2.0f / 3.0f, -2.0f / 3.0f)),
+                         make_float2(1.4f, 1.4f)));
+    const float2 p2 = __ffma2_rn(
+        hinv,
+        __ffma2_rn(q2,
+                   __ffma2_rn(q,
+                              __ffma2_rn(q, __ffma2_rn(make_float2(1.0f / 30.0f, 1.0f / 30.0f), q, make_float2(-0.3f, -0.3f)),
+                                         make_float2(1.0f, 1.0f)),
+                              make_float2(-4.0f / 3.0f, -4.0f / 3.0f)),
+                   make_float2(1.6f, 1.6f)),
+        __fmul2_rn(make_float2(-1.0f / 15.0f, -1.0f / 15.0f), rinv));
+    const float2 sr = make_float2(q.x < 1.0f ? s1.x : (q.x < 2.0f ? s2.x : rinv3.x),
+                                  q.y < 1.0f ? s1.y : (q.y < 2.0f ? s2.y : rinv3.y));
+    const float2 np = make_float2(q.x < 1.0f ? p1.x : (q.x < 2.0f ? p2.x : rinv.x),
+                                  q.y < 1.0f ? p1.y : (q.y < 2.0f ? p2.y : rinv.y));
+    const float2 nm = make_float2(b.z, b.w);  // -m_b
+    const float2 nw = __fmul2_rn(nm, sr);
+    L.In[0] = __ffma2_rn(nw, dx, L.In[0]);
+    L.In[1] = __ffma2_rn(nw, dy, L.In[1]);
+    L.In[2] = __ffma2_rn(nw, dz, L.In[2]);
+    L.In[3] = __ffma2_rn(nm, np, L.In[3]);  // (-m_b)(-phi)
+    return r2;
+}
+
+// The float64 definition of the neighbour test (b a sorted index, -1 for a padding slot).
+__device__ __noinline__ int nb_settle(const double *px, const double *py, const double *pz, const double *ph, int a,
+                                      int b) {
+    if (b == a || b < 0) return 0;
+    const double s2 = __dmul_rn(2.0, ph[a]);
+    return dist2_rn(px[a], py[a], pz[a], px[b], py[b], pz[b]) < __dmul_rn(s2, s2) ? 1 : 0;
+}
+
+// The pair loops of one staged tile for the lane's sink particle a (stream j of S).  Each loop
+// runs in blocks of kFoldIters source pairs, folded into the compensated totals after each
+// block.  With NB the candidate part of the close region also counts the pairs with d^2 below
+// (2h)^2 (by the sign of d^2 - (2h)^2, exact outside the band |d^2 - (2h)^2| <= B); a block in
+// which some pair fell inside the band is gone through again with the float64 test deciding
+// those pairs.
 template <bool NB>
-__global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
+__device__ __forceinline__ void near_tile_lane(const GCtx &c, const NearSmem &sm, const NearTile &tl, int j, int S,
+                                               int a, NearLane &L) {
+    const int pcc = tl.ncc >> 1, pc = tl.nclose >> 1;
+    int k = j;
+    if (NB) {
+        const float2 h2 = make_float2(L.h2, L.h2);
+        while (k < pcc) {
+            const int kb = k;
+            float bandmin = 3e38f;
+            int cnt = 0;
+#pragma unroll 2
+            for (int t = 0; t < kFoldIters && k < pcc; ++t, k += S) {
+                const float2 r2 = near_pair_close(L, sm.A[k], sm.B[k], sm.C[k]);
+                const float2 e = __fadd2_rn(r2, make_float2(-h2.x, -h2.y));  // r^2 - (2h)^2
+                cnt += (int)(__float_as_uint(e.x) >> 31) + (int)(__float_as_uint(e.y) >> 31);
+                bandmin = fminf(bandmin, fminf(fabsf(e.x), fabsf(e.y)));
+            }
+            near_fold(L);
+            if (bandmin <= L.B) {  // rare: some pair of the block lies inside the band
+                for (int kk = kb; kk < k; kk += S) {
+                    const float4 a4 = sm.A[kk], b4 = sm.B[kk], c4 = sm.C[kk];
+                    float2 dx, dy, dz;
+                    const float2 r2 = near_r2(L, a4, b4, dx, dy, dz);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const float e = __fsub_rn(u ? r2.y : r2.x, h2.x);
+                        if (fabsf(e) <= L.B) {
+                            cnt -= (int)(__float_as_uint(e) >> 31);
+                            cnt += nb_settle(c.px, c.py, c.pz, c.ph, a, __float_as_int(u ? c4.w : c4.z));
+                            ++L.nfb;
+                        }
+                    }
+                }
+            }
+            L.cnt += cnt;
+        }
+    }
+    while (k < pc) {
+#pragma unroll 2
+        for (int t = 0; t < kFoldIters && k < pc; ++t, k += S) near_pair_close(L, sm.A[k], sm.B[k], sm.C[k]);
+        near_fold(L);
+    }
+    const int pf = kNearTile >> 1;
+    k = ((kNearTile - tl.nfar) >> 1) + j;
+    while (k < pf) {
+#pragma unroll 4
+        for (int t = 0; t < kFoldIters && k < pf; ++t, k += S) near_pair_newton(L, sm.A[k], sm.B[k]);
+        near_fold(L);
+    }
+}
+
+// Mixed near field; with NB also the neighbour counts of Sec. 2.3 on the same staged sources
+// (to nb_counts by original index).  The float32 neighbour filter compares d^2 with (2h)^2 -+ B,
+// B = 2^-19 ((W + |d_a|_1)^2 + (2h)^2) + 1e-30, W the tile's largest w (see stage_near_mixed):
+// the input and offset roundings, the squares and sums, the rounding of d^2 - (2h)^2 and of
+// (2h)^2 stay below 16 u F, half of B; inside the band the float64 test (the definition) decides.
+// The pair of a particle with itself (d^2 = 0) counts whenever (2h)^2 > B and is then taken off
+// the count; inside the band the float64 test excludes it by index.
+template <bool NB>
+__global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(GCtx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const NearSmem<NB> sm(smem_raw + (size_t)w * NearSmem<NB>::bytes);
-    NbGroup g;
-    g.nfb = 0;
+    const NearSmem sm(smem_raw + (size_t)w * NearSmem::bytes);
+    int nfb_total = 0;
     for (int s = blockIdx.x * kNearWarps + w; s < c.nsinks; s += gridDim.x * kNearWarps) {
         const int A = c.sinks[s];
         const int fA = c.nfirst[A], nA = c.ncount[A];
@@ -614,117 +619,98 @@ __global__ void __launch_bounds__(kNearWarps * 32, 2) k_near_mixed(GCtx c) {
             RA = sqrtf(R2) * (1.0f + 0x1p-10f);
             HA = H;
         }
-        // Up to kSuper groups of eight sink particles share each staged tile: the tile loop is
-        // outside the group loop, and each group's lane totals and neighbour counts wait in
-        // shared memory while another group runs.  Sinks with more particles take several
-        // such passes.
-        float wmax = 0.f;
-        for (int A0 = 0; A0 < nA; A0 += kSuper * kGroupMixed) {
-            const int ng = min(kSuper, (nA - A0 + kGroupMixed - 1) / kGroupMixed);
-            for (int gi = 0; gi < ng; ++gi) {
-                sm.gacc[gi * 32 + lane] = make_float2(0.f, 0.f);
-                if (NB && lane < kGroupMixed) sm.grun[gi * kGroupMixed + lane] = 0;
+        // passes of up to 32 sink particles (one pass unless the cell holds more)
+        for (int a0 = 0; a0 < nA; a0 += 32) {
+            const int P = min(32, nA - a0), S = 32 / P;
+            const int i = lane % P, j = lane / P;
+            const bool active = j < S;
+            const int a = fA + a0 + i;
+            NearLane L;
+            const float4 pa = c.p32[a];
+            const float ha = c.h32[a];
+            L.xa = make_float2(pa.x, pa.x);
+            L.ya = make_float2(pa.y, pa.y);
+            L.za = make_float2(pa.z, pa.z);
+            L.ha = make_float2(ha, ha);
+            {
+                const float h2f = 2.0f * ha;  // = float32(2 h) exactly
+                L.h2 = h2f * h2f;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                L.In[q] = make_float2(0.f, 0.f);
+                L.sum[q] = 0.f;
+                L.comp[q] = 0.f;
+            }
+            L.cnt = 0;
+            L.nfb = 0;
+            NearCursor cur{0, 0, 0};
+            for (;;) {
+                float wmax = 0.f;
+                const NearTile tl = stage_near_mixed<NB>(c, s, A, fA, a0, P, nlist, nr, cur, sm, RA, HA, wmax);
+                if (NB) {
+                    const float F = wmax + (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z));
+                    L.B = fmaf(F, F, L.h2) * 0x1p-19f + 1e-30f;
+                    // the self pair counts below (once, in stream 0)
+                    if (active && j == 0 && sm.self[i] >= 0 && L.B < L.h2) --L.cnt;
+                }
+                if (active) near_tile_lane<NB>(c, sm, tl, j, S, a, L);
+                __syncwarp();
+                if (tl.last) break;
+            }
+            // sum the S streams of each sink particle (compensated), through shared memory
+            float *red = reinterpret_cast<float *>(sm.A);
+            if (active) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    red[lane * 9 + q] = L.sum[q];
+                    red[lane * 9 + 4 + q] = L.comp[q];
+                }
+                red[lane * 9 + 8] = __int_as_float(L.cnt);
             }
             __syncwarp();
-            for (int64_t t0 = 0;; t0 += kNearTile) {
-                const NearTile tl = stage_near_mixed<NB>(c, s, A, nlist, nr, t0, sm, RA, HA, wmax);
-                for (int gi = 0; gi < ng; ++gi) {
-                    const int a0 = A0 + gi * kGroupMixed;
-                    const int na = min(kGroupMixed, nA - a0);
-                    if (lane < kGroupMixed) {
-                        const int i = min(lane, na - 1);
-                        const float4 pa = c.p32[fA + a0 + i];
-                        sm.snk[lane] = make_float4(pa.x, pa.y, pa.z, c.h32[fA + a0 + i]);
-                    }
-                    __syncwarp();
-                    if (lane < kGroupMixed) {
-                        const float4 u = sm.snk[lane & ~1], v = sm.snk[lane | 1];
-                        sm.snk2[lane] = (lane & 1) ? make_float4(u.z, v.z, u.w, v.w) : make_float4(u.x, v.x, u.y, v.y);
-                    }
-                    if (NB) {
-                        g.a0 = fA + a0;
+            if (lane < P) {
+                float ts[4], tc[4];
+                int tn = 0;
 #pragma unroll
-                        for (int i = 0; i < kGroupMixed; ++i) g.run[i] = sm.grun[gi * kGroupMixed + i];
-                        // neighbour band of each sink particle for this tile (-1: padding slot)
-                        if (lane < kGroupMixed) {
-                            float2 bd = make_float2(-1.f, -1.f);
-                            if (lane < na) {
-                                const float4 pa = c.p32[fA + a0 + lane];
-                                const float h2f = 2.0f * c.h32[fA + a0 + lane];  // = float32(2 h) exactly
-                                const float h2 = h2f * h2f;
-                                const float F = wmax + (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z));
-                                const float B = fmaf(F, F, h2) * 0x1p-19f + 1e-30f;
-                                bd = make_float2(h2 - B, h2 + B);
-                            }
-                            sm.band[lane] = bd;
-                        }
-                        __syncwarp();
-                        if (lane < kGroupMixed / 2) {
-                            sm.hi2[lane] = make_float2(sm.band[2 * lane].y, sm.band[2 * lane + 1].y);
-                            sm.lo2[lane] = make_float2(sm.band[2 * lane].x, sm.band[2 * lane + 1].x);
-                        }
-                    }
-                    __syncwarp();
-                    const float2 st = sm.gacc[gi * 32 + lane];
-                    float rs = st.x, rc = st.y;  // compensated total of value lane mod 4 G (= 4 i + q)
-                    near_tile<kGroupMixed, NB>(c, sm, tl, na, rs, rc, g);
-                    __syncwarp();
-                    sm.gacc[gi * 32 + lane] = make_float2(rs, rc);
-                    if (NB && lane < kGroupMixed) {
-                        int n = g.run[0];
-#pragma unroll
-                        for (int i = 1; i < kGroupMixed; ++i)
-                            if (lane == i) n = g.run[i];
-                        sm.grun[gi * kGroupMixed + lane] = n;
-                    }
-                    __syncwarp();
+                for (int q = 0; q < 4; ++q) {
+                    ts[q] = 0.f;
+                    tc[q] = 0.f;
                 }
-                if (t0 + kNearTile >= tl.S) break;
-            }
-            for (int gi = 0; gi < ng; ++gi) {
-                const int a0 = A0 + gi * kGroupMixed;
-                const int na = min(kGroupMixed, nA - a0);
-                const float2 st = sm.gacc[gi * 32 + lane];
-                const double tot = __dadd_rn((double)st.x, (double)st.y);  // lane l < 4 na: particle l/4, quantity l%4
-                const double q0v = __shfl_sync(0xffffffffu, tot, (4 * lane) & 31);
-                const double q1v = __shfl_sync(0xffffffffu, tot, (4 * lane + 1) & 31);
-                const double q2v = __shfl_sync(0xffffffffu, tot, (4 * lane + 2) & 31);
-                const double q3v = __shfl_sync(0xffffffffu, tot, (4 * lane + 3) & 31);
-                if (lane < na) {
-                    const int a = fA + a0 + lane;
-                    const float4 pa = c.p32[a];
-                    const float d[3] = {pa.x, pa.y, pa.z};
-                    // the tile loop included the pair of a with itself: zero force, potential
-                    // m_a phi(0) = m_a (-1.4) 2 / (h_a + h_a) computed exactly as the loop did
-                    const float ha = c.h32[a];
-                    const float self_pot = pa.w * (__fdividef(2.0f, ha + ha) * -1.4f);
-                    float Cf[20];
+                for (int jj = 0; jj < S; ++jj) {
+                    const float *r = red + (lane + jj * P) * 9;
 #pragma unroll
-                    for (int i = 0; i < 20; ++i) Cf[i] = c.coef32[(int64_t)s * 20 + i];
-                    float phf, af[3];
-                    taylor_eval<float>(Cf, d, phf, af);
-                    const int o = c.pidx[a];
-                    c.acc[3 * (int64_t)o] = q0v + (double)af[0];
-                    c.acc[3 * (int64_t)o + 1] = q1v + (double)af[1];
-                    c.acc[3 * (int64_t)o + 2] = q2v + (double)af[2];
-                    if (c.pot) c.pot[o] = q3v + (double)phf - (double)self_pot;
-                    if (NB) {
-                        const int n = sm.grun[gi * kGroupMixed + lane];
-                        c.nb_counts[o] = n;
-                        if (n > kNbRowCap) {
-                            const int q = atomicAdd(&c.status[ST_LONGROWS], 1);
-                            if (q < c.cap_long) c.nb_long[q] = make_int2(a, s);
-                        }
+                    for (int q = 0; q < 4; ++q) {
+                        float t, e;
+                        two_sum(ts[q], r[q], t, e);
+                        ts[q] = t;
+                        tc[q] = __fadd_rn(__fadd_rn(tc[q], r[4 + q]), e);
                     }
+                    tn += __float_as_int(r[8]);
                 }
+                // the tile loops included the pair of a with itself: zero force, potential
+                // m_a phi(0) = -1.4 m_a 2 / (h_a + h_a), accumulated as (-m_a)(1.4 hinv)
+                const float self_pot = -pa.w * (__fdividef(2.0f, ha + ha) * 1.4f);
+                float Cf[20];
+#pragma unroll
+                for (int q = 0; q < 20; ++q) Cf[q] = c.coef32[(int64_t)s * 20 + q];
+                const float d[3] = {pa.x, pa.y, pa.z};
+                float phf, af[3];
+                taylor_eval<float>(Cf, d, phf, af);
+                const int o = c.pidx[a];
+                c.acc[3 * (int64_t)o] = __dadd_rn((double)ts[0], (double)tc[0]) + (double)af[0];
+                c.acc[3 * (int64_t)o + 1] = __dadd_rn((double)ts[1], (double)tc[1]) + (double)af[1];
+                c.acc[3 * (int64_t)o + 2] = __dadd_rn((double)ts[2], (double)tc[2]) + (double)af[2];
+                if (c.pot) c.pot[o] = __dadd_rn((double)ts[3], (double)tc[3]) + (double)phf - (double)self_pot;
+                if (NB) c.nb_counts[o] = tn;
             }
+            nfb_total += L.nfb;
             __syncwarp();
         }
     }
     if (NB) {
-        int n = g.nfb;
-        for (int o = 16; o >= 1; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-        if (lane == 0 && n) atomicAdd(&c.status[ST_NBFALLBACK], n);
+        for (int o = 16; o >= 1; o >>= 1) nfb_total += __shfl_xor_sync(0xffffffffu, nfb_total, o);
+        if (lane == 0 && nfb_total) atomicAdd(&c.status[ST_NBFALLBACK], nfb_total);
     }
 }
 
@@ -866,9 +852,6 @@ GCtx make_gctx(rcb_tree *t, double *acc, double *pot) {
     c.acc = acc;
     c.pot = pot;
     c.nb_counts = t->nb_count;
-    c.nb_rows = t->nb_rows;
-    c.nb_long = t->nb_long;
-    c.cap_long = (int)t->N;
     c.status = t->d_status;
     return c;
 }
@@ -896,16 +879,16 @@ namespace {
 template <bool NB>
 int launch_near_mixed(rcb_tree *t, const GCtx &c) {
     const int nsm = sm_count_g();
-    const size_t smem = (size_t)kNearWarps * NearSmem<NB>::bytes;
+    const size_t smem = (size_t)kNearWarps * NearSmem::bytes;
     RCB_CUDA_TRY(cudaFuncSetAttribute(k_near_mixed<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int nb = std::max(1, std::min((t->nsinks + kNearWarps - 1) / kNearWarps, nsm * 2 * 16));
+    const int nb = std::max(1, std::min((t->nsinks + kNearWarps - 1) / kNearWarps, nsm * kNearMinBlocks * 16));
     k_near_mixed<NB><<<nb, kNearWarps * 32, smem, t->stream>>>(c); note_launch();
     RCB_CUDA_TRY(cudaGetLastError());
     return RCB_OK;
 }
 
 // Far field and near field; with NB (mixed form only) the near kernel also counts the
-// neighbours and writes their slot rows.
+// neighbours.
 int gravity_impl(rcb_tree *t, double *acc, double *pot, bool nb) {
     cudaStream_t st = t->stream;
     const GCtx c = make_gctx(t, acc, pot);
@@ -945,9 +928,8 @@ int gravity_neighbours(rcb_tree *t, double *acc, double *pot) {
         if (rc) return rc;
         return count_neighbours(t);
     }
-    if (t->nb_valid) return gravity_impl(t, acc, pot, false);  // counts and rows are current
-    int rc = ensure_nb_rows(t);
-    if (rc) return rc;
+    if (t->nb_valid) return gravity_impl(t, acc, pot, false);  // the counts are current
+    int rc;
     RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_NBFALLBACK, 0, 2 * sizeof(int), t->stream));
     rc = gravity_impl(t, acc, pot, true);
     if (rc) return rc;

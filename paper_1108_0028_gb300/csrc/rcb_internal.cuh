@@ -12,7 +12,6 @@ namespace rcb {
 typedef __int128 i128;
 typedef unsigned __int128 u128;
 
-constexpr int kNbRowCap = 128;  // slots of a particle's neighbour row before the compaction
 constexpr int kMaxL = 28;           // deepest supported lowest level (node labels < 2^29)
 constexpr int kTcta = 1024;        // largest cell whose subtree one CTA builds in shared memory (two CTAs per SM)
 constexpr int kCtaThreads = 256;    // threads of that CTA
@@ -30,7 +29,6 @@ enum StatusWord {
     ST_NCHUNKS = 6,    // chunks of the current level pass
     ST_NSINKS = 7,     // non-empty ll-cells
     ST_NBFALLBACK = 8, // neighbour decisions taken in FP64
-    ST_LONGROWS = 9,   // neighbour rows too long for the in-warp sort
     ST_OUTSIDE = 10,   // particles outside their ll-cell (tree integrity check)
     ST_NWORDS = 16
 };
@@ -263,10 +261,6 @@ struct rcb_tree {
     double *coef;    // [nsinks][20] far-field Taylor coefficients
     float *coef32;   // their float32 values (mixed form)
     int64_t *nb_count;
-    int2 *nb_long;     // [N] (sorted particle, sink) of rows longer than the slot rows
-    int32_t *nb_rows;  // [N][128] neighbour rows before the compaction (allocated on first use)
-    int64_t cap_rows;
-    int nb_nlong;
     void *scan_tmp;
     int64_t cap_scan;
     int64_t nb_total;
@@ -322,8 +316,7 @@ int density(rcb_tree *t, const int64_t *offsets, const int32_t *idx, double *rho
 // neighbours.cu
 int neighbour_counts(rcb_tree *t, int64_t *counts, int *status);  // count pass into caller memory
 int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *needed);
-int ensure_nb_rows(rcb_tree *t);          // slot rows of the neighbour pass ([N][kNbRowCap])
-int count_neighbours(rcb_tree *t);        // counts, slot rows and offsets (nb_count) unless valid
+int count_neighbours(rcb_tree *t);        // counts and offsets (nb_count) unless valid
 int scan_neighbour_counts(rcb_tree *t);   // nb_count: counts by original index -> offsets
 int fetch_neighbour_total(rcb_tree *t);   // total and long-row count to the host; counts valid
 // gravity.cu
