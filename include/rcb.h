@@ -205,20 +205,21 @@ int rcb_density(rcb_tree *tree, const int64_t *offsets, const int32_t *idx, doub
 
 /*
  * rcb_neighbour_offsets_noalloc -- the paper has no counterpart: this is a convenience for
- *   callers that cannot allocate device memory when they need neighbour offsets (for example
- *   code being recorded into a CUDA graph, where cudaMalloc is not allowed, or an application
- *   whose memory manager owns the whole device and forbids allocations by libraries).
+ *   callers that cannot allocate device memory when they need neighbour offsets (for example an
+ *   application whose memory manager owns the whole device and forbids allocations by libraries).
  *   It returns the same offsets as rcb_neighbours(tree, offsets, NULL, 0, needed, stream) and
  *   allocates nothing: the per-particle counts are written straight into `offsets` and the only
- *   other scratch (the scan's per-tile sums and one counter) is a fixed static array of about
- *   33 KB inside the library, which every GPU that loads the library keeps until the process
- *   exits.
+ *   other scratch (the scan's per-tile sums and the status words) is a fixed static array of
+ *   about 33 KB inside the library, which every GPU that loads the library keeps until the
+ *   process exits.
  *   offsets  device, [N+1] int64, written;  needed  host, out: offsets[N]
  *   Limit: N <= 33,554,432 (2^25); larger trees return RCB_ERR_CAPACITY.
  *   The first call on a device looks the static array up (cudaGetSymbolAddress) with that
- *   device current; make that first call before any stream capture.  All calls share the one
- *   array, so calls that overlap on the GPU (other streams, other threads) race: serialise
- *   them.  Synchronises `stream`.
+ *   device current and keeps its address for the life of the process (the device's primary
+ *   context must stay alive: no cudaDeviceReset in between).  All calls share the one array, so
+ *   calls that overlap on the GPU (other streams, other threads) race: serialise them.
+ *   The call reads the total back and synchronises `stream`; it cannot be made while the stream
+ *   is being captured into a CUDA graph.
  */
 int rcb_neighbour_offsets_noalloc(rcb_tree *tree, int64_t *offsets, int64_t *needed, void *stream);
 

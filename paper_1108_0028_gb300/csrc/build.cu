@@ -1096,6 +1096,7 @@ __global__ void k_pack_nodes(PackCtx c, int64_t nn) {
 // ------------------------------------------------------------------------------------------
 // Three-phase device-wide exclusive scans (int32 -> int32 and int64 -> int64).
 constexpr int kScanThreads = 1024, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
+static_assert(kScanTile == kScanTileElems, "the scan's scratch size is derived from kScanTileElems");
 
 template <typename T>
 __device__ T block_scan_excl_t(T v, T *warp_tot, T *total) {
@@ -1325,7 +1326,7 @@ size_t chunk_part_bytes(int64_t cap_chunks) {
     return std::max<size_t>((size_t)cap_chunks * sizeof(ChunkPart), (size_t)4096 * sizeof(Red));
 }
 
-int64_t scan_tmp_bytes(int64_t n) { return ((n + kScanTile - 1) / kScanTile + 2) * (int64_t)sizeof(int64_t); }
+int64_t scan_tmp_bytes(int64_t n) { return scan_tmp_words(n) * (int64_t)sizeof(int64_t); }
 
 int scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, void *tmp, cudaStream_t st) {
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;

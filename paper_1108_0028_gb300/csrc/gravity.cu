@@ -30,6 +30,7 @@
 #include <cstring>
 
 #include "far_math.cuh"
+#include "nb_rows.cuh"
 #include "rcb_internal.cuh"
 
 namespace rcb {
@@ -57,8 +58,9 @@ struct GCtx {
     double *coef;
     float *coef32;
     double *acc, *pot;
-    // neighbour counts fused into the mixed near field
+    // neighbour rows fused into the mixed near field
     int64_t *nb_counts;  // [N] by original index
+    RowOut ro;
     int *status;
 };
 
@@ -241,29 +243,40 @@ constexpr int kNearTile = 256;  // staged source slots per warp (even)
 constexpr int kNearPad = 4;     // slots kept free for padding the regions to even length
 constexpr int kFoldIters = 16;  // source pairs summed in float32 before a compensated fold
 
-// Shared memory of one warp: per source pair k, A[k], B[k], C[k] (see above), and the slot of
+// Shared memory of one warp: per source pair k, A[k], B[k], C[k] (see above); with the neighbour
+// rows (NB) also D[k] = (original indices, unused), the row buffer (nb_rows.cuh) and the slot of
 // each sink particle of the pass in the current tile (-1 if not staged there).
+template <bool NB>
 struct NearSmem {
-    static constexpr size_t bytes = (size_t)(kNearTile / 2) * 3 * sizeof(float4) + 32 * sizeof(int);
-    float4 *A, *B, *C;
+    static constexpr int H = kNearTile / 2;  // source pairs per tile
+    static constexpr size_t bytes =
+        (size_t)H * (NB ? 4 : 3) * sizeof(float4) + (NB ? kRowBuf * sizeof(int32_t) + 32 * sizeof(int) : 0) + 32 * sizeof(int);
+    float4 *P;      // A[H], B[H], C[H], D[H] (NB)
+    int32_t *rows;  // NB: row buffer
+    int *rowcnt;    // NB: [32] entries of each row of the pass so far
     int *self;
     __device__ NearSmem(unsigned char *p) {
-        A = reinterpret_cast<float4 *>(p);
-        B = A + kNearTile / 2;
-        C = B + kNearTile / 2;
-        self = reinterpret_cast<int *>(C + kNearTile / 2);
+        P = reinterpret_cast<float4 *>(p);
+        rows = reinterpret_cast<int32_t *>(P + (NB ? 4 : 3) * H);
+        rowcnt = rows + (NB ? kRowBuf : 0);
+        self = rowcnt + (NB ? 32 : 0);
     }
-    // store source slot s: offset d (from the sink's centre of mass), mass, h, sorted index
-    __device__ __forceinline__ void put(int s, float dx, float dy, float dz, float m, float h, int idx) const {
-        float *a = reinterpret_cast<float *>(A + (s >> 1)), *b = reinterpret_cast<float *>(B + (s >> 1));
-        float *cc = reinterpret_cast<float *>(C + (s >> 1));
+    __device__ __forceinline__ float4 a(int k) const { return P[k]; }
+    __device__ __forceinline__ float4 b(int k) const { return P[k + H]; }
+    __device__ __forceinline__ float4 c(int k) const { return P[k + 2 * H]; }
+    __device__ __forceinline__ const int4 *D() const { return reinterpret_cast<const int4 *>(P + 3 * H); }
+    // store source slot s: offset d (from the sink's centre of mass), mass, h, sorted and original
+    // index
+    __device__ __forceinline__ void put(int s, float dx, float dy, float dz, float m, float h, int idx, int oidx) const {
+        float *q = reinterpret_cast<float *>(P + (s >> 1));
         const int u = s & 1;
-        a[u] = -dx;
-        a[2 + u] = -dy;
-        b[u] = -dz;
-        b[2 + u] = -m;
-        cc[u] = h;
-        cc[2 + u] = __int_as_float(idx);
+        q[u] = -dx;
+        q[2 + u] = -dy;
+        q[4 * H + u] = -dz;
+        q[4 * H + 2 + u] = -m;
+        q[8 * H + u] = h;
+        q[8 * H + 2 + u] = __int_as_float(idx);
+        if (NB) reinterpret_cast<int *>(q)[12 * H + u] = oidx;
     }
 };
 
@@ -302,7 +315,7 @@ struct NearTile {
 // of the neighbour filter.
 template <bool NB>
 __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0, int P, int nlist, int nr,
-                                     NearCursor &cur, const NearSmem &sm, float RA, float HA, float &wmax) {
+                                     NearCursor &cur, const NearSmem<NB> &sm, float RA, float HA, float &wmax) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)s * c.cap_near;
@@ -353,13 +366,16 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0
             }
             float4 pb[2];
             float hb[2];
+            int ob[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 pb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 hb[u] = 0.f;
+                ob[u] = 0;
                 if (act[u]) {
                     pb[u] = c.p32[b[u]];
                     hb[u] = c.h32[b[u]];
+                    if (NB) ob[u] = c.pidx[b[u]];
                 }
             }
 #pragma unroll
@@ -373,7 +389,7 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0
                 const unsigned mf = __ballot_sync(0xffffffffu, act[u] && far);
                 if (act[u]) {
                     const int at = far ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt);
-                    sm.put(at, vx, vy, vz, pb[u].w, hb[u], b[u]);
+                    sm.put(at, vx, vy, vz, pb[u].w, hb[u], b[u], ob[u]);
                     if (NB) {
                         if (cand)
                             wl = fmaxf(wl, (fabsf(cx[u]) + fabsf(cy[u]) + fabsf(cz[u])) + fabsf(pb[u].x) +
@@ -395,7 +411,7 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0
         cur.k0 = min(cur.k0 + 32, kend);
         if (cur.k0 == nr && ncc < 0) {  // all candidates staged: pad the candidate part to even
             if (nclose & 1) {
-                if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1);
+                if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1, -1);
                 ++nclose;
             }
             ncc = nclose;
@@ -404,16 +420,16 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0
     if (!full) cur.t0 = cur.pos;
     if (ncc < 0) ncc = cur.k0 < nr ? nclose : 0;
     if (ncc & 1) {  // the tile ended inside the candidates
-        if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1);
+        if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1, -1);
         ++nclose;
         ++ncc;
     }
     if (nclose & 1) {
-        if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1);
+        if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1, -1);
         ++nclose;
     }
     if (nfar & 1) {
-        if (lane == 0) sm.put(kNearTile - 1 - nfar, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1);
+        if (lane == 0) sm.put(kNearTile - 1 - nfar, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1, -1);
         ++nfar;
     }
     if (NB) {
@@ -469,7 +485,8 @@ __device__ __forceinline__ void near_pair_newton(NearLane &L, const float4 a, co
 // branch of each half selected by its q); -phi is evaluated, so that the stored -m_b multiplies
 // it.  Returns r^2 of both pairs.  The pair of a particle with itself has r = 0: zero force,
 // potential m_a phi(0) (removed in the epilogue).
-__device__ __forceinline__ float2 near_pair_close(NearLane &L, const float4 a, const float4 b, const float4 cc) {
+__device__ __forceinline__ float2 near_pair_close(NearLane &L, const float4 a, const float4 b, const float4 cc,
+                                                  bool ok = true) {
     float2 dx, dy, dz;
     const float2 r2 = near_r2(L, a, b, dx, dy, dz);
     const float2 rinv = make_float2(rsqrtf(fmaxf(r2.x, 1e-30f)), rsqrtf(fmaxf(r2.y, 1e-30f)));
@@ -511,7 +528,7 @@ __device__ __forceinline__ float2 near_pair_close(NearLane &L, const float4 a, c
                                   q.y < 1.0f ? s1.y : (q.y < 2.0f ? s2.y : rinv3.y));
     const float2 np = make_float2(q.x < 1.0f ? p1.x : (q.x < 2.0f ? p2.x : rinv.x),
                                   q.y < 1.0f ? p1.y : (q.y < 2.0f ? p2.y : rinv.y));
-    const float2 nm = make_float2(b.z, b.w);  // -m_b
+    const float2 nm = ok ? make_float2(b.z, b.w) : make_float2(0.f, 0.f);  // -m_b
     const float2 nw = __fmul2_rn(nm, sr);
     L.In[0] = __ffma2_rn(nw, dx, L.In[0]);
     L.In[1] = __ffma2_rn(nw, dy, L.In[1]);
@@ -528,60 +545,71 @@ __device__ __noinline__ int nb_settle(const double *px, const double *py, const 
     return dist2_rn(px[a], py[a], pz[a], px[b], py[b], pz[b]) < __dmul_rn(s2, s2) ? 1 : 0;
 }
 
-// The pair loops of one staged tile for the lane's sink particle a (stream j of S).  Each loop
-// runs in blocks of kFoldIters source pairs, folded into the compensated totals after each
-// block.  With NB the candidate part of the close region also counts the pairs with d^2 below
-// (2h)^2 (by the sign of d^2 - (2h)^2, exact outside the band |d^2 - (2h)^2| <= B); a block in
-// which some pair fell inside the band is gone through again with the float64 test deciding
-// those pairs.
+// The pair loops of one staged tile for the lane's sink particle a (stream j of S; lanes with
+// active false hold no particle of the pass).  Each loop runs in blocks of kFoldIters source
+// pairs, folded into the compensated totals after each block.  With NB the candidate part of the
+// close region also tests every pair for |r_a - r_b| < 2 h_a: by the sign of d^2 - (2h)^2, exact
+// outside the band |d^2 - (2h)^2| <= B; a block in which some pair fell inside the band is gone
+// through again with the float64 test deciding those pairs.  A block's neighbours are flagged in
+// a bit mask and their original indices appended to the lane's row once per block (row_append);
+// the pair of a particle with itself (slot self) is skipped.
 template <bool NB>
-__device__ __forceinline__ void near_tile_lane(const GCtx &c, const NearSmem &sm, const NearTile &tl, int j, int S,
-                                               int a, NearLane &L) {
+__device__ __forceinline__ void near_tile_lane(const GCtx &c, const NearSmem<NB> &sm, const NearTile &tl, int j, int S,
+                                               bool active, int a, int i, int self, int32_t *rowp, int rc,
+                                               NearLane &L) {
     const int pcc = tl.ncc >> 1, pc = tl.nclose >> 1;
     int k = j;
     if (NB) {
-        const float2 h2 = make_float2(L.h2, L.h2);
-        while (k < pcc) {
-            const int kb = k;
+        const float2 nh2 = make_float2(-L.h2, -L.h2);
+        const int nst = (pcc + S - 1) / S;  // loop steps of the warp (stream 0 the longest)
+        for (int t0 = 0; t0 < nst; t0 += kFoldIters) {
+            const int kb = j + t0 * S;
+            unsigned mask = 0;
             float bandmin = 3e38f;
-            int cnt = 0;
-#pragma unroll 2
-            for (int t = 0; t < kFoldIters && k < pcc; ++t, k += S) {
-                const float2 r2 = near_pair_close(L, sm.A[k], sm.B[k], sm.C[k]);
-                const float2 e = __fadd2_rn(r2, make_float2(-h2.x, -h2.y));  // r^2 - (2h)^2
-                cnt += (int)(__float_as_uint(e.x) >> 31) + (int)(__float_as_uint(e.y) >> 31);
-                bandmin = fminf(bandmin, fminf(fabsf(e.x), fabsf(e.y)));
+            if (active) {
+                int kq = kb;
+                for (int t = 0; t < kFoldIters && kq < pcc; ++t, kq += S) {
+                    const float2 r2 = near_pair_close(L, sm.a(kq), sm.b(kq), sm.c(kq));
+                    const float2 e = __fadd2_rn(r2, nh2);  // d^2 - (2h)^2
+                    const float ex = fabsf(e.x), ey = fabsf(e.y);
+                    bandmin = fminf(bandmin, fminf(ex, ey));
+                    mask |= (unsigned)(e.x < 0.f && ex > L.B && 2 * kq != self) << (2 * t);
+                    mask |= (unsigned)(e.y < 0.f && ey > L.B && 2 * kq + 1 != self) << (2 * t + 1);
+                }
+                near_fold(L);
             }
-            near_fold(L);
-            if (bandmin <= L.B) {  // rare: some pair of the block lies inside the band
-                for (int kk = kb; kk < k; kk += S) {
-                    const float4 a4 = sm.A[kk], b4 = sm.B[kk], c4 = sm.C[kk];
+            if (__any_sync(0xffffffffu, bandmin <= L.B) && active) {  // rare
+                int kq = kb;
+                for (int t = 0; t < kFoldIters && kq < pcc; ++t, kq += S) {
                     float2 dx, dy, dz;
-                    const float2 r2 = near_r2(L, a4, b4, dx, dy, dz);
+                    const float2 r2 = near_r2(L, sm.a(kq), sm.b(kq), dx, dy, dz);
+                    const float2 e = __fadd2_rn(r2, nh2);
+                    const float4 c4 = sm.c(kq);
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
-                        const float e = __fsub_rn(u ? r2.y : r2.x, h2.x);
-                        if (fabsf(e) <= L.B) {
-                            cnt -= (int)(__float_as_uint(e) >> 31);
-                            cnt += nb_settle(c.px, c.py, c.pz, c.ph, a, __float_as_int(u ? c4.w : c4.z));
+                        if (fabsf(u ? e.y : e.x) <= L.B) {
+                            if (nb_settle(c.px, c.py, c.pz, c.ph, a, __float_as_int(u ? c4.w : c4.z)))
+                                mask |= 1u << (2 * t + u);
                             ++L.nfb;
                         }
                     }
                 }
             }
-            L.cnt += cnt;
+            if (mask) row_append(rowp, rc, sm.rowcnt + i, mask, kb, S, sm.D());
         }
+        k = j + S * ((max(pcc - j, 0) + S - 1) / S);  // the stream's first pair at or after pcc
     }
+    if (!active) return;
     while (k < pc) {
 #pragma unroll 2
-        for (int t = 0; t < kFoldIters && k < pc; ++t, k += S) near_pair_close(L, sm.A[k], sm.B[k], sm.C[k]);
+        for (int t = 0; t < kFoldIters && k < pc; ++t, k += S) near_pair_close(L, sm.a(k), sm.b(k), sm.c(k));
         near_fold(L);
     }
     const int pf = kNearTile >> 1;
     k = ((kNearTile - tl.nfar) >> 1) + j;
     while (k < pf) {
 #pragma unroll 4
-        for (int t = 0; t < kFoldIters && k < pf; ++t, k += S) near_pair_newton(L, sm.A[k], sm.B[k]);
+        for (int t = 0; t < kFoldIters && k < pf; ++t, k += S) near_pair_newton(L, sm.a(k), sm.b(k));
         near_fold(L);
     }
 }
@@ -597,7 +625,7 @@ template <bool NB>
 __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(GCtx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const NearSmem sm(smem_raw + (size_t)w * NearSmem::bytes);
+    const NearSmem<NB> sm(smem_raw + (size_t)w * NearSmem<NB>::bytes);
     int nfb_total = 0;
     for (int s = blockIdx.x * kNearWarps + w; s < c.nsinks; s += gridDim.x * kNearWarps) {
         const int A = c.sinks[s];
@@ -644,34 +672,38 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
             }
             L.cnt = 0;
             L.nfb = 0;
+            const int rc = NB ? kRowBuf / P : 0;
+            int32_t *rowp = sm.rows + i * rc;
+            if (NB) {
+                if (lane < P) sm.rowcnt[lane] = 0;
+                __syncwarp();
+            }
             NearCursor cur{0, 0, 0};
             for (;;) {
                 float wmax = 0.f;
                 const NearTile tl = stage_near_mixed<NB>(c, s, A, fA, a0, P, nlist, nr, cur, sm, RA, HA, wmax);
+                int self = -1;
                 if (NB) {
                     const float F = wmax + (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z));
                     L.B = fmaf(F, F, L.h2) * 0x1p-19f + 1e-30f;
-                    // the self pair counts below (once, in stream 0)
-                    if (active && j == 0 && sm.self[i] >= 0 && L.B < L.h2) --L.cnt;
+                    self = sm.self[i];
                 }
-                if (active) near_tile_lane<NB>(c, sm, tl, j, S, a, L);
+                near_tile_lane<NB>(c, sm, tl, j, S, active, a, i, self, rowp, rc, L);
                 __syncwarp();
                 if (tl.last) break;
             }
             // sum the S streams of each sink particle (compensated), through shared memory
-            float *red = reinterpret_cast<float *>(sm.A);
+            float *red = reinterpret_cast<float *>(sm.P);
             if (active) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     red[lane * 9 + q] = L.sum[q];
                     red[lane * 9 + 4 + q] = L.comp[q];
                 }
-                red[lane * 9 + 8] = __int_as_float(L.cnt);
             }
             __syncwarp();
             if (lane < P) {
                 float ts[4], tc[4];
-                int tn = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     ts[q] = 0.f;
@@ -686,7 +718,6 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
                         ts[q] = t;
                         tc[q] = __fadd_rn(__fadd_rn(tc[q], r[4 + q]), e);
                     }
-                    tn += __float_as_int(r[8]);
                 }
                 // the tile loops included the pair of a with itself: zero force, potential
                 // m_a phi(0) = -1.4 m_a 2 / (h_a + h_a), accumulated as (-m_a)(1.4 hinv)
@@ -702,10 +733,11 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
                 c.acc[3 * (int64_t)o + 1] = __dadd_rn((double)ts[1], (double)tc[1]) + (double)af[1];
                 c.acc[3 * (int64_t)o + 2] = __dadd_rn((double)ts[2], (double)tc[2]) + (double)af[2];
                 if (c.pot) c.pot[o] = __dadd_rn((double)ts[3], (double)tc[3]) + (double)phf - (double)self_pot;
-                if (NB) c.nb_counts[o] = tn;
+                if (NB) c.nb_counts[o] = sm.rowcnt[lane];
             }
             nfb_total += L.nfb;
             __syncwarp();
+            if (NB) rows_finish(c.ro, sm.rows, rc, P, lane < P ? sm.rowcnt[lane] : 0, lane < P ? c.pidx[a] : 0, s, a0);
         }
     }
     if (NB) {
@@ -852,6 +884,7 @@ GCtx make_gctx(rcb_tree *t, double *acc, double *pot) {
     c.acc = acc;
     c.pot = pot;
     c.nb_counts = t->nb_count;
+    c.ro = row_out(t);
     c.status = t->d_status;
     return c;
 }
@@ -879,7 +912,7 @@ namespace {
 template <bool NB>
 int launch_near_mixed(rcb_tree *t, const GCtx &c) {
     const int nsm = sm_count_g();
-    const size_t smem = (size_t)kNearWarps * NearSmem::bytes;
+    const size_t smem = (size_t)kNearWarps * NearSmem<NB>::bytes;
     RCB_CUDA_TRY(cudaFuncSetAttribute(k_near_mixed<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nb = std::max(1, std::min((t->nsinks + kNearWarps - 1) / kNearWarps, nsm * kNearMinBlocks * 16));
     k_near_mixed<NB><<<nb, kNearWarps * 32, smem, t->stream>>>(c); note_launch();
@@ -929,8 +962,8 @@ int gravity_neighbours(rcb_tree *t, double *acc, double *pot) {
         return count_neighbours(t);
     }
     if (t->nb_valid) return gravity_impl(t, acc, pot, false);  // the counts are current
-    int rc;
-    RCB_CUDA_TRY(cudaMemsetAsync(t->d_status + ST_NBFALLBACK, 0, 2 * sizeof(int), t->stream));
+    int rc = reset_nb_rows(t);
+    if (rc) return rc;
     rc = gravity_impl(t, acc, pot, true);
     if (rc) return rc;
     stage_begin(t, SG_NB_COUNT);

@@ -1,13 +1,14 @@
 // Neighbour-list offsets for callers that cannot allocate device memory.
 //
 // rcb_neighbours keeps its per-particle counts and the scan's partial sums in scratch arrays
-// that rcb_build allocates with the tree.  Some callers cannot allocate at all when they need
-// the offsets -- for example code being recorded into a CUDA graph, where cudaMalloc is not
-// allowed, or an application whose own memory manager owns the whole device and does not let
-// libraries allocate after start-up.  rcb_neighbour_offsets_noalloc gives them the same offsets
-// without any allocation: the count pass writes straight into the caller's offsets array, and
-// the only other scratch, the exclusive scan's per-tile sums plus one counter, lives in the
-// fixed-size array below, compiled into the library and reused by every call.
+// that rcb_build allocates with the tree.  Some callers cannot allocate at all when they need the
+// offsets: an application whose own memory manager owns the whole device and does not let
+// libraries allocate after start-up, for example.  rcb_neighbour_offsets_noalloc gives them the
+// same offsets without any allocation: the count pass writes straight into the caller's offsets
+// array, and the only other scratch, the exclusive scan's per-tile sums plus the status words,
+// lives in the fixed-size array below, compiled into the library and reused by every call.  The
+// call reads the total back and synchronises its stream, so it cannot be recorded into a CUDA
+// graph.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -17,9 +18,10 @@
 namespace {
 
 constexpr int64_t kNoAllocMaxN = (int64_t)1 << 25;  // 33,554,432 particles
-constexpr int64_t kScanTileParticles = 8192;         // particles per scan tile (build.cu)
-constexpr int64_t kScanWords = kNoAllocMaxN / kScanTileParticles + 2;
-constexpr int64_t kStatusWords = 8;                  // 16 int32 status words
+// the scan over N + 1 counts needs scan_tmp_words(N + 1) words; the array holds that for the
+// largest N it accepts
+constexpr int64_t kScanWords = rcb::scan_tmp_words(kNoAllocMaxN + 1);
+constexpr int64_t kStatusWords = 8;  // 16 int32 status words
 constexpr int64_t kScratchWords = kScanWords + kStatusWords;
 
 // The static scratch (about 33 KB).  In host code this name is only a stand-in for the symbol;
@@ -30,7 +32,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 int64_t *g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the static scratch on the current device, looked up once per device.
+// Device address of the static scratch on the current device, looked up once per device and kept
+// for the life of the process.  This assumes the device's primary context stays alive: after a
+// cudaDeviceReset the cached address is stale and must not be used (the library does not reset
+// devices itself).
 int scratch_for_current_device(int64_t **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RCB_ERR_CUDA;

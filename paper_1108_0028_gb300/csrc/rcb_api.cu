@@ -88,7 +88,7 @@ void for_each_array(rcb_tree *t, F f) {
                   (void **)&t->narrive, (void **)&t->roots, (void **)&t->chunks, (void **)&t->cell_chunk0,
                   (void **)&t->chunk_part, (void **)&t->sinks, (void **)&t->sink_of_leaf, (void **)&t->near_nr,
                   (void **)&t->near_nn, (void **)&t->far_n, (void **)&t->near_list, (void **)&t->far_list,
-                  (void **)&t->coef, (void **)&t->coef32, (void **)&t->nb_count, (void **)&t->scan_tmp, (void **)&t->tnear_off,
+                  (void **)&t->coef, (void **)&t->coef32, (void **)&t->nb_count, (void **)&t->nb_tmp, (void **)&t->nb_tstart, (void **)&t->nb_cursor, (void **)&t->nb_long, (void **)&t->scan_tmp, (void **)&t->tnear_off,
                   (void **)&t->tnear_sink, (void **)&t->tfar_off, (void **)&t->tfar_sink, (void **)&t->adj,
                   (void **)&t->dens_hl, (void **)&t->ones, (void **)&t->cand_list, (void **)&t->cand_far,
                   (void **)&t->cand_n, (void **)&t->mps_hist, (void **)&t->mps_prefix, (void **)&t->mps_rank};
@@ -104,6 +104,7 @@ void release_arrays(rcb_tree *t) {
     t->cap_L = 0;
     t->cap_near = t->cap_far = 0;
     t->cap_lists_near = t->cap_lists_far = 0;
+    t->cap_tmp = 0;
 }
 
 int allocate_arrays(rcb_tree *t, int64_t N, int L) {
@@ -171,6 +172,9 @@ int allocate_arrays(rcb_tree *t, int64_t N, int L) {
     A((void **)&t->coef, 20 * nl * sizeof(double));
     A((void **)&t->coef32, 20 * nl * sizeof(float));
     A((void **)&t->nb_count, (capN + 1) * sizeof(int64_t));
+    A((void **)&t->nb_tstart, capN * sizeof(int64_t));
+    A((void **)&t->nb_cursor, sizeof(unsigned long long));
+    A((void **)&t->nb_long, capN * sizeof(int2));
     A((void **)&t->scan_tmp, (size_t)scan_tmp_bytes(std::max<int64_t>(capN + 1, nl)) + 256);
     if (!ok) return RCB_ERR_ALLOC;
     t->cap_N = capN;

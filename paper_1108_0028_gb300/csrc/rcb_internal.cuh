@@ -17,6 +17,9 @@ constexpr int kTcta = 1024;        // largest cell whose subtree one CTA builds 
 constexpr int kCtaThreads = 256;    // threads of that CTA
 constexpr int kChunk = 2048;        // particles per chunk in the level passes over large cells
 constexpr int kChunkThreads = 256;
+constexpr int64_t kScanTileElems = 8192;  // elements per tile of the device-wide scans (build.cu)
+// int64 words of scratch a scan over n elements needs (its per-tile sums and two spare words)
+constexpr int64_t scan_tmp_words(int64_t n) { return (n + kScanTileElems - 1) / kScanTileElems + 2; }
 
 // Device status words (int32), zeroed at the start of each build.
 enum StatusWord {
@@ -29,10 +32,11 @@ enum StatusWord {
     ST_NCHUNKS = 6,    // chunks of the current level pass
     ST_NSINKS = 7,     // non-empty ll-cells
     ST_NBFALLBACK = 8, // neighbour decisions taken in FP64
+    ST_NBLONG = 9,     // passes of sink particles with a neighbour row longer than its buffer slice
     ST_OUTSIDE = 10,   // particles outside their ll-cell (tree integrity check)
     ST_NWORDS = 16
 };
-enum ErrBits { ERRBIT_ARG = 1, ERRBIT_LIMIT = 2, ERRBIT_FIXED = 4, ERRBIT_STATE = 8 };
+enum ErrBits { ERRBIT_ARG = 1, ERRBIT_LIMIT = 2, ERRBIT_FIXED = 4, ERRBIT_STATE = 8, ERRBIT_NBTMP = 16 };
 
 // ------------------------------------------------------------------------------------------
 // Exact helpers.
@@ -261,6 +265,16 @@ struct rcb_tree {
     double *coef;    // [nsinks][20] far-field Taylor coefficients
     float *coef32;   // their float32 values (mixed form)
     int64_t *nb_count;
+    // neighbour rows staged by the fused near field or the standalone pass: a compact buffer of
+    // sorted rows (original indices), each particle's row start in it (by original index), the
+    // buffer's fill cursor, and the queue of passes whose rows did not fit
+    int32_t *nb_tmp;
+    int64_t cap_tmp;
+    int64_t *nb_tstart;
+    unsigned long long *nb_cursor;
+    int2 *nb_long;
+    int nb_nlong;   // queued passes (after the last count)
+    int nb_tmp_ok;  // 1 if every row that fitted its slice is in nb_tmp
     void *scan_tmp;
     int64_t cap_scan;
     int64_t nb_total;
@@ -316,7 +330,11 @@ int density(rcb_tree *t, const int64_t *offsets, const int32_t *idx, double *rho
 // neighbours.cu
 int neighbour_counts(rcb_tree *t, int64_t *counts, int *status);  // count pass into caller memory
 int neighbours(rcb_tree *t, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *needed);
-int count_neighbours(rcb_tree *t);        // counts and offsets (nb_count) unless valid
+int count_neighbours(rcb_tree *t);        // counts, offsets (nb_count) and staged rows unless valid
+struct RowOut;
+RowOut row_out(rcb_tree *t);              // where staged neighbour rows go (nb_rows.cuh)
+int ensure_nb_tmp(rcb_tree *t);           // staging buffer of neighbour rows (grown from the last total)
+int reset_nb_rows(rcb_tree *t);           // before a pass that stages rows: cursor, queue and flags
 int scan_neighbour_counts(rcb_tree *t);   // nb_count: counts by original index -> offsets
 int fetch_neighbour_total(rcb_tree *t);   // total and long-row count to the host; counts valid
 // gravity.cu
