@@ -240,26 +240,25 @@ __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_
 constexpr int kNearWarps = 8;   // warps per block
 constexpr int kNearMinBlocks = 2;
 constexpr int kNearTile = 256;  // staged source slots per warp (even)
-constexpr int kNearPad = 4;     // slots kept free for padding the regions to even length
+constexpr int kNearPad = 2;     // slots kept free for padding the regions to even length
 constexpr int kFoldIters = 16;  // source pairs summed in float32 before a compensated fold
 
-// Shared memory of one warp: per source pair k, A[k], B[k], C[k] (see above); with the neighbour
-// rows (NB) also D[k] = (original indices, unused), the row buffer (nb_rows.cuh) and the slot of
-// each sink particle of the pass in the current tile (-1 if not staged there).
+// Shared memory of one warp: per source pair k, A[k], B[k], C[k] = (h_2k, h_2k+1, original
+// indices); with the neighbour rows (NB) also D[k] = (sorted indices, unused), the row buffer
+// (nb_rows.cuh), per-lane counts and the slot of each sink particle of the pass in the current
+// tile (-1 if not staged there).
 template <bool NB>
 struct NearSmem {
     static constexpr int H = kNearTile / 2;  // source pairs per tile
     static constexpr size_t bytes =
-        (size_t)H * (NB ? 4 : 3) * sizeof(float4) + (NB ? kRowBuf * sizeof(int32_t) + 32 * sizeof(int) : 0) + 32 * sizeof(int);
+        (size_t)H * (NB ? 4 : 3) * sizeof(float4) + (NB ? kRowBuf * sizeof(int32_t) + 64 * sizeof(int) : 0);
     float4 *P;      // A[H], B[H], C[H], D[H] (NB)
     int32_t *rows;  // NB: row buffer
-    int *rowcnt;    // NB: [32] entries of each row of the pass so far
-    int *self;
+    int *rowcnt;    // NB: [32] per-lane counts when a pass is handed over, then [32] dummy words
     __device__ NearSmem(unsigned char *p) {
         P = reinterpret_cast<float4 *>(p);
         rows = reinterpret_cast<int32_t *>(P + (NB ? 4 : 3) * H);
         rowcnt = rows + (NB ? kRowBuf : 0);
-        self = rowcnt + (NB ? 32 : 0);
     }
     __device__ __forceinline__ float4 a(int k) const { return P[k]; }
     __device__ __forceinline__ float4 b(int k) const { return P[k + H]; }
@@ -275,17 +274,15 @@ struct NearSmem {
         q[4 * H + u] = -dz;
         q[4 * H + 2 + u] = -m;
         q[8 * H + u] = h;
-        q[8 * H + 2 + u] = __int_as_float(idx);
-        if (NB) reinterpret_cast<int *>(q)[12 * H + u] = oidx;
+        q[8 * H + 2 + u] = __int_as_float(oidx);
+        if (NB) reinterpret_cast<int *>(q)[12 * H + u] = idx;
     }
 };
 
-// Where the next tile starts: position t0 of the concatenated source sequence (cells in list
-// order: the reachable ones, then the others) lies in the batch of up to 32 near cells that
-// begins at list entry k0, whose first particle is at position pos.
+// Where the next tile starts: list entry k0 of the sink's near list (the reachable cells come
+// first, then the others), of whose particles the first off0 are already staged.
 struct NearCursor {
-    int k0;
-    int64_t pos, t0;
+    int k0, off0;
 };
 
 // One staged tile: close sources in slots [0, nclose), of which [0, ncc) come from neighbour
@@ -297,15 +294,18 @@ struct NearTile {
 };
 
 // Stage the next tile of sink s (cell A, sorted particles [fA, fA + nA), this pass the P
-// particles from a0).  For 32 cells at a time lanes describe the cells (first particle, count,
-// centre-of-mass offset); then every lane takes two slots per round (both gathers in flight
-// together), finds the slot's cell, forms the particle's float32 offset from the sink's centre of
-// mass and stores it, close sources from the front of the tile and far ones from the back.  The
-// cell offset o is the double-float difference of the two centres of mass: it differs from the
-// float64 difference by at most 2u |dCOM| + 3 2^-48 (|COM_A|_1 + |COM_B|_1) per component
-// (u = 2^-24).  With NB, wmax gets the tile's largest w = |o|_1 + |d_b|_1 + 2^-20 (|COM_A|_1 +
-// |COM_B|_1) over candidate sources: the last term makes the representation error's share of
-// the d^2 error at most 6 2^-28 F, well inside the neighbour band.
+// particles from a0).  A tile is one batch of up to 32 near cells, all from the same part of the
+// list (reachable or not), as many whole cells as fit in kNearTile - kNearPad slots (part of one
+// cell if a single cell is larger).  Lanes describe the cells (first particle, count, centre-of-
+// mass offset), then every lane issues the gathers of half its slots (lane + 32 u) before using
+// any of them, so that a tile costs three rounds of memory latency; then each slot's float32
+// offset from the sink's centre of mass is formed and stored, close sources from the front of the
+// tile and far ones from the back.  The cell offset o is the double-float difference of the two
+// centres of mass: it differs from the float64 difference by at most 2u |dCOM| + 3 2^-48
+// (|COM_A|_1 + |COM_B|_1) per component (u = 2^-24).  With NB, wmax gets the tile's largest
+// w = |o|_1 + |d_b|_1 + 2^-20 (|COM_A|_1 + |COM_B|_1) over candidate sources: the last term makes
+// the representation error's share of the d^2 error at most 6 2^-28 F, well inside the neighbour
+// band.
 //
 // Far sources: with R_A the largest |d_a| and H_A the largest h_a of the sink's particles, a
 // source b with |d_b| > (R_A + X_b)(1 + 2^-10) has r_ab >= |d_b| - |d_a| > X_b for every sink
@@ -316,113 +316,100 @@ struct NearTile {
 template <bool NB>
 __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0, int P, int nlist, int nr,
                                      NearCursor &cur, const NearSmem<NB> &sm, float RA, float HA, float &wmax) {
+    constexpr int kCap = kNearTile - kNearPad;
+    constexpr int kU = (kCap + 31) / 32;  // slots per lane
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)s * c.cap_near;
-    const float2 a0f = c.ncomdf[3 * (int64_t)A], a1f = c.ncomdf[3 * (int64_t)A + 1], a2f = c.ncomdf[3 * (int64_t)A + 2];
-    const float aabs = fabsf(a0f.x) + fabsf(a1f.x) + fabsf(a2f.x);
-    const int64_t t0 = cur.t0;
-    const int64_t tend = t0 + (kNearTile - kNearPad);
-    sm.self[lane] = -1;
-    __syncwarp();
-    float wl = 0.f;
-    int nclose = 0, nfar = 0, ncc = -1;
-    bool full = false;
-    while (cur.k0 < nlist) {
-        const int kend = cur.k0 < nr ? nr : nlist;  // the batch stays within one of the two parts
-        const int k = cur.k0 + lane;
-        int f = 0, n = 0;
-        float ox = 0.f, oy = 0.f, oz = 0.f, ow = 0.f;
-        if (k < kend) {
-            const int B = near_entry(c, base, nr, k);
-            f = c.nfirst[B];
-            n = c.ncount[B];
-            const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1],
-                         b2 = c.ncomdf[3 * (int64_t)B + 2];
-            ox = (b0.x - a0f.x) + (b0.y - a0f.y);
-            oy = (b1.x - a1f.x) + (b1.y - a1f.y);
-            oz = (b2.x - a2f.x) + (b2.y - a2f.y);
-            if (NB) ow = 0x1p-20f * (aabs + (fabsf(b0.x) + fabsf(b1.x) + fabsf(b2.x)));
-        }
-        const bool cand = cur.k0 < nr;
-        const int excl = warp_excl_scan(n);
-        const int total = __shfl_sync(0xffffffffu, excl + n, 31);
-        const int64_t pos = cur.pos;
-        const int64_t hi = pos + total < tend ? pos + total : tend;
-        for (int64_t j0 = pos > t0 ? pos : t0; j0 < hi; j0 += 64) {
-            int b[2], cl[2];
-            float cx[2], cy[2], cz[2], cw[2];
-            bool act[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int rel = (int)(j0 + 32 * u + lane - pos);
-                cl[u] = warp_run_of(excl, n, (int)(j0 + 32 * u - pos));
-                b[u] = __shfl_sync(0xffffffffu, f, cl[u]) + rel - __shfl_sync(0xffffffffu, excl, cl[u]);
-                cx[u] = __shfl_sync(0xffffffffu, ox, cl[u]);
-                cy[u] = __shfl_sync(0xffffffffu, oy, cl[u]);
-                cz[u] = __shfl_sync(0xffffffffu, oz, cl[u]);
-                cw[u] = NB ? __shfl_sync(0xffffffffu, ow, cl[u]) : 0.f;
-                act[u] = j0 + 32 * u + lane < hi;
-            }
-            float4 pb[2];
-            float hb[2];
-            int ob[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                pb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                hb[u] = 0.f;
-                ob[u] = 0;
-                if (act[u]) {
-                    pb[u] = c.p32[b[u]];
-                    hb[u] = c.h32[b[u]];
-                    if (NB) ob[u] = c.pidx[b[u]];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const float vx = cx[u] + pb[u].x, vy = cy[u] + pb[u].y, vz = cz[u] + pb[u].z;
-                const float d2 = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
-                const float X = NB ? fmaxf(HA + hb[u], HA + HA) : HA + hb[u];
-                const float R = (RA + X) * (1.0f + 0x1p-10f);
-                const bool far = d2 > R * R;
-                const unsigned mc = __ballot_sync(0xffffffffu, act[u] && !far);
-                const unsigned mf = __ballot_sync(0xffffffffu, act[u] && far);
-                if (act[u]) {
-                    const int at = far ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt);
-                    sm.put(at, vx, vy, vz, pb[u].w, hb[u], b[u], ob[u]);
-                    if (NB) {
-                        if (cand)
-                            wl = fmaxf(wl, (fabsf(cx[u]) + fabsf(cy[u]) + fabsf(cz[u])) + fabsf(pb[u].x) +
-                                               fabsf(pb[u].y) + fabsf(pb[u].z) + cw[u]);
-                        const int i = b[u] - fA - a0;  // a sink particle of this pass?
-                        if (i >= 0 && i < P) sm.self[i] = at;
-                    }
-                }
-                nclose += __popc(mc);
-                nfar += __popc(mf);
-            }
-        }
-        if (pos + total > tend) {  // the tile is full: the next one continues inside this batch
-            full = true;
-            cur.t0 = tend;
-            break;
-        }
-        cur.pos = pos + total;
-        cur.k0 = min(cur.k0 + 32, kend);
-        if (cur.k0 == nr && ncc < 0) {  // all candidates staged: pad the candidate part to even
-            if (nclose & 1) {
-                if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1, -1);
-                ++nclose;
-            }
-            ncc = nclose;
+    if (cur.k0 >= nlist) {
+        __syncwarp();
+        return NearTile{0, 0, 0, true};
+    }
+    const int k0 = cur.k0, kend = k0 < nr ? nr : nlist;  // the tile stays within one part
+    const bool cand = k0 < nr;
+    const int k = k0 + lane;
+    int f = 0, n = 0;
+    float ox = 0.f, oy = 0.f, oz = 0.f, ow = 0.f;
+    if (k < kend) {
+        const int B = near_entry(c, base, nr, k);
+        const float2 a0f = c.ncomdf[3 * (int64_t)A], a1f = c.ncomdf[3 * (int64_t)A + 1],
+                     a2f = c.ncomdf[3 * (int64_t)A + 2];
+        f = c.nfirst[B];
+        n = c.ncount[B];
+        const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1], b2 = c.ncomdf[3 * (int64_t)B + 2];
+        ox = (b0.x - a0f.x) + (b0.y - a0f.y);
+        oy = (b1.x - a1f.x) + (b1.y - a1f.y);
+        oz = (b2.x - a2f.x) + (b2.y - a2f.y);
+        if (NB) ow = 0x1p-20f * ((fabsf(a0f.x) + fabsf(a1f.x) + fabsf(a2f.x)) + (fabsf(b0.x) + fabsf(b1.x) + fabsf(b2.x)));
+        if (lane == 0) {  // the part of the first cell not staged yet
+            f += cur.off0;
+            n -= cur.off0;
         }
     }
-    if (!full) cur.t0 = cur.pos;
-    if (ncc < 0) ncc = cur.k0 < nr ? nclose : 0;
-    if (ncc & 1) {  // the tile ended inside the candidates
-        if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1, -1);
-        ++nclose;
-        ++ncc;
+    int excl = warp_excl_scan(n);
+    // whole cells that fit; if none, the first cell's next kCap particles
+    const unsigned fit = __ballot_sync(0xffffffffu, k < kend && excl + n <= kCap);
+    const int nfit = __popc(fit);  // cells fit from lane 0 on: fit = 2^nfit - 1
+    int nslots;
+    if (nfit > 0) {
+        nslots = __shfl_sync(0xffffffffu, excl + n, nfit - 1);
+        if (lane >= nfit) n = 0;
+        cur.k0 = k0 + nfit;
+        cur.off0 = 0;
+    } else {
+        nslots = kCap;
+        if (lane > 0) n = 0;
+        if (lane == 0) n = kCap;
+        cur.off0 += kCap;
+    }
+    excl = warp_excl_scan(n);
+    // the slots in two halves of kU / 2 per lane: the gathers of a half are all issued before any
+    // is used
+    constexpr int kH = kU / 2;
+    float wl = 0.f;
+    int nclose = 0, nfar = 0;
+#pragma unroll 1
+    for (int hh = 0; hh < 2; ++hh) {
+        int b[kH], cl[kH], ob[kH];
+        float4 pb[kH];
+        float hb[kH];
+#pragma unroll
+        for (int u = 0; u < kH; ++u) {
+            const int r0 = 32 * (hh * kH + u), r = r0 + lane;
+            cl[u] = warp_run_of(excl, n, r0);
+            b[u] = __shfl_sync(0xffffffffu, f, cl[u]) + r - __shfl_sync(0xffffffffu, excl, cl[u]);
+            pb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            hb[u] = 0.f;
+            ob[u] = 0;
+            if (r < nslots) {
+                pb[u] = c.p32[b[u]];
+                hb[u] = c.h32[b[u]];
+                if (NB) ob[u] = c.pidx[b[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kH; ++u) {
+            const bool act = 32 * (hh * kH + u) + lane < nslots;
+            const float cx = __shfl_sync(0xffffffffu, ox, cl[u]), cy = __shfl_sync(0xffffffffu, oy, cl[u]),
+                        cz = __shfl_sync(0xffffffffu, oz, cl[u]);
+            const float cw = NB ? __shfl_sync(0xffffffffu, ow, cl[u]) : 0.f;
+            const float vx = cx + pb[u].x, vy = cy + pb[u].y, vz = cz + pb[u].z;
+            const float d2 = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+            const float X = NB ? fmaxf(HA + hb[u], HA + HA) : HA + hb[u];
+            const float R = (RA + X) * (1.0f + 0x1p-10f);
+            const bool far = d2 > R * R;
+            const unsigned mc = __ballot_sync(0xffffffffu, act && !far);
+            const unsigned mf = __ballot_sync(0xffffffffu, act && far);
+            if (act) {
+                const int at = far ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt);
+                sm.put(at, vx, vy, vz, pb[u].w, hb[u], b[u], ob[u]);
+                if (NB && cand)
+                    wl = fmaxf(wl, (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb[u].x) + fabsf(pb[u].y) +
+                                       fabsf(pb[u].z) + cw);
+            }
+            nclose += __popc(mc);
+            nfar += __popc(mf);
+        }
     }
     if (nclose & 1) {
         if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1, -1);
@@ -437,7 +424,7 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0
         wmax = wl;
     }
     __syncwarp();
-    return NearTile{nclose, ncc, nfar, !full};
+    return NearTile{nclose, cand ? nclose : 0, nfar, cur.k0 >= nlist};
 }
 
 // Lane state of the mixed near field: the lane's sink particle (float32 offset from the sink's
@@ -448,7 +435,9 @@ struct NearLane {
     float h2, B;   // (2 h_a)^2 and the half width of the neighbour band
     float2 In[4];
     float sum[4], comp[4];
-    int cnt;  // neighbours counted
+    int32_t *wp;     // NB: where the lane's next row entry goes (entry e of its part at part[e stride])
+    int32_t *dummy;  // NB: the lane's scratch word for entries not kept
+    int nsub, capsub, stride;
     int nfb;  // float64 neighbour decisions taken
 };
 
@@ -545,70 +534,76 @@ __device__ __noinline__ int nb_settle(const double *px, const double *py, const 
     return dist2_rn(px[a], py[a], pz[a], px[b], py[b], pz[b]) < __dmul_rn(s2, s2) ? 1 : 0;
 }
 
-// The pair loops of one staged tile for the lane's sink particle a (stream j of S; lanes with
-// active false hold no particle of the pass).  Each loop runs in blocks of kFoldIters source
-// pairs, folded into the compensated totals after each block.  With NB the candidate part of the
-// close region also tests every pair for |r_a - r_b| < 2 h_a: by the sign of d^2 - (2h)^2, exact
-// outside the band |d^2 - (2h)^2| <= B; a block in which some pair fell inside the band is gone
-// through again with the float64 test deciding those pairs.  A block's neighbours are flagged in
-// a bit mask and their original indices appended to the lane's row once per block (row_append);
-// the pair of a particle with itself (slot self) is skipped.
+// Append original index o to the lane's part of its row (entries past its capacity are counted
+// only: the row is then recomputed by the direct fill).
+__device__ __forceinline__ void sub_push(NearLane &L, bool nb, int o) {
+    const bool st = nb && L.nsub < L.capsub;
+    *(st ? L.wp : L.dummy) = o;  // branch-free: a store to the lane's dummy word when not kept
+    L.wp += st ? L.stride : 0;
+    L.nsub += nb ? 1 : 0;
+}
+
+// The float64 decisions of one block of loop steps (pairs k0, k0 + S, ... below kend, at most
+// kFoldIters) for the pairs inside the band |d^2 - (2h)^2| <= B, gone through again after the
+// block when its smallest |d^2 - (2h)^2| fell inside (rare).  The pair of a particle with itself
+// is kept, as the fast path keeps it (see k_near_mixed).
+template <bool NB>
+__device__ __forceinline__ void near_band(const GCtx &c, const NearSmem<NB> &sm, NearLane &L, int a, int k0, int kend,
+                                       int S) {
+    const float2 nh2 = make_float2(-L.h2, -L.h2);
+    int k = k0;
+    for (int t = 0; t < kFoldIters && k < kend; ++t, k += S) {
+        float2 dx, dy, dz;
+        const float2 e = __fadd2_rn(near_r2(L, sm.a(k), sm.b(k), dx, dy, dz), nh2);
+        const float4 c4 = sm.c(k);
+        const int4 d4 = sm.D()[k];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (fabsf(u ? e.y : e.x) <= L.B) {
+                const int b = u ? d4.y : d4.x;
+                const bool nb = b == a || nb_settle(c.px, c.py, c.pz, c.ph, a, b) != 0;
+                sub_push(L, nb, __float_as_int(u ? c4.w : c4.z));
+                ++L.nfb;
+            }
+        }
+    }
+}
+
+// The pair loops of one staged tile for the lane's sink particle a (stream j of S).  Each loop
+// runs in blocks of kFoldIters source pairs, folded into the compensated totals after each
+// block.  With NB, in a tile of neighbour candidates (reachable cells) the close loop also tests
+// every pair for |r_a - r_b| < 2 h_a: by the sign of d^2 - (2h)^2 where |d^2 - (2h)^2| > B (exact
+// there), by the float64 test inside the band; each neighbour's original index goes to the lane's
+// part of the row.
 template <bool NB>
 __device__ __forceinline__ void near_tile_lane(const GCtx &c, const NearSmem<NB> &sm, const NearTile &tl, int j, int S,
-                                               bool active, int a, int i, int self, int32_t *rowp, int rc,
-                                               NearLane &L) {
-    const int pcc = tl.ncc >> 1, pc = tl.nclose >> 1;
+                                               int a, NearLane &L) {
+    const int pc = tl.nclose >> 1;
+    const bool nbtile = NB && tl.ncc > 0;  // a tile of neighbour candidates (the same for the whole warp)
+    const float2 nh2 = make_float2(-L.h2, -L.h2);
+    const float nB = -L.B;
     int k = j;
-    if (NB) {
-        const float2 nh2 = make_float2(-L.h2, -L.h2);
-        const int nst = (pcc + S - 1) / S;  // loop steps of the warp (stream 0 the longest)
-        for (int t0 = 0; t0 < nst; t0 += kFoldIters) {
-            const int kb = j + t0 * S;
-            unsigned mask = 0;
-            float bandmin = 3e38f;
-            if (active) {
-                int kq = kb;
-                for (int t = 0; t < kFoldIters && kq < pcc; ++t, kq += S) {
-                    const float2 r2 = near_pair_close(L, sm.a(kq), sm.b(kq), sm.c(kq));
-                    const float2 e = __fadd2_rn(r2, nh2);  // d^2 - (2h)^2
-                    const float ex = fabsf(e.x), ey = fabsf(e.y);
-                    bandmin = fminf(bandmin, fminf(ex, ey));
-                    mask |= (unsigned)(e.x < 0.f && ex > L.B && 2 * kq != self) << (2 * t);
-                    mask |= (unsigned)(e.y < 0.f && ey > L.B && 2 * kq + 1 != self) << (2 * t + 1);
-                }
-                near_fold(L);
-            }
-            if (__any_sync(0xffffffffu, bandmin <= L.B) && active) {  // rare
-                int kq = kb;
-                for (int t = 0; t < kFoldIters && kq < pcc; ++t, kq += S) {
-                    float2 dx, dy, dz;
-                    const float2 r2 = near_r2(L, sm.a(kq), sm.b(kq), dx, dy, dz);
-                    const float2 e = __fadd2_rn(r2, nh2);
-                    const float4 c4 = sm.c(kq);
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        if (fabsf(u ? e.y : e.x) <= L.B) {
-                            if (nb_settle(c.px, c.py, c.pz, c.ph, a, __float_as_int(u ? c4.w : c4.z)))
-                                mask |= 1u << (2 * t + u);
-                            ++L.nfb;
-                        }
-                    }
-                }
-            }
-            if (mask) row_append(rowp, rc, sm.rowcnt + i, mask, kb, S, sm.D());
-        }
-        k = j + S * ((max(pcc - j, 0) + S - 1) / S);  // the stream's first pair at or after pcc
-    }
-    if (!active) return;
     while (k < pc) {
-#pragma unroll 2
-        for (int t = 0; t < kFoldIters && k < pc; ++t, k += S) near_pair_close(L, sm.a(k), sm.b(k), sm.c(k));
+        const int kb = k;
+        float bandmin = 3e38f;
+#pragma unroll 1
+        for (int t = 0; t < kFoldIters && k < pc; ++t, k += S) {
+            const float4 c4 = sm.c(k);
+            const float2 r2 = near_pair_close(L, sm.a(k), sm.b(k), c4);
+            if (nbtile) {
+                const float2 e = __fadd2_rn(r2, nh2);  // d^2 - (2h)^2
+                sub_push(L, e.x < nB, __float_as_int(c4.z));
+                sub_push(L, e.y < nB, __float_as_int(c4.w));
+                bandmin = fminf(bandmin, fminf(fabsf(e.x), fabsf(e.y)));
+            }
+        }
         near_fold(L);
+        if (nbtile && bandmin <= L.B) near_band<NB>(c, sm, L, a, kb, pc, S);
     }
     const int pf = kNearTile >> 1;
     k = ((kNearTile - tl.nfar) >> 1) + j;
     while (k < pf) {
-#pragma unroll 4
+#pragma unroll 2
         for (int t = 0; t < kFoldIters && k < pf; ++t, k += S) near_pair_newton(L, sm.a(k), sm.b(k));
         near_fold(L);
     }
@@ -619,8 +614,9 @@ __device__ __forceinline__ void near_tile_lane(const GCtx &c, const NearSmem<NB>
 // B = 2^-19 ((W + |d_a|_1)^2 + (2h)^2) + 1e-30, W the tile's largest w (see stage_near_mixed):
 // the input and offset roundings, the squares and sums, the rounding of d^2 - (2h)^2 and of
 // (2h)^2 stay below 16 u F, half of B; inside the band the float64 test (the definition) decides.
-// The pair of a particle with itself (d^2 = 0) counts whenever (2h)^2 > B and is then taken off
-// the count; inside the band the float64 test excludes it by index.
+// The pair of a particle with itself (d^2 = 0) is kept in the staged row (below the band, or by
+// index inside it): every staged row holds the particle itself once, which the copy into the
+// CSR drops.
 template <bool NB>
 __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(GCtx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -670,25 +666,23 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
                 L.sum[q] = 0.f;
                 L.comp[q] = 0.f;
             }
-            L.cnt = 0;
             L.nfb = 0;
-            const int rc = NB ? kRowBuf / P : 0;
-            int32_t *rowp = sm.rows + i * rc;
-            if (NB) {
-                if (lane < P) sm.rowcnt[lane] = 0;
-                __syncwarp();
-            }
-            NearCursor cur{0, 0, 0};
+            // NB: lane (i, j) keeps its part of row i as column g = i S + j of the row buffer seen as
+            // rows of P S entries (simultaneous appends of different lanes fall in different banks)
+            L.stride = P * S;
+            L.capsub = NB ? kRowBuf / L.stride : 0;
+            L.wp = sm.rows + (i * S + j);
+            L.dummy = sm.rowcnt + 32 + lane;
+            L.nsub = 0;
+            NearCursor cur{0, 0};
             for (;;) {
                 float wmax = 0.f;
                 const NearTile tl = stage_near_mixed<NB>(c, s, A, fA, a0, P, nlist, nr, cur, sm, RA, HA, wmax);
-                int self = -1;
                 if (NB) {
                     const float F = wmax + (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z));
                     L.B = fmaf(F, F, L.h2) * 0x1p-19f + 1e-30f;
-                    self = sm.self[i];
                 }
-                near_tile_lane<NB>(c, sm, tl, j, S, active, a, i, self, rowp, rc, L);
+                if (active) near_tile_lane<NB>(c, sm, tl, j, S, a, L);
                 __syncwarp();
                 if (tl.last) break;
             }
@@ -733,11 +727,12 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
                 c.acc[3 * (int64_t)o + 1] = __dadd_rn((double)ts[1], (double)tc[1]) + (double)af[1];
                 c.acc[3 * (int64_t)o + 2] = __dadd_rn((double)ts[2], (double)tc[2]) + (double)af[2];
                 if (c.pot) c.pot[o] = __dadd_rn((double)ts[3], (double)tc[3]) + (double)phf - (double)self_pot;
-                if (NB) c.nb_counts[o] = sm.rowcnt[lane];
             }
             nfb_total += L.nfb;
             __syncwarp();
-            if (NB) rows_finish(c.ro, sm.rows, rc, P, lane < P ? sm.rowcnt[lane] : 0, lane < P ? c.pidx[a] : 0, s, a0);
+            if (NB)
+                rows_finish_parts(c.ro, c.nb_counts, sm.rows, sm.rowcnt, L.capsub, P, S, active ? L.nsub : 0,
+                                  lane < P ? c.pidx[a] : 0, s, a0);
         }
     }
     if (NB) {

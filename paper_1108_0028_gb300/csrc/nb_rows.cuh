@@ -3,9 +3,11 @@
 // sorting networks that order a row by original index, and the hand-off of a finished pass of
 // rows to the compact staging buffer from which rcb_neighbours copies them into the caller's CSR.
 //
-// Layout: the P rows of a pass share a buffer of kRowBuf entries, row i at [i rc, i rc + rc) with
-// rc = kRowBuf / P.  Entries beyond rc are counted but not stored; such a row is "long" and its
-// pass is queued for the direct fill (which recomputes it straight into the CSR).
+// A staged row holds the particle's neighbours and the particle itself (once, in any order); the
+// copy into the CSR sorts the row by original index and drops the particle itself.  The row
+// buffer of a pass has kRowBuf entries, split into equal slices (one per row, or one per lane
+// holding a part of a row).  Entries beyond a slice are counted but not stored; such a row is
+// "long" and its pass is queued for the direct fill (which recomputes it straight into the CSR).
 #pragma once
 
 #include <climits>
@@ -178,10 +180,16 @@ __device__ inline void warp_sort_inplace(int32_t *p, int n) {
 }
 
 // Sort rows src[rs[i] .. rs[i] + len[i]) (shared or global memory) and store each at dst + off[i],
-// for the rows i < P with len[i] >= 0 (negative: skip).  Two rows of at most 64 entries at a time, one
-// per half-warp; longer rows over the whole warp (in place in src beyond 128 entries).  rs, len
-// and off are read with a shuffle from lane i.
-__device__ inline void rows_sort_store(int32_t *src, int64_t rs_l, int len_l, int64_t off_l, int32_t *dst, int P) {
+// for the rows i < P with len[i] >= 0 (negative: skip); every entry equal to self[i] is left out
+// (a staged row holds its own particle once, so the stored row is one shorter).  Four rows of
+// at most 64 entries at a time, one per group of 8 lanes; longer rows over the whole warp (in
+// place in src beyond 128 entries).  rs, len, off and self are read with a shuffle from lane i.
+__device__ __forceinline__ void store_dropping(int32_t *dst, int64_t o, int e, int n, int32_t v, int32_t self) {
+    if (e < n && v != self) dst[o + e - (v > self ? 1 : 0)] = v;
+}
+
+__device__ inline void rows_sort_store(int32_t *src, int64_t rs_l, int len_l, int64_t off_l, int32_t self_l, int32_t *dst,
+                                       int P) {
     const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
     int i = 0;
     while (i < P) {
@@ -191,6 +199,7 @@ __device__ inline void rows_sort_store(int32_t *src, int64_t rs_l, int len_l, in
         const int nr = i + g < P ? nr0 : -1;
         const int64_t rs = __shfl_sync(0xffffffffu, rs_l, r);
         const int64_t o = __shfl_sync(0xffffffffu, off_l, r);
+        const int32_t sf = __shfl_sync(0xffffffffu, self_l, r);
         const int nmax = __reduce_max_sync(0xffffffffu, nr);
         if (nmax <= 64) {
             const int n = max(nr, 0);
@@ -200,24 +209,21 @@ __device__ inline void rows_sort_store(int32_t *src, int64_t rs_l, int len_l, in
                 for (int q = 0; q < 2; ++q) v[q] = q * 8 + gl < n ? src[rs + q * 8 + gl] : INT32_MAX;
                 seg8_sort<2>(v);
 #pragma unroll
-                for (int q = 0; q < 2; ++q)
-                    if (q * 8 + gl < n) dst[o + q * 8 + gl] = v[q];
+                for (int q = 0; q < 2; ++q) store_dropping(dst, o, q * 8 + gl, n, v[q], sf);
             } else if (nmax <= 32) {
                 int32_t v[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) v[q] = q * 8 + gl < n ? src[rs + q * 8 + gl] : INT32_MAX;
                 seg8_sort<4>(v);
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q * 8 + gl < n) dst[o + q * 8 + gl] = v[q];
+                for (int q = 0; q < 4; ++q) store_dropping(dst, o, q * 8 + gl, n, v[q], sf);
             } else {
                 int32_t v[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) v[q] = q * 8 + gl < n ? src[rs + q * 8 + gl] : INT32_MAX;
                 seg8_sort<8>(v);
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (q * 8 + gl < n) dst[o + q * 8 + gl] = v[q];
+                for (int q = 0; q < 8; ++q) store_dropping(dst, o, q * 8 + gl, n, v[q], sf);
             }
             i += 4;
             continue;
@@ -226,6 +232,7 @@ __device__ inline void rows_sort_store(int32_t *src, int64_t rs_l, int len_l, in
         const int n = __shfl_sync(0xffffffffu, len_l, i);
         const int64_t r0 = __shfl_sync(0xffffffffu, rs_l, i);
         const int64_t o0 = __shfl_sync(0xffffffffu, off_l, i);
+        const int32_t s0 = __shfl_sync(0xffffffffu, self_l, i);
         if (n > 0) {
             if (n <= 128) {
                 int32_t v[4];
@@ -233,11 +240,11 @@ __device__ inline void rows_sort_store(int32_t *src, int64_t rs_l, int len_l, in
                 for (int q = 0; q < 4; ++q) v[q] = q * 32 + lane < n ? src[r0 + q * 32 + lane] : INT32_MAX;
                 warp_sort<4>(v);
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q * 32 + lane < n) dst[o0 + q * 32 + lane] = v[q];
+                for (int q = 0; q < 4; ++q) store_dropping(dst, o0, q * 32 + lane, n, v[q], s0);
             } else {
                 warp_sort_inplace(src + r0, n);
-                for (int q = lane; q < n; q += 32) dst[o0 + q] = src[r0 + q];
+                __syncwarp();
+                for (int q = lane; q < n; q += 32) store_dropping(dst, o0, q, n, src[r0 + q], s0);
             }
         }
         __syncwarp();
@@ -274,6 +281,55 @@ __device__ inline void rows_finish(const RowOut &ro, int32_t *rows, int rc, int 
             for (int e = lane; e < n; e += 32) ro.tmp[d + e] = rows[q * rc + e];
         }
     }
+    __syncwarp();
+}
+
+// Hand a finished pass over when every lane (i, j) of the P S lanes holding a sink particle kept
+// its part of row i as column g = i S + j of the row buffer seen as rows of P S entries, cap
+// entries at most (nsub of them counted): part lengths go
+// through cnt (shared memory, 32 entries); lane l < P holds row l's particle (original index o).
+// The parts of every row that fits are copied in order to the staging buffer (one reservation
+// per pass); counts[o] receives the row length less the particle itself.
+static __device__ __noinline__ void rows_finish_parts(const RowOut &ro, int64_t *counts, const int32_t *rows, int *cnt, int cap,
+                                         int P, int S, int nsub, int o, int s, int a0) {
+    const int lane = threadIdx.x & 31;
+    const int i = lane % P, j = lane / P;
+    const int PS = P * S;
+    if (j < S) cnt[i * S + j] = nsub;
+    __syncwarp();
+    int tot = 0;
+    bool over = false;
+    if (lane < P)
+        for (int jj = 0; jj < S; ++jj) {
+            const int v = cnt[lane * S + jj];
+            tot += v;
+            over = over || v > cap;
+        }
+    // the parts, in slice order g = lane
+    const bool gover = __shfl_sync(0xffffffffu, (int)over, min(lane / S, 31)) != 0;
+    const int seglen = lane < PS && !gover ? cnt[lane] : 0;
+    const int exg = warp_excl_scan(seglen);
+    const int T = __shfl_sync(0xffffffffu, exg + seglen, 31);
+    unsigned long long base = 0;
+    if (lane == 0 && T > 0) base = atomicAdd(ro.cursor, (unsigned long long)T);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const bool fits = T == 0 || base + (unsigned long long)T <= (unsigned long long)ro.cap_tmp;
+    if (!fits && lane == 0) atomicOr(&ro.status[ST_ERR], ERRBIT_NBTMP);
+    const int rstart = __shfl_sync(0xffffffffu, exg, min(lane * S, 31));
+    if (lane < P) {
+        ro.tstart[o] = (over || !fits) ? -1 : (int64_t)base + rstart;
+        counts[o] = tot - 1;
+    }
+    if (__any_sync(0xffffffffu, over) && lane == 0) {
+        const int q = atomicAdd(&ro.status[ST_NBLONG], 1);
+        if (q < ro.cap_long) ro.long_q[q] = make_int2(s, a0);
+    }
+    if (fits)
+        for (int g = 0; g < PS; ++g) {  // part g, lanes over its entries
+            const int ng = __shfl_sync(0xffffffffu, seglen, g);
+            const int64_t d = (int64_t)base + __shfl_sync(0xffffffffu, exg, g);
+            for (int e = lane; e < ng; e += 32) ro.tmp[d + e] = rows[e * PS + g];
+        }
     __syncwarp();
 }
 

@@ -92,100 +92,105 @@ struct NbSmem {
     }
 };
 
+// Where the next tile starts: candidate entry k0, of whose particles the first off0 are staged.
 struct NbCursor {
-    int k0;
-    int64_t pos, t0;
+    int k0, off0;
 };
 
-// Stage the next tile: candidate cells in list order, 32 at a time (lanes describe the cells,
-// then take two slots each per round), sources beyond (R_A + 2 H_A)(1 + 2^-10) dropped.  Returns
-// the number staged (padded to even with a far-away source); wmax gets the tile's largest w.
+// Stage the next tile: one batch of up to 32 candidate cells, as many whole cells as fit in
+// kNbTile - 2 slots (part of one cell if a single cell is larger).  Lanes describe the cells,
+// every lane issues the gathers of all its slots before using any of them (two rounds of memory
+// latency per tile), then sources beyond (R_A + 2 H_A)(1 + 2^-10) are dropped and the others
+// stored.  Returns the number stored (padded to even with a far-away source); wmax gets the
+// tile's largest w.
 template <int MODE>
 __device__ int stage_nb(const NbCtx &c, int s, int A, int fA, int a0, int P, int nr, NbCursor &cur,
                         const NbSmem<MODE> &sm, float Rcut, float &wmax, bool &last) {
+    constexpr int kCap = kNbTile - 2;
+    constexpr int kU = (kCap + 31) / 32;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)s * c.cap_near;
-    const float2 a0f = c.ncomdf[3 * (int64_t)A], a1f = c.ncomdf[3 * (int64_t)A + 1], a2f = c.ncomdf[3 * (int64_t)A + 2];
-    const float aabs = fabsf(a0f.x) + fabsf(a1f.x) + fabsf(a2f.x);
-    const int64_t t0 = cur.t0, tend = t0 + (kNbTile - 2);
     const float R2cut = Rcut * Rcut;
     sm.self[lane] = -1;
+    wmax = 0.f;
+    if (cur.k0 >= nr) {
+        last = true;
+        __syncwarp();
+        return 0;
+    }
+    const int k0 = cur.k0;
+    const int k = k0 + lane;
+    int f = 0, n = 0;
+    float ox = 0.f, oy = 0.f, oz = 0.f, ow = 0.f;
+    if (k < nr) {
+        const int B = c.near_list[base + k];
+        const float2 a0f = c.ncomdf[3 * (int64_t)A], a1f = c.ncomdf[3 * (int64_t)A + 1],
+                     a2f = c.ncomdf[3 * (int64_t)A + 2];
+        f = c.nfirst[B];
+        n = c.ncount[B];
+        const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1], b2 = c.ncomdf[3 * (int64_t)B + 2];
+        ox = (b0.x - a0f.x) + (b0.y - a0f.y);
+        oy = (b1.x - a1f.x) + (b1.y - a1f.y);
+        oz = (b2.x - a2f.x) + (b2.y - a2f.y);
+        ow = 0x1p-20f * ((fabsf(a0f.x) + fabsf(a1f.x) + fabsf(a2f.x)) + (fabsf(b0.x) + fabsf(b1.x) + fabsf(b2.x)));
+        if (lane == 0) {  // the part of the first cell not staged yet
+            f += cur.off0;
+            n -= cur.off0;
+        }
+    }
+    int excl = warp_excl_scan(n);
+    const unsigned fit = __ballot_sync(kFull, k < nr && excl + n <= kCap);
+    const int nfit = __popc(fit);
+    int nslots;
+    if (nfit > 0) {
+        nslots = __shfl_sync(kFull, excl + n, nfit - 1);
+        if (lane >= nfit) n = 0;
+        cur.k0 = k0 + nfit;
+        cur.off0 = 0;
+    } else {
+        nslots = kCap;
+        if (lane > 0) n = 0;
+        if (lane == 0) n = kCap;
+        cur.off0 += kCap;
+    }
+    last = cur.k0 >= nr;
+    excl = warp_excl_scan(n);
+    int b[kU], cl[kU], ob[kU];
+    float4 pb[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        const int r = 32 * u + lane;
+        cl[u] = warp_run_of(excl, n, 32 * u);
+        b[u] = __shfl_sync(kFull, f, cl[u]) + r - __shfl_sync(kFull, excl, cl[u]);
+        pb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ob[u] = 0;
+        if (r < nslots) {
+            pb[u] = c.p32[b[u]];
+            if (MODE != NB_COUNT) ob[u] = c.pidx[b[u]];
+        }
+    }
     __syncwarp();
     float wl = 0.f;
     int n_st = 0;
-    last = true;
-    while (cur.k0 < nr) {
-        const int k = cur.k0 + lane;
-        int f = 0, n = 0;
-        float ox = 0.f, oy = 0.f, oz = 0.f, ow = 0.f;
-        if (k < nr) {
-            const int B = c.near_list[base + k];
-            f = c.nfirst[B];
-            n = c.ncount[B];
-            const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1],
-                         b2 = c.ncomdf[3 * (int64_t)B + 2];
-            ox = (b0.x - a0f.x) + (b0.y - a0f.y);
-            oy = (b1.x - a1f.x) + (b1.y - a1f.y);
-            oz = (b2.x - a2f.x) + (b2.y - a2f.y);
-            ow = 0x1p-20f * (aabs + (fabsf(b0.x) + fabsf(b1.x) + fabsf(b2.x)));
-        }
-        const int excl = warp_excl_scan(n);
-        const int total = __shfl_sync(kFull, excl + n, 31);
-        const int64_t pos = cur.pos;
-        const int64_t hi = pos + total < tend ? pos + total : tend;
-        for (int64_t j0 = pos > t0 ? pos : t0; j0 < hi; j0 += 64) {
-            int b[2], cl[2];
-            float cx[2], cy[2], cz[2], cw[2];
-            bool act[2];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int rel = (int)(j0 + 32 * u + lane - pos);
-                cl[u] = warp_run_of(excl, n, (int)(j0 + 32 * u - pos));
-                b[u] = __shfl_sync(kFull, f, cl[u]) + rel - __shfl_sync(kFull, excl, cl[u]);
-                cx[u] = __shfl_sync(kFull, ox, cl[u]);
-                cy[u] = __shfl_sync(kFull, oy, cl[u]);
-                cz[u] = __shfl_sync(kFull, oz, cl[u]);
-                cw[u] = __shfl_sync(kFull, ow, cl[u]);
-                act[u] = j0 + 32 * u + lane < hi;
-            }
-            float4 pb[2];
-            int ob[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                pb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                ob[u] = 0;
-                if (act[u]) {
-                    pb[u] = c.p32[b[u]];
-                    if (MODE != NB_COUNT) ob[u] = c.pidx[b[u]];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const float vx = cx[u] + pb[u].x, vy = cy[u] + pb[u].y, vz = cz[u] + pb[u].z;
-                const float d2 = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
-                const bool keep = act[u] && !(d2 > R2cut);
-                const unsigned mk = __ballot_sync(kFull, keep);
-                if (keep) {
-                    const int at = n_st + __popc(mk & lt);
-                    sm.put(at, vx, vy, vz, b[u], ob[u]);
-                    wl = fmaxf(wl, (fabsf(cx[u]) + fabsf(cy[u]) + fabsf(cz[u])) + fabsf(pb[u].x) + fabsf(pb[u].y) +
-                                       fabsf(pb[u].z) + cw[u]);
-                    const int i = b[u] - fA - a0;  // a sink particle of this pass?
-                    if (i >= 0 && i < P) sm.self[i] = at;
-                }
-                n_st += __popc(mk);
-            }
+    for (int u = 0; u < kU; ++u) {
+        const bool act = 32 * u + lane < nslots;
+        const float cx = __shfl_sync(kFull, ox, cl[u]), cy = __shfl_sync(kFull, oy, cl[u]),
+                    cz = __shfl_sync(kFull, oz, cl[u]), cw = __shfl_sync(kFull, ow, cl[u]);
+        const float vx = cx + pb[u].x, vy = cy + pb[u].y, vz = cz + pb[u].z;
+        const float d2 = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+        const bool keep = act && !(d2 > R2cut);
+        const unsigned mk = __ballot_sync(kFull, keep);
+        if (keep) {
+            const int at = n_st + __popc(mk & lt);
+            sm.put(at, vx, vy, vz, b[u], ob[u]);
+            wl = fmaxf(wl, (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb[u].x) + fabsf(pb[u].y) + fabsf(pb[u].z) + cw);
+            const int i = b[u] - fA - a0;  // a sink particle of this pass?
+            if (i >= 0 && i < P) sm.self[i] = at;
         }
-        if (pos + total > tend) {  // the tile is full: the next one continues inside this batch
-            cur.t0 = tend;
-            last = false;
-            break;
-        }
-        cur.pos = pos + total;
-        cur.k0 = min(cur.k0 + 32, nr);
+        n_st += __popc(mk);
     }
-    if (last) cur.t0 = cur.pos;
     if (n_st & 1) {
         if (lane == 0) sm.put(n_st, 1e18f, 1e18f, 1e18f, -1, -1);
         ++n_st;
@@ -261,7 +266,7 @@ __device__ void nb_pass(const NbCtx &c, const NbSmem<MODE> &sm, int s, int a0, i
     }
     if (lane < P) sm.rowcnt[lane] = 0;
     __syncwarp();
-    NbCursor cur{0, 0, 0};
+    NbCursor cur{0, 0};
     bool last = false;
     while (!last) {
         float wmax;
@@ -286,8 +291,9 @@ __device__ void nb_pass(const NbCtx &c, const NbSmem<MODE> &sm, int s, int a0, i
                     const float2 e = __fadd2_rn(r2, nh2);  // d^2 - (2h)^2
                     const float ex = fabsf(e.x), ey = fabsf(e.y);
                     bandmin = fminf(bandmin, fminf(ex, ey));
-                    mask |= (unsigned)(e.x < 0.f && ex > B && 2 * k != self) << (2 * t);
-                    mask |= (unsigned)(e.y < 0.f && ey > B && 2 * k + 1 != self) << (2 * t + 1);
+                    // STAGE keeps the particle itself in its row (the copy into the CSR drops it)
+                    mask |= (unsigned)(e.x < 0.f && ex > B && (MODE == NB_STAGE || 2 * k != self)) << (2 * t);
+                    mask |= (unsigned)(e.y < 0.f && ey > B && (MODE == NB_STAGE || 2 * k + 1 != self)) << (2 * t + 1);
                 }
             }
             // rare: a pair of these steps inside the band, the float64 test decides it
@@ -303,7 +309,8 @@ __device__ void nb_pass(const NbCtx &c, const NbSmem<MODE> &sm, int s, int a0, i
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         if (fabsf(u ? e.y : e.x) <= B) {
-                            if (nb_exact(c.px, c.py, c.pz, c.ph, a, __float_as_int(u ? b4.w : b4.z)))
+                            const int bb = __float_as_int(u ? b4.w : b4.z);
+                            if ((MODE == NB_STAGE && bb == a) || nb_exact(c.px, c.py, c.pz, c.ph, a, bb))
                                 mask |= 1u << (2 * t + u);
                             ++nfb;
                         }
@@ -321,7 +328,7 @@ __device__ void nb_pass(const NbCtx &c, const NbSmem<MODE> &sm, int s, int a0, i
     if constexpr (MODE == NB_COUNT) {
         if (lane < P) c.counts[c.pidx[fA + a0 + lane]] = run;
     } else if constexpr (MODE == NB_STAGE) {
-        if (lane < P) c.counts[c.pidx[fA + a0 + lane]] = run;
+        if (lane < P) c.counts[c.pidx[fA + a0 + lane]] = run - 1;  // the row holds the particle itself
         rows_finish(c.ro, sm.rows, rc, P, run, lane < P ? c.pidx[fA + a0 + lane] : 0, s, a0);
     } else {
         if (lane < P && run != rc) atomicOr(&c.status[ST_ERR], ERRBIT_STATE);
@@ -333,7 +340,7 @@ __device__ void nb_pass(const NbCtx &c, const NbSmem<MODE> &sm, int s, int a0, i
                 warp_sort_inplace(c.idx + o, n);
             }
         } else {
-            rows_sort_store(sm.rows, exl, lenl, goff, c.idx, P);
+            rows_sort_store(sm.rows, exl, lenl, goff, INT32_MAX, c.idx, P);  // these rows hold no self entry
         }
     }
     __syncwarp();
@@ -360,11 +367,11 @@ __global__ void __launch_bounds__(kNbWarps * 32, 2) k_nb(NbCtx c) {
     if (lane == 0 && nfb && MODE != NB_FILL) atomicAdd(&c.status[ST_NBFALLBACK], nfb);
 }
 
-// Copy the staged rows to the CSR, sorting each by original index.  A warp takes 32 consecutive
-// particles (original order) and their rows four at a time, one per group of 8 lanes, with the
-// sorting networks of nb_rows.cuh (rows longer than 64 entries over the whole warp; beyond 128 in
-// place in the staging buffer).  Rows that were not staged (tstart < 0) are left to the direct
-// fill.
+// Copy the staged rows to the CSR, sorting each by original index and leaving out the particle
+// itself.  A warp takes 32 consecutive particles (original order) and their rows four at a time,
+// one per group of 8 lanes, with the sorting networks of nb_rows.cuh (rows longer than 64 entries
+// over the whole warp; beyond 128 in place in the staging buffer).  Rows that were not staged
+// (tstart < 0) are left to the direct fill.
 __global__ void __launch_bounds__(256, 4) k_nb_copy(const int64_t *tstart, const int64_t *offsets, int32_t *tmp,
                                                  int32_t *idx, int64_t N) {
     const int lane = threadIdx.x & 31;
@@ -376,10 +383,10 @@ __global__ void __launch_bounds__(256, 4) k_nb_copy(const int64_t *tstart, const
         if (base + lane < N) {
             src = tstart[base + lane];
             dst = offsets[base + lane];
-            len = src >= 0 ? (int)(offsets[base + lane + 1] - dst) : -1;
+            len = src >= 0 ? (int)(offsets[base + lane + 1] - dst) + 1 : -1;  // the staged row holds the particle
         }
         const int cnt = (int)(N - base < 32 ? N - base : 32);
-        rows_sort_store(tmp, src, len, dst, idx, cnt);
+        rows_sort_store(tmp, src, len, dst, (int32_t)(base + lane), idx, cnt);
     }
 }
 
