@@ -59,6 +59,8 @@ def parse():
                    help="cut of the headline tree (Sec. 2.1.3): centre of mass, centre of number, median")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-sinks", type=int, default=256)
+    p.add_argument("--direct-targets", type=int, default=4000,
+                   help="targets of the oracle's direct sum for accuracy_vs_direct")
     p.add_argument("--headline-only", action="store_true",
                    help="time only the headline step (no FP64 form, accuracy, e2e or CPU legs); for profiling")
     return p.parse_args()
@@ -144,15 +146,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------ CPU oracle
-def oracle_sample_run(x, m, h, theta, n_sinks, seed=7):
-    """The oracle as it stands on the host cores: full build, then walk + neighbours + gravity
-    for a seeded sample of sinks; returns (seconds for a full-N step extrapolated, details)."""
+def oracle_sample_run(x, m, h, theta, n_sinks, seed=7, tree=None):
+    """The oracle as it stands on the host cores: the full build (or the tree given), then walk +
+    neighbours + gravity for a seeded sample of sinks.  Returns (t_build, t_sample, details, the
+    sampled particles' original indices, their oracle accelerations, the tree)."""
     import numpy as np
 
     import oracle
-    N = x.shape[0]
     t0 = time.perf_counter()
-    T = oracle.OracleTree(x, m, h, n_ll=N_LL)
+    T = tree if tree is not None else oracle.OracleTree(x, m, h, n_ll=N_LL)
     t_build = time.perf_counter() - t0
     nd = T.nodes()
     leaf0 = 1 << T.L
@@ -163,38 +165,60 @@ def oracle_sample_run(x, m, h, theta, n_sinks, seed=7):
     t0 = time.perf_counter()
     T.walk(theta, sinks)
     T.neighbours()
-    T.gravity()
+    acc, _ = T.gravity()
     t_sample = time.perf_counter() - t0
-    t_step = t_build + t_sample * N / max(n_part, 1)
-    return t_step, {"t_build_s": t_build, "t_sample_s": t_sample, "sample_particles": n_part,
-                    "sample_sinks": int(len(sinks))}
+    perm = T.perm()
+    parts = np.concatenate([perm[nd["first"][leaf0 + j]:nd["first"][leaf0 + j] + nd["count"][leaf0 + j]] for j in sinks])
+    return t_build, t_sample, {"sample_particles": n_part, "sample_sinks": int(len(sinks))}, parts, acc[parts], T
 
 
 def run_reference(a, rank, world):
+    """The reference arm: the CPU oracle as it stands, on the host cores.  The tree is built once
+    (timed); every step then runs the walk, neighbour search and gravity for a fresh seeded sample
+    of sinks (timed).  A step's time is that sample's time plus the build's measured cost for the
+    sample's particles (build time x sample particles / N); the value is the sample's particles over
+    that time, so both describe work that ran.  The full-N step the same per-particle costs give is
+    reported on its own (extrapolated_full_n_ms)."""
     if rank != 0:
         return
     import oracle
     import synth
     x, m, h = synth.make_particles(a.kind, a.n, synth.seed_for(3, 0), a.mass)
     oracle.build()
-    times = []
+    t0 = time.perf_counter()
+    T = oracle.OracleTree(x, m, h, n_ll=N_LL)
+    t_build = time.perf_counter() - t0
+    steps_ms, parts = [], []
     det = None
     for i in range(a.warmup + a.steps):
-        t, det = oracle_sample_run(x, m, h, a.theta, a.cpu_sample_sinks, seed=100 + i)
+        _, t_sample, det, _, _, _ = oracle_sample_run(x, m, h, a.theta, a.cpu_sample_sinks, seed=100 + i, tree=T)
+        n_part = det["sample_particles"]
         if i >= a.warmup:
-            times.append(t)
-    t = statistics.mean(times)
-    value = a.n / t / 1e6
-    sample = (f"full-N oracle build, then walk+neighbours+gravity for {det['sample_sinks']} random sinks "
-              f"({det['sample_particles']} particles), extrapolated to N per step")
+            steps_ms.append((t_sample + t_build * n_part / a.n) * 1e3)
+            parts.append(n_part)
+    ms = statistics.mean(steps_ms)
+    value = statistics.mean(parts) / (ms * 1e-3) / 1e6
+    sample = (f"oracle tree built once ({t_build:.2f} s for N={a.n}); per step walk+neighbours+gravity for "
+              f"{det['sample_sinks']} random sinks (~{int(statistics.mean(parts))} particles), plus the build's "
+              f"measured cost for those particles")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": bench_config(a, world),
+            "build_s": t_build,
+            "extrapolated_full_n_ms": ms * a.n / statistics.mean(parts),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def rel_err_stats(a_gpu, a_ref):
+    """RMS, 99.9th percentile and maximum of |a - a_ref| / |a_ref| over the rows given."""
+    import numpy as np
+    e = np.linalg.norm(a_gpu - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
+    return {"n": int(e.size), "rms": float(np.sqrt(np.mean(e * e))), "p99.9": float(np.percentile(e, 99.9)),
+            "max": float(e.max())}
 
 
 # ------------------------------------------------------------------------------------------ GPU
@@ -263,6 +287,7 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
                              "tested separately: RMS 1e-15)",
                 "rms": float(np.sqrt(np.mean(e * e))), "p99.9": float(np.percentile(e, 99.9)),
                 "max": float(e.max()), "pot_rms": float(np.sqrt(np.mean(ep * ep)))}
+    forces = {"mixed": acc_m.cpu().numpy(), "fp64": acc_d.cpu().numpy()}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     xh, mh, hh = (torch.from_numpy(v).pin_memory() for v in (x, m, h))
@@ -381,6 +406,20 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
     g_acc = 2.0 * acc_b
     tree.gravity_backward(g_acc)
     bwd_ms = staged(lambda: tree.gravity_backward(g_acc), ["backward"])
+    # the first backward after a build also transposes the near lists: time it on a fresh build
+    bwd_first = []
+    for _ in range(3):
+        tree.rebuild(xt, mt, ht)
+        tree.gravity()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tree.gravity_backward(g_acc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bwd_first.append(e0.elapsed_time(e1))
+    bwd_first_ms = statistics.mean(bwd_first)
     # tree update (Sec. 2.1.8): integrity check, refit and a new walk, when every particle is
     # still in its ll-cell; positions displaced by 1e-12 (alternating with the originals)
     gen = torch.Generator(device=xt.device)
@@ -473,8 +512,11 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
                    "path": "rcb_update: integrity check, refit, new walk (no particle left its ll-cell)"},
         "gravity_backward": {"ms": bwd_ms, "mparticles_s": job_throughput(world, a.n, bwd_ms),
                              "path": "rcb_gravity_backward on the built tree (lists already transposed)"},
+        "gravity_backward_first": {"ms": bwd_first_ms, "setup_ms": bwd_first_ms - bwd_ms,
+                                   "path": "the first rcb_gravity_backward after a build, transposition of the near "
+                                           "lists included (setup_ms: its excess over a later call)"},
     }
-    return fp64, accuracy, e2e, int(idx0.numel()), per_stage
+    return fp64, accuracy, e2e, int(idx0.numel()), per_stage, forces
 
 
 def run_ours(a, rank, world, local_rank):
@@ -534,11 +576,13 @@ def run_ours(a, rank, world, local_rank):
     stage_ms = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
     info = tree.info()
 
-    fp64 = accuracy = e2e = per_stage = None
+    fp64 = accuracy = e2e = per_stage = forces = None
     idx_total = None
+    alu = None
     if not a.headline_only:
-        fp64, accuracy, e2e, idx_total, per_stage = extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step,
-                                                    barrier, ms, stage_ms)
+        fp64, accuracy, e2e, idx_total, per_stage, forces = extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush,
+                                                                       stream, step, barrier, ms, stage_ms)
+        alu = rcb.alu_rates(SMS)
     clocks = sampler.stop() if sampler else None
 
     if rank != 0:
@@ -579,14 +623,28 @@ def run_ours(a, rank, world, local_rank):
             per_stage[k]["hbm_peak_gbs"] = hbm
             per_stage[k]["frac"] = per_stage[k]["achieved_gbs"] / hbm
     cpu = None
+    acc_vs_oracle = acc_vs_direct = None
     if not a.no_cpu_baseline and not a.headline_only and world == 1:
+        import numpy as np
+
         import oracle
         oracle.build()
-        t_step, det = oracle_sample_run(x, m, h, a.theta, a.cpu_sample_sinks)
+        t_build, t_sample, det, parts, acc_o, _ = oracle_sample_run(x, m, h, a.theta, a.cpu_sample_sinks)
+        t_step = t_build + t_sample * a.n / det["sample_particles"]
         cpu = {"value": a.n / t_step / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": (f"full-N build ({det['t_build_s']:.2f} s), then walk+neighbours+gravity for "
+               "sample": (f"full-N build ({t_build:.2f} s), then walk+neighbours+gravity for "
                           f"{det['sample_sinks']} random sinks ({det['sample_particles']} particles, "
-                          f"{det['t_sample_s']:.2f} s) extrapolated to N")}
+                          f"{t_sample:.2f} s); value = N over the build plus the sample's time scaled to N")}
+        # accuracy against the truth (Sec. 3.1): the oracle's own tree forces for the sampled sinks'
+        # particles, and the direct kernel-softened sum for a seeded sample of targets
+        acc_vs_oracle = {k: rel_err_stats(v[parts], acc_o) for k, v in forces.items()}
+        acc_vs_oracle["sample"] = f"{det['sample_particles']} particles of {det['sample_sinks']} random sinks"
+        tg = np.sort(np.random.default_rng(11).choice(a.n, min(a.direct_targets, a.n), replace=False))
+        t0 = time.perf_counter()
+        acc_dir, _ = oracle.direct(x, m, h, tg)
+        acc_vs_direct = {k: rel_err_stats(v[tg], acc_dir) for k, v in forces.items()}
+        acc_vs_direct["sample"] = (f"{len(tg)} seeded random targets, oracle direct sum over all N "
+                                   f"({time.perf_counter() - t0:.1f} s on {oracle.num_threads()} cores)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -602,6 +660,11 @@ def run_ours(a, rank, world, local_rank):
         "per_stage": per_stage,
         "fp64": fp64,
         "accuracy_mixed_vs_fp64": accuracy,
+        "accuracy_vs_oracle": acc_vs_oracle,
+        "accuracy_vs_direct": acc_vs_direct,
+        "fp32_peak_measured": None if alu is None else dict(alu, note="alu_rate probe (peak/alu_rate.cu): best of "
+                                                            "three runs; the roofline peak above is the nominal "
+                                                            "SMs x lanes x 2 x clock"),
         "tree": {k: info[k] for k in ("L", "nsinks", "near_total", "far_total", "reach_total", "near_pairs",
                                         "candidate_pairs", "walk_fp64_decisions", "smem_subtrees")},
         "neighbours_total": idx_total,

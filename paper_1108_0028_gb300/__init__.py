@@ -130,15 +130,46 @@ def _cuda_f64(t, shape, name):
 # ---------------------------------------------------------------------------------------------
 # C-ABI mirrors (argument marshalling only)
 
-def rcb_build(x, m, h, n_ll=12, theta=0.7, precision="mixed", tree=None, stream=None, flags=0):
-    """Build (or rebuild in place) a tree; returns the handle (ctypes.c_void_p)."""
+# torch's caching allocator behind the library's allocator callbacks (rcb_alloc_fn, rcb_free_fn):
+# the tree's device arrays then come from, and return to, the same pool as PyTorch's tensors
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def _torch_alloc(nbytes, ctx, stream):
+    try:
+        return _torch().cuda.caching_allocator_alloc(int(nbytes), None, int(stream or 0))
+    except Exception:  # the library reports RCB_ERR_ALLOC
+        return None
+
+
+def _torch_free(ptr, ctx, stream):
+    try:
+        if ptr:
+            _torch().cuda.caching_allocator_delete(int(ptr))
+    except Exception:  # torch already torn down at interpreter exit
+        pass
+
+
+_TORCH_ALLOC = _ALLOC_FN(_torch_alloc)
+_TORCH_FREE = _FREE_FN(_torch_free)
+
+
+def rcb_build(x, m, h, n_ll=12, theta=0.7, precision="mixed", tree=None, stream=None, flags=0,
+              allocator: str = "torch"):
+    """Build (or rebuild in place) a tree; returns the handle (ctypes.c_void_p).  allocator:
+    "torch" (the caching allocator, through rcb_alloc_fn / rcb_free_fn) or "cuda" (the library's
+    own cudaMallocAsync / cudaFreeAsync).  A rebuild keeps the tree's first allocator."""
     N = x.shape[0] if x.dim() == 2 else 0
     _cuda_f64(x, (N, 3), "x")
     _cuda_f64(m, (N,), "m")
     _cuda_f64(h, (N,), "h")
+    if allocator not in ("torch", "cuda"):
+        raise ValueError("allocator must be 'torch' or 'cuda'")
     p = rcb_params(int(n_ll), _PRECISION[precision], float(theta), int(flags), 0)
     handle = tree if tree is not None else ctypes.c_void_p(None)
-    st = lib().rcb_build(_dptr(x), _dptr(m), _dptr(h), N, ctypes.byref(p), None, None, None, _stream_ptr(stream),
+    fa, ff = (_TORCH_ALLOC, _TORCH_FREE) if allocator == "torch" else (None, None)
+    st = lib().rcb_build(_dptr(x), _dptr(m), _dptr(h), N, ctypes.byref(p), fa, ff, None, _stream_ptr(stream),
                          ctypes.byref(handle))
     _check(st, "rcb_build")
     return handle

@@ -25,6 +25,7 @@
 #include <type_traits>
 
 #include "far_math.cuh"
+#include "nb_rows.cuh"
 #include "rcb_internal.cuh"
 
 namespace rcb {
@@ -911,19 +912,22 @@ __global__ void k_tnear_fill(BCtx c, int32_t *cursor, int32_t *out) {
     }
 }
 
-// Sort each transposed row (insertion sort by one thread: rows are short) for a fixed order.
-__global__ void k_tnear_sort(const int32_t *off, int64_t nleaves, int32_t *rows) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nleaves; j += (int64_t)gridDim.x * blockDim.x) {
-        const int a = off[j], b = off[j + 1];
-        for (int i = a + 1; i < b; ++i) {
-            const int v = rows[i];
-            int k = i - 1;
-            while (k >= a && rows[k] > v) {
-                rows[k + 1] = rows[k];
-                --k;
-            }
-            rows[k + 1] = v;
+// Sort each transposed row, for a fixed order: a warp takes 32 rows and sorts them in registers,
+// four at a time on groups of 8 lanes (longer rows over the whole warp; beyond 128 entries in
+// place), with the sorting networks of the neighbour rows.
+__global__ void __launch_bounds__(256, 4) k_tnear_sort(const int32_t *off, int64_t nleaves, int32_t *rows) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = gw * 32; base < nleaves; base += nw * 32) {
+        int64_t a = 0;
+        int n = -1;
+        if (base + lane < nleaves) {
+            a = off[base + lane];
+            n = (int)(off[base + lane + 1] - a);
         }
+        const int cnt = (int)(nleaves - base < 32 ? nleaves - base : 32);
+        rows_sort_store(rows, a, n, a, INT32_MAX, rows, cnt);
     }
 }
 
@@ -1094,8 +1098,8 @@ int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double
         if (rc) return rc;
         RCB_CUDA_TRY(cudaMemcpyAsync(cnt, t->tnear_off, nl * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         k_tnear_fill<<<gridw, kBW * 32, 0, st>>>(c, cnt, t->tnear_sink); note_launch();
-        k_tnear_sort<<<(int)std::min<int64_t>((nl + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(t->tnear_off, nl,
-                                                                                            t->tnear_sink); note_launch();
+        k_tnear_sort<<<(int)std::max<int64_t>(1, std::min<int64_t>((nl + 255) / 256, (int64_t)nsm * 16)), 256, 0, st>>>(
+            t->tnear_off, nl, t->tnear_sink); note_launch();
         k_bwd_pleaf<<<gridw, kBW * 32, 0, st>>>(c); note_launch();
         RCB_CUDA_TRY(cudaGetLastError());
         t->bwd_valid = 1;

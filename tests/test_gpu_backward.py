@@ -83,3 +83,24 @@ def test_autograd_function():
     ex, _ = _close(xt.grad.cpu().numpy(), ox, 1e-9)
     em, _ = _close(mt.grad.cpu().numpy(), om, 1e-9)
     assert ex < 1e-9 and em < 1e-9
+
+
+def test_autograd_function_mixed():
+    # the torch.autograd.Function in the mixed form: its gradient matches the oracle's FP64 VJP to
+    # the mixed backward's tolerance (1e-5 of the largest component)
+    import paper_1108_0028_gb300 as rcb
+    N = 2500
+    x, m, h = synth.make_particles("sphere", N, 93, "loguniform10")
+    xt, mt, ht = _gpu(x, m, h)
+    xt.requires_grad_(True)
+    mt.requires_grad_(True)
+    acc, pot = rcb.rcb_gravity_fn(xt, mt, ht, 12, 0.6, "mixed")
+    loss = (acc * acc).sum() + pot.sum()
+    loss.backward()
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(0.6)
+    a, p = ref.gravity()
+    ox, om = ref.gravity_backward(2 * a, np.ones(N))
+    ex, _ = _close(xt.grad.cpu().numpy(), ox, 1e-5)
+    em, _ = _close(mt.grad.cpu().numpy(), om, 1e-5)
+    assert ex < 1e-5 and em < 1e-5, (ex, em)

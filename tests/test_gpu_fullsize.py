@@ -19,9 +19,12 @@ pytestmark = pytest.mark.gpu
 FULL = [
     # kind, N, masses, theta, config, case
     ("sphere", 4194304, "loguniform10", 0.7, 3, 0),   # the headline workload
+    ("sphere", 4194304, "loguniform10", 0.5, 3, 2),
     ("plummer", 4194304, "loguniform10", 0.5, 3, 1),
+    ("plummer", 4194304, "loguniform10", 0.7, 3, 3),  # long far lists: the paired walk at full size
     ("plummer", 1000000, "equal", 0.5, 2, 0),
     ("cube", 10000000, "equal", 0.7, 4, 0),
+    ("plummer", 10000000, "equal", 0.7, 4, 1),        # the Plummer half of the scaling sweep
     ("cube", 100000000, "equal", 0.7, 4, 2),          # the largest size of the scaling sweep
 ]
 
