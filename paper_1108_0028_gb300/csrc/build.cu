@@ -983,7 +983,15 @@ __device__ void parent_moments(const LeafCtx &c, int P) {
     c.nhnode[P] = 0.0;
 }
 
-// One thread per sink: Eq. 1, radii, float32 copies.
+// One thread per sink: Eq. 1, radii, float32 copies.  FP64 runs at 1/64 of FP32 on this GPU, so
+// the float64 work per particle is kept small: the quadrupole accumulates with fused
+// multiply-adds (it is compared within a tolerance, not bit for bit), and the two radii are
+// exact maxima found from float32 estimates: every distance estimate has relative error below
+// 2^-21, so when the runner-up estimate is more than 2^-18 below the leader the exact maximum is
+// the leader's (only it is evaluated in float64); otherwise every particle is.
+//   h_int  = max_a |r_a - r_g|          (a correctly rounded square root is monotonic, so the
+//                                        exact maximum of the squares gives the same double)
+//   h_node = max_a (|r_a - r_g| + 2 h_a)
 __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsinks) return;
@@ -997,29 +1005,32 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
     double com[3] = {c.ncom[3 * (int64_t)n], c.ncom[3 * (int64_t)n + 1], c.ncom[3 * (int64_t)n + 2]};
     double rg[3] = {c.nrg[3 * (int64_t)n], c.nrg[3 * (int64_t)n + 1], c.nrg[3 * (int64_t)n + 2]};
     double Q[6] = {0, 0, 0, 0, 0, 0};
-    // h_int = max_a |r_a - r_g| = sqrt(max_a |r_a - r_g|^2): a correctly rounded square root is
-    // monotonic, so one root per cell gives the same double.  h_node = max_a (|r_a - r_g| + 2 h_a):
-    // float32 estimates (relative error < 2^-21) find the leader; when the runner-up estimate is
-    // more than 2^-18 below it, the exact maximum is the leader's (only it is evaluated in
-    // float64), otherwise every particle is.
-    double d2max = 0.0;
-    float e1 = -1.f, e2 = -1.f;  // largest and second largest estimates
-    int a1 = f;
+    float i1 = -1.f, i2 = -1.f, e1 = -1.f, e2 = -1.f;  // largest and second largest estimates
+    int ai = f, a1 = f;
     for (int a = f; a < f + cnt; ++a) {
-        double x = px[a], y = py[a], z = pz[a], m = pm[a], h = ph[a];
-        double dx[3] = {__dsub_rn(x, com[0]), __dsub_rn(y, com[1]), __dsub_rn(z, com[2])};
-        double dr2 = __dadd_rn(__dadd_rn(__dmul_rn(dx[0], dx[0]), __dmul_rn(dx[1], dx[1])), __dmul_rn(dx[2], dx[2]));
-        double tm = __dmul_rn(3.0, m);
-        int k = 0;
-        for (int i = 0; i < 3; ++i)
-            for (int j = i; j < 3; ++j, ++k) {
-                double v = tm * dx[i] * dx[j];
-                if (i == j) v -= m * dr2;
-                Q[k] += v;
-            }
-        const double d2 = dist2_rn(x, y, z, rg[0], rg[1], rg[2]);
-        d2max = fmax(d2max, d2);
-        const float est = __fadd_rn(__fsqrt_rn(__double2float_rn(d2)), __double2float_rn(__dmul_rn(2.0, h)));
+        const double x = px[a], y = py[a], z = pz[a], m = pm[a], h = ph[a];
+        const double dx = __dsub_rn(x, com[0]), dy = __dsub_rn(y, com[1]), dz = __dsub_rn(z, com[2]);
+        const double dr2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double tx = 3.0 * m * dx, ty = 3.0 * m * dy, tz = 3.0 * m * dz, md = m * dr2;
+        Q[0] = fma(tx, dx, Q[0]) - md;
+        Q[1] = fma(tx, dy, Q[1]);
+        Q[2] = fma(tx, dz, Q[2]);
+        Q[3] = fma(ty, dy, Q[3]) - md;
+        Q[4] = fma(ty, dz, Q[4]);
+        Q[5] = fma(tz, dz, Q[5]) - md;
+        // r_a - r_g in float64, rounded once to float32 per component (relative error 2^-24 each),
+        // so the float32 distance has relative error below 2^-21
+        const float gx = __double2float_rn(__dsub_rn(x, rg[0])), gy = __double2float_rn(__dsub_rn(y, rg[1])),
+                    gz = __double2float_rn(__dsub_rn(z, rg[2]));
+        const float dg = __fsqrt_rn(fmaf(gz, gz, fmaf(gy, gy, gx * gx)));
+        const float est = __fadd_rn(dg, __double2float_rn(__dmul_rn(2.0, h)));
+        if (dg > i1) {
+            i2 = i1;
+            i1 = dg;
+            ai = a;
+        } else if (dg > i2) {
+            i2 = dg;
+        }
         if (est > e1) {
             e2 = e1;
             e1 = est;
@@ -1027,10 +1038,13 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
         } else if (est > e2) {
             e2 = est;
         }
-        p32[a] = make_float4(__double2float_rn(dx[0]), __double2float_rn(dx[1]), __double2float_rn(dx[2]),
-                             __double2float_rn(m));
+        p32[a] = make_float4(__double2float_rn(dx), __double2float_rn(dy), __double2float_rn(dz), __double2float_rn(m));
         h32[a] = __double2float_rn(h);
     }
+    double d2max = 0.0;
+    const bool clear_i = i2 < __fmul_rn(i1, 1.0f - 0x1p-18f);
+    for (int a = clear_i ? ai : f; a < (clear_i ? ai + 1 : f + cnt); ++a)
+        d2max = fmax(d2max, dist2_rn(px[a], py[a], pz[a], rg[0], rg[1], rg[2]));
     const double hint = __dsqrt_rn(d2max);
     double hnode = 0.0;
     const bool clear = e2 < __fmul_rn(e1, 1.0f - 0x1p-18f);

@@ -307,15 +307,16 @@ struct NearTile {
 // the representation error's share of the d^2 error at most 6 2^-28 F, well inside the neighbour
 // band.
 //
-// Far sources: with R_A the largest |d_a| and H_A the largest h_a of the sink's particles, a
-// source b with |d_b| > (R_A + X_b)(1 + 2^-10) has r_ab >= |d_b| - |d_a| > X_b for every sink
-// particle a.  X_b = H_A + h_b puts all its pairs on the Newtonian branch of Eq. 10 (q >= 2);
-// with NB, X_b = max(H_A + h_b, 2 H_A) also keeps it out of every sink particle's neighbour
-// sphere (r < 2 h_a).  The 2^-10 margin is far above the float32 rounding of the test, of q and
-// of the neighbour filter.
+// Far sources: with H_A the largest h_a of the sink's particles and the box [blo, bhi] of their
+// float32 offsets d_a, a source b whose distance g from the box exceeds X_b (1 + 2^-10) has
+// r_ab >= g > X_b for every sink particle a.  X_b = H_A + h_b puts all its pairs on the
+// Newtonian branch of Eq. 10 (q >= 2); with NB, X_b = max(H_A + h_b, 2 H_A) also keeps it out of
+// every sink particle's neighbour sphere (r < 2 h_a).  The 2^-10 margin is far above the float32
+// rounding of the test, of q and of the neighbour filter.
 template <bool NB>
 __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0, int P, int nlist, int nr,
-                                     NearCursor &cur, const NearSmem<NB> &sm, float RA, float HA, float &wmax) {
+                                     NearCursor &cur, const NearSmem<NB> &sm, float3 blo, float3 bhi, float HA,
+                                     float &wmax) {
     constexpr int kCap = kNearTile - kNearPad;
     constexpr int kU = (kCap + 31) / 32;  // slots per lane
     const int lane = threadIdx.x & 31;
@@ -394,10 +395,12 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0
                         cz = __shfl_sync(0xffffffffu, oz, cl[u]);
             const float cw = NB ? __shfl_sync(0xffffffffu, ow, cl[u]) : 0.f;
             const float vx = cx + pb[u].x, vy = cy + pb[u].y, vz = cz + pb[u].z;
-            const float d2 = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
-            const float X = NB ? fmaxf(HA + hb[u], HA + HA) : HA + hb[u];
-            const float R = (RA + X) * (1.0f + 0x1p-10f);
-            const bool far = d2 > R * R;
+            // squared distance from the source to the sink particles' box
+            const float gx = fmaxf(fmaxf(blo.x - vx, vx - bhi.x), 0.f), gy = fmaxf(fmaxf(blo.y - vy, vy - bhi.y), 0.f),
+                        gz = fmaxf(fmaxf(blo.z - vz, vz - bhi.z), 0.f);
+            const float g2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+            const float X = (NB ? fmaxf(HA + hb[u], HA + HA) : HA + hb[u]) * (1.0f + 0x1p-10f);
+            const bool far = g2 > X * X;
             const unsigned mc = __ballot_sync(0xffffffffu, act && !far);
             const unsigned mf = __ballot_sync(0xffffffffu, act && far);
             if (act) {
@@ -627,21 +630,23 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
         const int A = c.sinks[s];
         const int fA = c.nfirst[A], nA = c.ncount[A];
         const int nr = c.near_nr[s], nlist = nr + c.near_nn[s];
-        // R_A and H_A of the sink cell (float32 offsets from its centre of mass)
-        float RA, HA;
-        {
-            float R2 = 0.f, H = 0.f;
-            for (int i = lane; i < nA; i += 32) {
-                const float4 pa = c.p32[fA + i];
-                R2 = fmaxf(R2, fmaf(pa.z, pa.z, fmaf(pa.y, pa.y, pa.x * pa.x)));
-                H = fmaxf(H, c.h32[fA + i]);
-            }
-            for (int o = 16; o >= 1; o >>= 1) {
-                R2 = fmaxf(R2, __shfl_xor_sync(0xffffffffu, R2, o));
-                H = fmaxf(H, __shfl_xor_sync(0xffffffffu, H, o));
-            }
-            RA = sqrtf(R2) * (1.0f + 0x1p-10f);
-            HA = H;
+        // the box of the sink cell's particles (float32 offsets from its centre of mass) and H_A
+        float3 blo = make_float3(3e38f, 3e38f, 3e38f), bhi = make_float3(-3e38f, -3e38f, -3e38f);
+        float HA = 0.f;
+        for (int i = lane; i < nA; i += 32) {
+            const float4 pa = c.p32[fA + i];
+            blo = make_float3(fminf(blo.x, pa.x), fminf(blo.y, pa.y), fminf(blo.z, pa.z));
+            bhi = make_float3(fmaxf(bhi.x, pa.x), fmaxf(bhi.y, pa.y), fmaxf(bhi.z, pa.z));
+            HA = fmaxf(HA, c.h32[fA + i]);
+        }
+        for (int o = 16; o >= 1; o >>= 1) {
+            blo.x = fminf(blo.x, __shfl_xor_sync(0xffffffffu, blo.x, o));
+            blo.y = fminf(blo.y, __shfl_xor_sync(0xffffffffu, blo.y, o));
+            blo.z = fminf(blo.z, __shfl_xor_sync(0xffffffffu, blo.z, o));
+            bhi.x = fmaxf(bhi.x, __shfl_xor_sync(0xffffffffu, bhi.x, o));
+            bhi.y = fmaxf(bhi.y, __shfl_xor_sync(0xffffffffu, bhi.y, o));
+            bhi.z = fmaxf(bhi.z, __shfl_xor_sync(0xffffffffu, bhi.z, o));
+            HA = fmaxf(HA, __shfl_xor_sync(0xffffffffu, HA, o));
         }
         // passes of up to 32 sink particles (one pass unless the cell holds more)
         for (int a0 = 0; a0 < nA; a0 += 32) {
@@ -677,7 +682,7 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
             NearCursor cur{0, 0};
             for (;;) {
                 float wmax = 0.f;
-                const NearTile tl = stage_near_mixed<NB>(c, s, A, fA, a0, P, nlist, nr, cur, sm, RA, HA, wmax);
+                const NearTile tl = stage_near_mixed<NB>(c, s, A, fA, a0, P, nlist, nr, cur, sm, blo, bhi, HA, wmax);
                 if (NB) {
                     const float F = wmax + (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z));
                     L.B = fmaf(F, F, L.h2) * 0x1p-19f + 1e-30f;

@@ -16,7 +16,7 @@
 
 namespace rcb {
 
-constexpr int kRowBuf = 1024;  // entries of a warp's shared-memory row buffer
+constexpr int kRowBuf = 1280;  // entries of a warp's shared-memory row buffer
 
 // Where finished rows go.
 struct RowOut {

@@ -5,8 +5,8 @@
 // pass   one warp per sink stages its candidate particles in shared memory as float32 offsets
 //        from the sink's centre of mass (the double-float cell-centre difference plus each
 //        particle's float32 offset from its own cell's centre of mass), keeping only those within
-//        (R_A + 2 H_A)(1 + 2^-10) of it: R_A is the largest |d_a| and H_A the largest h_a of the
-//        sink's particles, so a source farther out has r_ab > 2 h_a for every sink particle.
+//        2 H_A (1 + 2^-10) of the box of the sink's particles (H_A their largest h_a), since a
+//        source farther out has r_ab > 2 h_a for every sink particle.
 //        Lanes take (sink particle i, source stream j) pairs as the near field does: with P sink
 //        particles, S = 32 / P streams, lane l holds particle l mod P and tests the source pairs
 //        j, j + S, ... (j = l / P), two at a time with paired float32 instructions.  Three forms:
@@ -100,18 +100,18 @@ struct NbCursor {
 // Stage the next tile: one batch of up to 32 candidate cells, as many whole cells as fit in
 // kNbTile - 2 slots (part of one cell if a single cell is larger).  Lanes describe the cells,
 // every lane issues the gathers of all its slots before using any of them (two rounds of memory
-// latency per tile), then sources beyond (R_A + 2 H_A)(1 + 2^-10) are dropped and the others
-// stored.  Returns the number stored (padded to even with a far-away source); wmax gets the
+// latency per tile), then sources farther than 2 H_A (1 + 2^-10) from the box of the sink's
+// particles are dropped (r_ab > 2 h_a for every sink particle a) and the others stored.  Returns the number stored (padded to even with a far-away source); wmax gets the
 // tile's largest w.
 template <int MODE>
 __device__ int stage_nb(const NbCtx &c, int s, int A, int fA, int a0, int P, int nr, NbCursor &cur,
-                        const NbSmem<MODE> &sm, float Rcut, float &wmax, bool &last) {
+                        const NbSmem<MODE> &sm, float3 blo, float3 bhi, float Xcut, float &wmax, bool &last) {
     constexpr int kCap = kNbTile - 2;
     constexpr int kU = (kCap + 31) / 32;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)s * c.cap_near;
-    const float R2cut = Rcut * Rcut;
+    const float X2cut = Xcut * Xcut;
     sm.self[lane] = -1;
     wmax = 0.f;
     if (cur.k0 >= nr) {
@@ -179,8 +179,10 @@ __device__ int stage_nb(const NbCtx &c, int s, int A, int fA, int a0, int P, int
         const float cx = __shfl_sync(kFull, ox, cl[u]), cy = __shfl_sync(kFull, oy, cl[u]),
                     cz = __shfl_sync(kFull, oz, cl[u]), cw = __shfl_sync(kFull, ow, cl[u]);
         const float vx = cx + pb[u].x, vy = cy + pb[u].y, vz = cz + pb[u].z;
-        const float d2 = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
-        const bool keep = act && !(d2 > R2cut);
+        // squared distance from the source to the sink particles' box
+        const float gx = fmaxf(fmaxf(blo.x - vx, vx - bhi.x), 0.f), gy = fmaxf(fmaxf(blo.y - vy, vy - bhi.y), 0.f),
+                    gz = fmaxf(fmaxf(blo.z - vz, vz - bhi.z), 0.f);
+        const bool keep = act && !(fmaf(gz, gz, fmaf(gy, gy, gx * gx)) > X2cut);
         const unsigned mk = __ballot_sync(kFull, keep);
         if (keep) {
             const int at = n_st + __popc(mk & lt);
@@ -219,22 +221,25 @@ __device__ void nb_pass(const NbCtx &c, const NbSmem<MODE> &sm, int s, int a0, i
     const int A = c.sinks[s];
     const int fA = c.nfirst[A], nA = c.ncount[A];
     const int nr = c.near_nr[s];
-    float RA, HA;
-    {
-        float R2 = 0.f, H = 0.f;
-        for (int i = lane; i < nA; i += 32) {
-            const float4 pa = c.p32[fA + i];
-            R2 = fmaxf(R2, fmaf(pa.z, pa.z, fmaf(pa.y, pa.y, pa.x * pa.x)));
-            H = fmaxf(H, c.h32[fA + i]);
-        }
-        for (int o = 16; o >= 1; o >>= 1) {
-            R2 = fmaxf(R2, __shfl_xor_sync(kFull, R2, o));
-            H = fmaxf(H, __shfl_xor_sync(kFull, H, o));
-        }
-        RA = sqrtf(R2) * (1.0f + 0x1p-10f);
-        HA = H;
+    // the box of the sink cell's particles (float32 offsets from its centre of mass) and H_A
+    float3 blo = make_float3(3e38f, 3e38f, 3e38f), bhi = make_float3(-3e38f, -3e38f, -3e38f);
+    float HA = 0.f;
+    for (int i = lane; i < nA; i += 32) {
+        const float4 pa = c.p32[fA + i];
+        blo = make_float3(fminf(blo.x, pa.x), fminf(blo.y, pa.y), fminf(blo.z, pa.z));
+        bhi = make_float3(fmaxf(bhi.x, pa.x), fmaxf(bhi.y, pa.y), fmaxf(bhi.z, pa.z));
+        HA = fmaxf(HA, c.h32[fA + i]);
     }
-    const float Rcut = (RA + 2.0f * HA) * (1.0f + 0x1p-10f);
+    for (int o = 16; o >= 1; o >>= 1) {
+        blo.x = fminf(blo.x, __shfl_xor_sync(kFull, blo.x, o));
+        blo.y = fminf(blo.y, __shfl_xor_sync(kFull, blo.y, o));
+        blo.z = fminf(blo.z, __shfl_xor_sync(kFull, blo.z, o));
+        bhi.x = fmaxf(bhi.x, __shfl_xor_sync(kFull, bhi.x, o));
+        bhi.y = fmaxf(bhi.y, __shfl_xor_sync(kFull, bhi.y, o));
+        bhi.z = fmaxf(bhi.z, __shfl_xor_sync(kFull, bhi.z, o));
+        HA = fmaxf(HA, __shfl_xor_sync(kFull, HA, o));
+    }
+    const float Xcut = 2.0f * HA * (1.0f + 0x1p-10f);
     const int P = min(32, nA - a0), S = 32 / P;
     const int i = lane % P, j = lane / P;
     const bool active = j < S;
@@ -270,7 +275,7 @@ __device__ void nb_pass(const NbCtx &c, const NbSmem<MODE> &sm, int s, int a0, i
     bool last = false;
     while (!last) {
         float wmax;
-        const int ns = stage_nb<MODE>(c, s, A, fA, a0, P, nr, cur, sm, Rcut, wmax, last);
+        const int ns = stage_nb<MODE>(c, s, A, fA, a0, P, nr, cur, sm, blo, bhi, Xcut, wmax, last);
         const float F = wmax + aabs1;
         const float B = fmaf(F, F, h2) * 0x1p-19f + 1e-30f;
         const int self = sm.self[i];
