@@ -486,6 +486,11 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
         try:
             split_variants[split] = split_variant_leg(rcb, a, split, xt, mt, ht, flush, acc_std)
         except (KeyError, TypeError, ValueError, rcb.RCBError) as e:  # a report of this leg only, not of the step
+            # a CUDA error leaves the context unusable: every later number would be invalid, so it
+            # ends the run instead of being reported as this leg's failure
+            if isinstance(e, rcb.RCBError) and e.status == rcb.RCB_ERR_CUDA:
+                raise
+            torch.cuda.synchronize()  # raises if the context holds a sticky error
             split_variants[split] = {"error": repr(e)}
     del acc_std
     L = tree.info()["L"]

@@ -338,3 +338,27 @@ def test_density_of_a_uniform_sphere_is_its_mean_density():
     self_term = np.array([m[a] * oracle.kernel_W(0.0, h[a]) for a in range(N)])
     mean = m.sum() / (4.0 / 3.0 * np.pi)
     assert abs(np.mean((rho - self_term)[inner]) / mean - 1.0) < 0.02
+
+
+def test_median_split_error_tail_does_not_depend_on_theta():
+    # Eq. 4 bounds the size of the source cell (H_B < theta R), not the extent of the sink cell about
+    # which the field is expanded (Eq. 6).  The median position split makes long, thin sink cells in
+    # the sparse outskirts of a Plummer sphere, whose particles sit far from the cell's centre of
+    # mass: their third-order Taylor error is the same at any theta, while at theta = 0 (every cell
+    # opened) the tree is exact.  The centre-of-mass split of the same set errs less.
+    N = 12000
+    x, m, h = synth.make_particles("plummer", N, synth.seed_for(9, 7), "loguniform10")
+    tg = np.sort(np.random.default_rng(3).choice(N, 600, replace=False))
+    ad, _ = oracle.direct(x, m, h, tg)
+
+    def rms(T, th):
+        T.walk(th)
+        a, _ = T.gravity()
+        e = np.linalg.norm(a[tg] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        return float(np.sqrt(np.mean(e * e)))
+
+    med = oracle.OracleTree(x, m, h, split="median")
+    r0, r3, r7 = rms(med, 0.0), rms(med, 0.3), rms(med, 0.7)
+    assert r0 < 1e-12
+    assert r3 > 1e-3 and abs(r7 - r3) < 0.05 * r3, (r3, r7)
+    assert rms(oracle.OracleTree(x, m, h), 0.7) < r7
