@@ -293,14 +293,45 @@ struct NearTile {
     bool last;  // no sources beyond this tile
 };
 
+// The cells of the next tile, loaded while the current tile is computed: the near-list entries
+// wk + lane and wk + 32 + lane (bw0, bw1; -1 past the list) and, as loaded, first particle, count
+// and double-float centre of mass of cell bw0 (the cell of entry wk + lane).  The loaded values
+// are first used by the next staging, so that their latency overlaps the pair loops.
+struct NearAhead {
+    int wk, bw0, bw1;
+    int f, n;
+    float2 b0, b1, b2;
+};
+
+// Load the near-list window from entry k0 and the descriptors of the cells of its first half.
+__device__ __forceinline__ void near_ahead_load(const GCtx &c, int64_t base, int nr, int nlist, int k0, int B0,
+                                                bool have_b0, NearAhead &ah) {
+    const int lane = threadIdx.x & 31;
+    const int B = have_b0 ? B0 : (k0 + lane < nlist ? near_entry(c, base, nr, k0 + lane) : -1);
+    ah.wk = k0;
+    ah.bw0 = B;
+    ah.bw1 = k0 + 32 + lane < nlist ? near_entry(c, base, nr, k0 + 32 + lane) : -1;
+    ah.f = 0;
+    ah.n = 0;
+    ah.b0 = ah.b1 = ah.b2 = make_float2(0.f, 0.f);
+    if (B >= 0) {
+        ah.f = c.nfirst[B];
+        ah.n = c.ncount[B];
+        ah.b0 = c.ncomdf[3 * (int64_t)B];
+        ah.b1 = c.ncomdf[3 * (int64_t)B + 1];
+        ah.b2 = c.ncomdf[3 * (int64_t)B + 2];
+    }
+}
+
 // Stage the next tile of sink s (cell A, sorted particles [fA, fA + nA), this pass the P
 // particles from a0).  A tile is one batch of up to 32 near cells, all from the same part of the
 // list (reachable or not), as many whole cells as fit in kNearTile - kNearPad slots (part of one
-// cell if a single cell is larger).  Lanes describe the cells (first particle, count, centre-of-
-// mass offset), then every lane issues the gathers of half its slots (lane + 32 u) before using
-// any of them, so that a tile costs three rounds of memory latency; then each slot's float32
-// offset from the sink's centre of mass is formed and stored, close sources from the front of the
-// tile and far ones from the back.  The cell offset o is the double-float difference of the two
+// cell if a single cell is larger).  The cells' descriptors (first particle, count, centre of
+// mass) arrive with ah, loaded during the previous tile's pair loops; once the batch is known, the
+// next tile's are loaded the same way.  Every lane then issues the gathers of half its slots
+// (lane + 32 u) before using any of them, so that a tile costs two rounds of memory latency;
+// each slot's float32 offset from the sink's centre of mass is formed and stored, close sources
+// from the front of the tile and far ones from the back.  The cell offset o is the double-float difference of the two
 // centres of mass: it differs from the float64 difference by at most 2u |dCOM| + 3 2^-48
 // (|COM_A|_1 + |COM_B|_1) per component (u = 2^-24).  With NB, wmax gets the tile's largest
 // w = |o|_1 + |d_b|_1 + 2^-20 (|COM_A|_1 + |COM_B|_1) over candidate sources: the last term makes
@@ -315,8 +346,8 @@ struct NearTile {
 // rounding of the test, of q and of the neighbour filter.
 template <bool NB>
 __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0, int P, int nlist, int nr,
-                                     NearCursor &cur, const NearSmem<NB> &sm, float3 blo, float3 bhi, float HA,
-                                     float &wmax) {
+                                     NearCursor &cur, NearAhead &ah, const NearSmem<NB> &sm, float3 blo,
+                                     float3 bhi, float HA, float &wmax) {
     constexpr int kCap = kNearTile - kNearPad;
     constexpr int kU = (kCap + 31) / 32;  // slots per lane
     const int lane = threadIdx.x & 31;
@@ -328,16 +359,15 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0
     }
     const int k0 = cur.k0, kend = k0 < nr ? nr : nlist;  // the tile stays within one part
     const bool cand = k0 < nr;
-    const int k = k0 + lane;
+    const int k = k0 + lane;  // = ah.wk + lane
     int f = 0, n = 0;
     float ox = 0.f, oy = 0.f, oz = 0.f, ow = 0.f;
     if (k < kend) {
-        const int B = near_entry(c, base, nr, k);
         const float2 a0f = c.ncomdf[3 * (int64_t)A], a1f = c.ncomdf[3 * (int64_t)A + 1],
                      a2f = c.ncomdf[3 * (int64_t)A + 2];
-        f = c.nfirst[B];
-        n = c.ncount[B];
-        const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1], b2 = c.ncomdf[3 * (int64_t)B + 2];
+        f = ah.f;
+        n = ah.n;
+        const float2 b0 = ah.b0, b1 = ah.b1, b2 = ah.b2;
         ox = (b0.x - a0f.x) + (b0.y - a0f.y);
         oy = (b1.x - a1f.x) + (b1.y - a1f.y);
         oz = (b2.x - a2f.x) + (b2.y - a2f.y);
@@ -362,6 +392,11 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0
         if (lane > 0) n = 0;
         if (lane == 0) n = kCap;
         cur.off0 += kCap;
+    }
+    {  // the next tile's cells: entry cur.k0 + lane lies in the window (cur.k0 - k0 <= 32)
+        const int d = cur.k0 - k0 + lane;
+        const int e0 = __shfl_sync(0xffffffffu, ah.bw0, d & 31), e1 = __shfl_sync(0xffffffffu, ah.bw1, d & 31);
+        near_ahead_load(c, base, nr, nlist, cur.k0, d < 32 ? e0 : e1, true, ah);
     }
     excl = warp_excl_scan(n);
     // the slots in two halves of kU / 2 per lane: the gathers of a half are all issued before any
@@ -633,6 +668,9 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
         // the box of the sink cell's particles (float32 offsets from its centre of mass) and H_A
         float3 blo = make_float3(3e38f, 3e38f, 3e38f), bhi = make_float3(-3e38f, -3e38f, -3e38f);
         float HA = 0.f;
+        // the first tile's cells, loaded alongside the sink's particles
+        NearAhead ah;
+        near_ahead_load(c, (int64_t)s * c.cap_near, nr, nlist, 0, 0, false, ah);
         for (int i = lane; i < nA; i += 32) {
             const float4 pa = c.p32[fA + i];
             blo = make_float3(fminf(blo.x, pa.x), fminf(blo.y, pa.y), fminf(blo.z, pa.z));
@@ -680,9 +718,11 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
             L.dummy = sm.rowcnt + 32 + lane;
             L.nsub = 0;
             NearCursor cur{0, 0};
+            if (a0 > 0) near_ahead_load(c, (int64_t)s * c.cap_near, nr, nlist, 0, 0, false, ah);
             for (;;) {
                 float wmax = 0.f;
-                const NearTile tl = stage_near_mixed<NB>(c, s, A, fA, a0, P, nlist, nr, cur, sm, blo, bhi, HA, wmax);
+                const NearTile tl =
+                    stage_near_mixed<NB>(c, s, A, fA, a0, P, nlist, nr, cur, ah, sm, blo, bhi, HA, wmax);
                 if (NB) {
                     const float F = wmax + (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z));
                     L.B = fmaf(F, F, L.h2) * 0x1p-19f + 1e-30f;
