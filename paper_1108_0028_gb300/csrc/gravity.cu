@@ -37,7 +37,6 @@ namespace rcb {
 namespace {
 
 constexpr int kGWarps = 4;
-constexpr int kGroupMixed = 8;  // sink particles per group (mixed near kernel)
 constexpr int kGroupF64 = 4;
 constexpr int kNearTileMixed = 1024;
 constexpr int kNearTileF64 = 384;
@@ -240,42 +239,38 @@ __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_
 constexpr int kNearWarps = 8;   // warps per block
 constexpr int kNearMinBlocks = 2;
 constexpr int kNearTile = 256;  // staged source slots per warp (even)
-constexpr int kNearPad = 2;     // slots kept free for padding the regions to even length
 constexpr int kFoldIters = 16;  // source pairs summed in float32 before a compensated fold
 
 // Shared memory of one warp: per source pair k, A[k], B[k], C[k] = (h_2k, h_2k+1, original
 // indices); with the neighbour rows (NB) also D[k] = (sorted indices, unused), the row buffer
-// (nb_rows.cuh), per-lane counts and the slot of each sink particle of the pass in the current
-// tile (-1 if not staged there).
+// (nb_rows.cuh) and per-lane counts; then the cell table of the tile being staged.
 template <bool NB>
 struct NearSmem {
     static constexpr int H = kNearTile / 2;  // source pairs per tile
-    static constexpr size_t bytes =
-        (size_t)H * (NB ? 4 : 3) * sizeof(float4) + (NB ? kRowBuf * sizeof(int32_t) + 64 * sizeof(int) : 0);
+    static constexpr size_t bytes = (size_t)H * (NB ? 4 : 3) * sizeof(float4) +
+                                    (NB ? kRowBuf * sizeof(int32_t) + 64 * sizeof(int) : 0) + 32 * sizeof(float4);
     float4 *P;      // A[H], B[H], C[H], D[H] (NB)
     int32_t *rows;  // NB: row buffer
     int *rowcnt;    // NB: [32] per-lane counts when a pass is handed over, then [32] dummy words
+    float4 *T;      // [32] cell table: offset of the cell's centre of mass, first particle - first slot
     __device__ NearSmem(unsigned char *p) {
         P = reinterpret_cast<float4 *>(p);
         rows = reinterpret_cast<int32_t *>(P + (NB ? 4 : 3) * H);
         rowcnt = rows + (NB ? kRowBuf : 0);
+        T = reinterpret_cast<float4 *>(rowcnt + (NB ? 64 : 0));
     }
     __device__ __forceinline__ float4 a(int k) const { return P[k]; }
     __device__ __forceinline__ float4 b(int k) const { return P[k + H]; }
     __device__ __forceinline__ float4 c(int k) const { return P[k + 2 * H]; }
     __device__ __forceinline__ const int4 *D() const { return reinterpret_cast<const int4 *>(P + 3 * H); }
-    // store source slot s: offset d (from the sink's centre of mass), mass, h, sorted and original
-    // index
-    __device__ __forceinline__ void put(int s, float dx, float dy, float dz, float m, float h, int idx, int oidx) const {
-        float *q = reinterpret_cast<float *>(P + (s >> 1));
-        const int u = s & 1;
-        q[u] = -dx;
-        q[2 + u] = -dy;
-        q[4 * H + u] = -dz;
-        q[4 * H + 2 + u] = -m;
-        q[8 * H + u] = h;
-        q[8 * H + 2 + u] = __int_as_float(oidx);
-        if (NB) reinterpret_cast<int *>(q)[12 * H + u] = idx;
+    // store source pair k: offsets v (from the sink's centre of mass), masses, h, original and
+    // sorted indices of both sources; the offsets and masses negated
+    __device__ __forceinline__ void put(int k, float3 v0, float3 v1, float m0, float m1, float h0, float h1, int o0,
+                                        int o1, int i0, int i1) const {
+        P[k] = make_float4(-v0.x, -v1.x, -v0.y, -v1.y);
+        P[k + H] = make_float4(-v0.z, -v1.z, -m0, -m1);
+        P[k + 2 * H] = make_float4(h0, h1, __int_as_float(o0), __int_as_float(o1));
+        if (NB) *reinterpret_cast<int2 *>(P + 3 * H + k) = make_int2(i0, i1);
     }
 };
 
@@ -285,9 +280,9 @@ struct NearCursor {
     int k0, off0;
 };
 
-// One staged tile: close sources in slots [0, nclose), of which [0, ncc) come from neighbour
-// candidates (reachable cells), far sources in [kNearTile - nfar, kNearTile); all three counts
-// are even (padding slots hold a massless source far away).
+// One staged tile: close source pairs in pair slots [0, nclose / 2), of which the first ncc / 2
+// come from neighbour candidates (reachable cells), far pairs in [H - nfar / 2, H); the counts
+// are in sources (even).
 struct NearTile {
     int nclose, ncc, nfar;
     bool last;  // no sources beyond this tile
@@ -323,33 +318,50 @@ __device__ __forceinline__ void near_ahead_load(const GCtx &c, int64_t base, int
     }
 }
 
+// Far test of one source at offset v with smoothing length hb (see stage_near_mixed).
+template <bool NB>
+__device__ __forceinline__ bool near_is_far(float3 v, float hb, float3 blo, float3 bhi, float HA) {
+    const float gx = fmaxf(fmaxf(blo.x - v.x, v.x - bhi.x), 0.f), gy = fmaxf(fmaxf(blo.y - v.y, v.y - bhi.y), 0.f),
+                gz = fmaxf(fmaxf(blo.z - v.z, v.z - bhi.z), 0.f);
+    const float g2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+    const float X = (NB ? fmaxf(HA + hb, HA + HA) : HA + hb) * (1.0f + 0x1p-10f);
+    return g2 > X * X;
+}
+
 // Stage the next tile of sink s (cell A, sorted particles [fA, fA + nA), this pass the P
 // particles from a0).  A tile is one batch of up to 32 near cells, all from the same part of the
-// list (reachable or not), as many whole cells as fit in kNearTile - kNearPad slots (part of one
-// cell if a single cell is larger).  The cells' descriptors (first particle, count, centre of
-// mass) arrive with ah, loaded during the previous tile's pair loops; once the batch is known, the
-// next tile's are loaded the same way.  Every lane then issues the gathers of half its slots
-// (lane + 32 u) before using any of them, so that a tile costs two rounds of memory latency;
-// each slot's float32 offset from the sink's centre of mass is formed and stored, close sources
-// from the front of the tile and far ones from the back.  The cell offset o is the double-float difference of the two
-// centres of mass: it differs from the float64 difference by at most 2u |dCOM| + 3 2^-48
-// (|COM_A|_1 + |COM_B|_1) per component (u = 2^-24).  With NB, wmax gets the tile's largest
-// w = |o|_1 + |d_b|_1 + 2^-20 (|COM_A|_1 + |COM_B|_1) over candidate sources: the last term makes
-// the representation error's share of the d^2 error at most 6 2^-28 F, well inside the neighbour
-// band.
+// list (reachable or not), as many whole cells as fit in kNearTile slots (part of one cell if a
+// single cell is larger).  The cells' descriptors (first particle, count, centre of mass) arrive
+// with ah, loaded during the previous tile's pair loops; once the batch is known, the next tile's
+// are loaded the same way.  The batch's cells go to a table in shared memory (offset of the
+// centre of mass, first particle minus first slot).  Each lane then takes the slots 2r and
+// 2r + 1 of pair slots r = lane + 32 u: it finds their cells from the cells' start bits, issues
+// the gathers of half its pairs before using any of them (a tile costs two rounds of memory
+// latency), forms each source's float32 offset from the sink's centre of mass and stores the
+// pair, far pairs (both sources far; a missing second source counts as far and is padded with a
+// massless source far away) from the back of the tile and the others from the front.  The cell
+// offset o is the double-float difference of the two centres of mass: it differs from the float64
+// difference by at most 2u |dCOM| + 3 2^-48 (|COM_A|_1 + |COM_B|_1) per component (u = 2^-24).
+// With NB, wmax gets a bound on the tile's largest w = |o|_1 + |d_b|_1 + 2^-20 (|COM_A|_1 +
+// |COM_B|_1) over candidate sources: the largest of the cell terms plus the largest |d_b|_1.  The
+// last cell term makes the representation error's share of the d^2 error at most 6 2^-28 F, well
+// inside the neighbour band.
 //
 // Far sources: with H_A the largest h_a of the sink's particles and the box [blo, bhi] of their
 // float32 offsets d_a, a source b whose distance g from the box exceeds X_b (1 + 2^-10) has
 // r_ab >= g > X_b for every sink particle a.  X_b = H_A + h_b puts all its pairs on the
 // Newtonian branch of Eq. 10 (q >= 2); with NB, X_b = max(H_A + h_b, 2 H_A) also keeps it out of
 // every sink particle's neighbour sphere (r < 2 h_a).  The 2^-10 margin is far above the float32
-// rounding of the test, of q and of the neighbour filter.
+// rounding of the test, of q and of the neighbour filter.  A close pair may hold one far source:
+// the close loop evaluates it on the Newtonian branch and never counts it as a neighbour.
 template <bool NB>
 __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0, int P, int nlist, int nr,
                                      NearCursor &cur, NearAhead &ah, const NearSmem<NB> &sm, float3 blo,
                                      float3 bhi, float HA, float &wmax) {
-    constexpr int kCap = kNearTile - kNearPad;
-    constexpr int kU = (kCap + 31) / 32;  // slots per lane
+    constexpr int kCap = kNearTile;
+    constexpr int H = NearSmem<NB>::H;
+    constexpr int kR = kNearTile / 64;  // rounds of 32 pair slots
+    constexpr int kH = kR / 2;          // rounds per half
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)s * c.cap_near;
@@ -399,70 +411,87 @@ __device__ NearTile stage_near_mixed(const GCtx &c, int s, int A, int fA, int a0
         near_ahead_load(c, base, nr, nlist, cur.k0, d < 32 ? e0 : e1, true, ah);
     }
     excl = warp_excl_scan(n);
-    // the slots in two halves of kU / 2 per lane: the gathers of a half are all issued before any
-    // is used
-    constexpr int kH = kU / 2;
+    float wc = 0.f;  // NB: the cell term of w
+    if (n > 0) {
+        sm.T[lane] = make_float4(ox, oy, oz, __int_as_float(f - excl));
+        if (NB) wc = ((fabsf(ox) + fabsf(oy)) + fabsf(oz)) + ow;
+    }
+    __syncwarp();
     float wl = 0.f;
-    int nclose = 0, nfar = 0;
+    int nclose = 0, nfar = 0;  // pair slots
 #pragma unroll 1
     for (int hh = 0; hh < 2; ++hh) {
-        int b[kH], cl[kH], ob[kH];
-        float4 pb[kH];
-        float hb[kH];
+        int cc0[kH], cc1[kH];
+        float4 pb0[kH], pb1[kH];
+        float hb0[kH], hb1[kH];
+        int ob0[kH], ob1[kH], ib0[kH], ib1[kH];
 #pragma unroll
         for (int u = 0; u < kH; ++u) {
-            const int r0 = 32 * (hh * kH + u), r = r0 + lane;
-            cl[u] = warp_run_of(excl, n, r0);
-            b[u] = __shfl_sync(0xffffffffu, f, cl[u]) + r - __shfl_sync(0xffffffffu, excl, cl[u]);
-            pb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            hb[u] = 0.f;
-            ob[u] = 0;
-            if (r < nslots) {
-                pb[u] = c.p32[b[u]];
-                hb[u] = c.h32[b[u]];
-                if (NB) ob[u] = c.pidx[b[u]];
+            const int w0 = 64 * (hh * kH + u), sl = w0 + 2 * lane;  // the round's and the lane's first slot
+            // the cells starting inside [w0, w0 + 64) as bits, and the number starting before it
+            const int st = excl - w0;
+            const bool in = n > 0 && st >= 0 && st < 64;
+            const unsigned lo = __reduce_or_sync(0xffffffffu, in && st < 32 ? 1u << (st & 31) : 0u);
+            const unsigned hi = __reduce_or_sync(0xffffffffu, in && st >= 32 ? 1u << (st & 31) : 0u);
+            const int before = __popc(__ballot_sync(0xffffffffu, n > 0 && st < 0));
+            const unsigned long long starts = ((unsigned long long)hi << 32) | lo;
+            const int bit = 2 * lane;
+            cc0[u] = min(31, max(0, before + __popcll(starts & ((2ull << bit) - 1ull)) - 1));
+            cc1[u] = min(31, cc0[u] + (int)((starts >> (bit + 1)) & 1ull));
+            pb0[u] = pb1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            hb0[u] = hb1[u] = 1.f;
+            ob0[u] = ob1[u] = ib0[u] = ib1[u] = -1;
+            if (sl < nslots) {
+                const int b = __float_as_int(sm.T[cc0[u]].w) + sl;
+                pb0[u] = c.p32[b];
+                hb0[u] = c.h32[b];
+                if (NB) {
+                    ib0[u] = b;
+                    ob0[u] = c.pidx[b];
+                }
+            }
+            if (sl + 1 < nslots) {
+                const int b = __float_as_int(sm.T[cc1[u]].w) + sl + 1;
+                pb1[u] = c.p32[b];
+                hb1[u] = c.h32[b];
+                if (NB) {
+                    ib1[u] = b;
+                    ob1[u] = c.pidx[b];
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < kH; ++u) {
-            const bool act = 32 * (hh * kH + u) + lane < nslots;
-            const float cx = __shfl_sync(0xffffffffu, ox, cl[u]), cy = __shfl_sync(0xffffffffu, oy, cl[u]),
-                        cz = __shfl_sync(0xffffffffu, oz, cl[u]);
-            const float cw = NB ? __shfl_sync(0xffffffffu, ow, cl[u]) : 0.f;
-            const float vx = cx + pb[u].x, vy = cy + pb[u].y, vz = cz + pb[u].z;
-            // squared distance from the source to the sink particles' box
-            const float gx = fmaxf(fmaxf(blo.x - vx, vx - bhi.x), 0.f), gy = fmaxf(fmaxf(blo.y - vy, vy - bhi.y), 0.f),
-                        gz = fmaxf(fmaxf(blo.z - vz, vz - bhi.z), 0.f);
-            const float g2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
-            const float X = (NB ? fmaxf(HA + hb[u], HA + HA) : HA + hb[u]) * (1.0f + 0x1p-10f);
-            const bool far = g2 > X * X;
+            const int sl = 64 * (hh * kH + u) + 2 * lane;
+            const bool act = sl < nslots, two = sl + 1 < nslots;
+            const float4 t0 = sm.T[cc0[u]], t1 = sm.T[cc1[u]];
+            const float3 v0 = make_float3(t0.x + pb0[u].x, t0.y + pb0[u].y, t0.z + pb0[u].z);
+            float3 v1 = make_float3(t1.x + pb1[u].x, t1.y + pb1[u].y, t1.z + pb1[u].z);
+            if (!two) v1 = make_float3(1e18f, 1e18f, 1e18f);
+            const bool far = near_is_far<NB>(v0, hb0[u], blo, bhi, HA) &&
+                             (!two || near_is_far<NB>(v1, hb1[u], blo, bhi, HA));
             const unsigned mc = __ballot_sync(0xffffffffu, act && !far);
             const unsigned mf = __ballot_sync(0xffffffffu, act && far);
             if (act) {
-                const int at = far ? kNearTile - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt);
-                sm.put(at, vx, vy, vz, pb[u].w, hb[u], b[u], ob[u]);
+                const int at = far ? H - 1 - (nfar + __popc(mf & lt)) : nclose + __popc(mc & lt);
+                sm.put(at, v0, v1, pb0[u].w, two ? pb1[u].w : 0.f, hb0[u], hb1[u], ob0[u], ob1[u], ib0[u], ib1[u]);
                 if (NB && cand)
-                    wl = fmaxf(wl, (fabsf(cx) + fabsf(cy) + fabsf(cz)) + fabsf(pb[u].x) + fabsf(pb[u].y) +
-                                       fabsf(pb[u].z) + cw);
+                    wl = fmaxf(wl, fmaxf((fabsf(pb0[u].x) + fabsf(pb0[u].y)) + fabsf(pb0[u].z),
+                                         (fabsf(pb1[u].x) + fabsf(pb1[u].y)) + fabsf(pb1[u].z)));
             }
             nclose += __popc(mc);
             nfar += __popc(mf);
         }
     }
-    if (nclose & 1) {
-        if (lane == 0) sm.put(nclose, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1, -1);
-        ++nclose;
-    }
-    if (nfar & 1) {
-        if (lane == 0) sm.put(kNearTile - 1 - nfar, 1e18f, 1e18f, 1e18f, 0.f, 1.f, -1, -1);
-        ++nfar;
-    }
     if (NB) {
-        for (int o = 16; o >= 1; o >>= 1) wl = fmaxf(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-        wmax = wl;
+        for (int o = 16; o >= 1; o >>= 1) {
+            wl = fmaxf(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+            wc = fmaxf(wc, __shfl_xor_sync(0xffffffffu, wc, o));
+        }
+        wmax = wc + wl;
     }
     __syncwarp();
-    return NearTile{nclose, cand ? nclose : 0, nfar, cur.k0 >= nlist};
+    return NearTile{2 * nclose, cand ? 2 * nclose : 0, 2 * nfar, cur.k0 >= nlist};
 }
 
 // Lane state of the mixed near field: the lane's sink particle (float32 offset from the sink's
