@@ -431,15 +431,20 @@ __global__ void k_level_finalize(Ctx c, int level, const int32_t *big, const int
                 loR[d] = min64(loR[d], shfl_xor_ll(loR[d], m));
                 hiR[d] = max64(hiR[d], shfl_xor_ll(hiR[d], m));
             }
+        // both children at once (lanes 0 and 1): the float64 work of write_cell costs the same
+        // per warp instruction with one active lane as with two
+        if (lane < 2) {
+            Red X = L;  // lane 0: the left child; lane 1: the right child
+            if (lane == 1) {
+                for (int q = 0; q < 4; ++q) X.S[q] = c.nS[4 * (int64_t)node + q] - L.S[q];
+                for (int d = 0; d < 3; ++d) { X.lo[d] = loR[d]; X.hi[d] = hiR[d]; }
+                X.n = cnt - L.n;
+            }
+            write_cell(c, 2 * node + lane, level + 1, lane == 0 ? f : f + L.n, X);
+        }
         if (lane == 0) {
-            Red R;
-            for (int q = 0; q < 4; ++q) R.S[q] = c.nS[4 * (int64_t)node + q] - L.S[q];
-            for (int d = 0; d < 3; ++d) { R.lo[d] = loR[d]; R.hi[d] = hiR[d]; }
-            R.n = cnt - L.n;
-            write_cell(c, 2 * node, level + 1, f, L);
-            write_cell(c, 2 * node + 1, level + 1, f + L.n, R);
             int kids[2] = {2 * node, 2 * node + 1};
-            int kn[2] = {L.n, R.n};
+            int kn[2] = {L.n, cnt - L.n};
             for (int s = 0; s < 2; ++s) {
                 if (kn[s] == 0) continue;
                 if (kn[s] > kTcta && level + 1 < c.L) {
@@ -656,6 +661,11 @@ struct SubtreeSmem {
     int64_t csplit[kTcta];
     int8_t caxis[kTcta];
     uint16_t newidx[2 * kTcta];
+    // reductions of the children larger than 32 particles (at most kTcta / 33 of them), written
+    // out together by one warp
+    Red bred[32];
+    int bci[32];
+    int nbred;
     int warp_tot[33];
     int nkids;
 };
@@ -863,7 +873,12 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
                 }
             }
             __syncthreads();
-            // 4. exact reductions of the children: a warp for large ones, a thread for small ones
+            // 4. exact reductions of the children: a warp for large ones (kept in shared memory),
+            // a thread for small ones; then the cells, one thread each: the float64 arithmetic of
+            // write_cell costs the same per warp instruction however few lanes are active, so the
+            // large cells' are written together by the last warp
+            if (tid == 0) s.nbred = 0;
+            __syncthreads();
             for (int ci = warp; ci < K2; ci += nwarps) {
                 int cn = s.ccount[nxt][ci];
                 if (cn <= 32) continue;
@@ -877,12 +892,19 @@ __global__ void __launch_bounds__(kCtaThreads, 2)
                 }
                 red_warp_allreduce(r);
                 if (lane == 0) {
-                    int node = s.cnode[nxt][ci];
-                    write_cell(c, node, level + 1, gfirst + f, r);
-                    if (level + 1 < c.L) {
-                        s.caxis[ci] = (int8_t)c.naxis[node];
-                        s.csplit[ci] = c.nsplitkey[node];
-                    }
+                    const int slot = atomicAdd(&s.nbred, 1);  // < 32: every such cell holds > 32 of <= kTcta
+                    s.bred[slot] = r;
+                    s.bci[slot] = ci;
+                }
+            }
+            __syncthreads();
+            if (tid >= nt - 32 && tid - (nt - 32) < s.nbred) {
+                const int slot = tid - (nt - 32), ci = s.bci[slot];
+                const int node = s.cnode[nxt][ci];
+                write_cell(c, node, level + 1, gfirst + s.cfirst[nxt][ci], s.bred[slot]);
+                if (level + 1 < c.L) {
+                    s.caxis[ci] = (int8_t)c.naxis[node];
+                    s.csplit[ci] = c.nsplitkey[node];
                 }
             }
             for (int ci = tid; ci < K2; ci += nt) {
