@@ -226,6 +226,46 @@ def idx_total_bytes(idx):
     return idx.numel() * idx.element_size()
 
 
+def memory_leg(rcb, a, xt, mt, ht):
+    """Device bytes per particle of each stage of the step, on a fresh tree (the library allocates
+    through torch's caching allocator, so torch's counters see every buffer): held after the call
+    and the peak during it, above what was held before.  The step's own outputs (accelerations,
+    potentials, CSR offsets and rows) are reported apart from the library's buffers."""
+    import torch
+    n = a.n
+
+    def held():
+        torch.cuda.synchronize()
+        return torch.cuda.memory_allocated()
+
+    base = held()
+    torch.cuda.reset_peak_memory_stats()
+    tree = rcb.RCBTree(xt, mt, ht, n_ll=N_LL, theta=a.theta, precision="mixed", split=a.split)
+    after_build = held()
+    peak_build = torch.cuda.max_memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    acc, pot, off, idx = tree.gravity_neighbours()
+    after_gn = held()
+    peak_gn = torch.cuda.max_memory_allocated()
+    outputs = sum(t.numel() * t.element_size() for t in (acc, pot, off, idx))
+    info = tree.info()
+    tree.free()
+    del acc, pot, off, idx, tree
+    return {
+        "unit": "B per particle",
+        "inputs": sum(t.numel() * t.element_size() for t in (xt, mt, ht)) / n,
+        "build_held": (after_build - base) / n,
+        "build_peak": (peak_build - base) / n,
+        "gravity_neighbours_library_held": (after_gn - after_build - outputs) / n,
+        "gravity_neighbours_peak": (peak_gn - after_build) / n,
+        "outputs": outputs / n,
+        "lists_entries_per_particle": {"near": info["near_total"] / n, "far": info["far_total"] / n},
+        "note": ("fresh tree after the timed region; build_held = tree arrays and the per-sink near/far "
+                 "lists; gravity_neighbours_library_held = far coefficients, the staged neighbour rows and "
+                 "their scratch; outputs = acc + pot (float64) and the CSR (int64 offsets, int32 rows)"),
+    }
+
+
 def split_variant_leg(rcb, a, split, xt, mt, ht, flush, acc_ref):
     """A tree cut by another rule of Sec. 2.1.3 on the same input: construction, walk and gravity
     times by the library's stage events, its list sizes, and its force difference from acc_ref
@@ -589,6 +629,9 @@ def run_ours(a, rank, world, local_rank):
                                                                        stream, step, barrier, ms, stage_ms)
         alu = rcb.alu_rates(SMS)
     clocks = sampler.stop() if sampler else None
+    tree.free()
+    del tree
+    memory = memory_leg(rcb, a, xt, mt, ht)
 
     if rank != 0:
         if dist is not None:
@@ -673,6 +716,7 @@ def run_ours(a, rank, world, local_rank):
         "tree": {k: info[k] for k in ("L", "nsinks", "near_total", "far_total", "reach_total", "near_pairs",
                                         "candidate_pairs", "walk_fp64_decisions", "smem_subtrees")},
         "neighbours_total": idx_total,
+        "memory": memory,
         "hbm_peak_gbs": hbm,
     }
     print(json.dumps(line), flush=True)
