@@ -259,10 +259,13 @@ def memory_leg(rcb, a, xt, mt, ht):
         "gravity_neighbours_library_held": (after_gn - after_build - outputs) / n,
         "gravity_neighbours_peak": (peak_gn - after_build) / n,
         "outputs": outputs / n,
+        "build_list_slots": info["nsinks"] * (info["cap_near"] + info["cap_far"]) * 4 / n,
         "lists_entries_per_particle": {"near": info["near_total"] / n, "far": info["far_total"] / n},
         "note": ("fresh tree after the timed region; build_held = tree arrays and the per-sink near/far "
-                 "lists; gravity_neighbours_library_held = far coefficients, the staged neighbour rows and "
-                 "their scratch; outputs = acc + pot (float64) and the CSR (int64 offsets, int32 rows)"),
+                 "list slots (build_list_slots: nsinks x (near + far capacity) int32, each capacity the "
+                 "longest list plus a margin); gravity_neighbours_library_held = far coefficients, the "
+                 "staged neighbour rows and their scratch; outputs = acc + pot (float64) and the CSR "
+                 "(int64 offsets, int32 rows)"),
     }
 
 

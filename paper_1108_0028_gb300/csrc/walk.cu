@@ -73,9 +73,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkCtx c) {
                 break;
             }
             bool open = false;
-            const float4 na = c.w32[2 * n];
+            // both halves of the node's 32-byte pack at once (one sector, one round of latency)
+            const float4 na = c.w32[2 * n], nb = c.w32[2 * n + 1];
             if (na.w >= 0.f) {  // non-empty
-                const float4 nb = c.w32[2 * n + 1];
                 const bool is_leaf = n >= leaf0;
                 // reachability
                 const float dx = rgA.x - na.x, dy = rgA.y - na.y, dz = rgA.z - na.z;
@@ -265,9 +265,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk_pair(WalkCtx c) {
             }
             if (skip0 && !in_subtree(n, skip0)) skip0 = 0;
             if (skip1 && !in_subtree(n, skip1)) skip1 = 0;
-            const float4 na = c.w32[2 * n];
+            // both halves of the node's 32-byte pack at once (one sector, one round of latency)
+            const float4 na = c.w32[2 * n], nb = c.w32[2 * n + 1];
             if (na.w >= 0.f) {  // non-empty
-                const float4 nb = c.w32[2 * n + 1];
                 const bool is_leaf = n >= leaf0;
                 const int a0 = skip0 ? 0 : wsink_visit(c, k0, n, na, nb, is_leaf, nfallback);
                 const int a1 = skip1 ? 0 : wsink_visit(c, k1, n, na, nb, is_leaf, nfallback);
