@@ -1005,7 +1005,7 @@ __device__ void parent_moments(const LeafCtx &c, int P) {
     c.nhnode[P] = 0.0;
 }
 
-// One thread per sink: Eq. 1, radii, float32 copies.  FP64 runs at 1/64 of FP32 on this GPU, so
+// One thread per sink: Eq. 1, radii, float32 copies.  FP64 runs at 1/66 of FP32 on this GPU, so
 // the float64 work per particle is kept small: the quadrupole accumulates with fused
 // multiply-adds (it is compared within a tolerance, not bit for bit), and the two radii are
 // exact maxima found from float32 estimates: every distance estimate has relative error below
@@ -1026,26 +1026,28 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
     float *__restrict__ h32 = c.h32;
     double com[3] = {c.ncom[3 * (int64_t)n], c.ncom[3 * (int64_t)n + 1], c.ncom[3 * (int64_t)n + 2]};
     double rg[3] = {c.nrg[3 * (int64_t)n], c.nrg[3 * (int64_t)n + 1], c.nrg[3 * (int64_t)n + 2]};
-    double Q[6] = {0, 0, 0, 0, 0, 0};
+    // Eq. 1 as Q = 3 S - tr(S) I with S = sum m d d^T: one multiply per axis and six fused
+    // multiply-adds per particle
+    double S[6] = {0, 0, 0, 0, 0, 0};
     float i1 = -1.f, i2 = -1.f, e1 = -1.f, e2 = -1.f;  // largest and second largest estimates
     int ai = f, a1 = f;
     for (int a = f; a < f + cnt; ++a) {
         const double x = px[a], y = py[a], z = pz[a], m = pm[a], h = ph[a];
         const double dx = __dsub_rn(x, com[0]), dy = __dsub_rn(y, com[1]), dz = __dsub_rn(z, com[2]);
-        const double dr2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        const double tx = 3.0 * m * dx, ty = 3.0 * m * dy, tz = 3.0 * m * dz, md = m * dr2;
-        Q[0] = fma(tx, dx, Q[0]) - md;
-        Q[1] = fma(tx, dy, Q[1]);
-        Q[2] = fma(tx, dz, Q[2]);
-        Q[3] = fma(ty, dy, Q[3]) - md;
-        Q[4] = fma(ty, dz, Q[4]);
-        Q[5] = fma(tz, dz, Q[5]) - md;
+        const double mx = m * dx, my = m * dy, mz = m * dz;
+        S[0] = fma(mx, dx, S[0]);
+        S[1] = fma(mx, dy, S[1]);
+        S[2] = fma(mx, dz, S[2]);
+        S[3] = fma(my, dy, S[3]);
+        S[4] = fma(my, dz, S[4]);
+        S[5] = fma(mz, dz, S[5]);
         // r_a - r_g in float64, rounded once to float32 per component (relative error 2^-24 each),
         // so the float32 distance has relative error below 2^-21
         const float gx = __double2float_rn(__dsub_rn(x, rg[0])), gy = __double2float_rn(__dsub_rn(y, rg[1])),
                     gz = __double2float_rn(__dsub_rn(z, rg[2]));
         const float dg = __fsqrt_rn(fmaf(gz, gz, fmaf(gy, gy, gx * gx)));
-        const float est = __fadd_rn(dg, __double2float_rn(__dmul_rn(2.0, h)));
+        const float hf = __double2float_rn(h);
+        const float est = __fadd_rn(dg, 2.0f * hf);  // 2 RN(h) = RN(2 h) exactly
         if (dg > i1) {
             i2 = i1;
             i1 = dg;
@@ -1061,8 +1063,10 @@ __global__ void k_leaves_up(LeafCtx c, const int32_t *sinks, int nsinks) {
             e2 = est;
         }
         p32[a] = make_float4(__double2float_rn(dx), __double2float_rn(dy), __double2float_rn(dz), __double2float_rn(m));
-        h32[a] = __double2float_rn(h);
+        h32[a] = hf;
     }
+    const double tr = S[0] + S[3] + S[5];
+    const double Q[6] = {3.0 * S[0] - tr, 3.0 * S[1], 3.0 * S[2], 3.0 * S[3] - tr, 3.0 * S[4], 3.0 * S[5] - tr};
     double d2max = 0.0;
     const bool clear_i = i2 < __fmul_rn(i1, 1.0f - 0x1p-18f);
     for (int a = clear_i ? ai : f; a < (clear_i ? ai + 1 : f + cnt); ++a)

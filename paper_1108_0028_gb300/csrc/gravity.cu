@@ -715,9 +715,12 @@ __global__ void __launch_bounds__(kNearWarps * 32, kNearMinBlocks) k_near_mixed(
             bhi.z = fmaxf(bhi.z, __shfl_xor_sync(0xffffffffu, bhi.z, o));
             HA = fmaxf(HA, __shfl_xor_sync(0xffffffffu, HA, o));
         }
-        // passes of up to 32 sink particles (one pass unless the cell holds more)
-        for (int a0 = 0; a0 < nA; a0 += 32) {
-            const int P = min(32, nA - a0), S = 32 / P;
+        // passes of up to 32 sink particles (one pass unless the cell holds more); with the
+        // neighbour test the passes of nb_pass_len (at most 16 particles, two or more streams
+        // per row), which the direct fill of a queued pass repeats
+        const int Pp = NB ? nb_pass_len(nA) : 32;
+        for (int a0 = 0; a0 < nA; a0 += Pp) {
+            const int P = min(Pp, nA - a0), S = 32 / P;
             const int i = lane % P, j = lane / P;
             const bool active = j < S;
             const int a = fA + a0 + i;

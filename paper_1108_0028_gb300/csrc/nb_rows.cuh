@@ -18,6 +18,16 @@ namespace rcb {
 
 constexpr int kRowBuf = 1280;  // entries of a warp's shared-memory row buffer
 
+// Sink particles per pass of the neighbour test: at most 16, as even as possible
+// (ceil(nA / ceil(nA / 16)), the last pass shorter), so that every particle of a pass has at
+// least two source streams and its row is spread over two or more parts of the row buffer (in
+// the fused kernel, or at least 80 entries of it in the standalone one).  A pass is (sink,
+// first particle a0); every kernel that runs or re-runs a pass takes its length from here.
+__host__ __device__ inline int nb_pass_len(int nA) {
+    const int np = (nA + 15) >> 4;
+    return np > 0 ? (nA + np - 1) / np : 1;
+}
+
 // Where finished rows go.
 struct RowOut {
     int32_t *tmp;                    // compact staging buffer of rows (original indices)

@@ -240,7 +240,7 @@ __device__ void nb_pass(const NbCtx &c, const NbSmem<MODE> &sm, int s, int a0, i
         HA = fmaxf(HA, __shfl_xor_sync(kFull, HA, o));
     }
     const float Xcut = 2.0f * HA * (1.0f + 0x1p-10f);
-    const int P = min(32, nA - a0), S = 32 / P;
+    const int P = min(nb_pass_len(nA), nA - a0), S = 32 / P;
     const int i = lane % P, j = lane / P;
     const bool active = j < S;
     const int a = fA + a0 + i;
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kNbWarps * 32, 2) k_nb(NbCtx c) {
     } else {
         for (int s = blockIdx.x * kNbWarps + w; s < c.nsinks; s += gridDim.x * kNbWarps) {
             const int nA = c.ncount[c.sinks[s]];
-            for (int a0 = 0; a0 < nA; a0 += 32) nb_pass<MODE>(c, sm, s, a0, nfb);
+            for (int a0 = 0; a0 < nA; a0 += nb_pass_len(nA)) nb_pass<MODE>(c, sm, s, a0, nfb);
         }
     }
     for (int o = 16; o >= 1; o >>= 1) nfb += __shfl_xor_sync(kFull, nfb, o);
