@@ -78,35 +78,31 @@ __global__ void __launch_bounds__(kGWarps * 32) k_far(GCtx c) {
 #pragma unroll
             for (int i = 0; i < 20; ++i) C2[i] = make_float2(0.f, 0.f);
             const float4 ah = c.nfar[4 * (int64_t)A], al = c.nfar[4 * (int64_t)A + 1];
-            float4 p[2][4];
-            auto fetch = [&](int k0) {
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int k = k0 + 32 * u;
-                    if (k < nf) {
-                        const float4 *r = c.nfar + 4 * (int64_t)c.far_list[fb + k];
-                        p[u][0] = r[0];
-                        p[u][1] = r[1];
-                        p[u][2] = r[2];
-                        p[u][3] = r[3];
-                    } else {
-                        // no node: zero mass and quadrupole (its offset is set to (1, 0, 0) below)
-                        p[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        p[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        p[u][2] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        p[u][3] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-            };
+            // the list entries of a round are loaded one round ahead (their latency overlaps the
+            // arithmetic), the nodes' records at the start of their round
             int k = lane;
+            int B[2] = {k < nf ? c.far_list[fb + k] : -1, k + 32 < nf ? c.far_list[fb + k + 32] : -1};
             while (k < nf) {
-                fetch(k);
                 float4 q[2][4];
 #pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) q[u][e] = p[u][e];
+                for (int u = 0; u < 2; ++u) {
+                    if (B[u] >= 0) {
+                        const float4 *r = c.nfar + 4 * (int64_t)B[u];
+                        q[u][0] = r[0];
+                        q[u][1] = r[1];
+                        q[u][2] = r[2];
+                        q[u][3] = r[3];
+                    } else {
+                        // no node: zero mass and quadrupole (its offset is set to (1, 0, 0) below)
+                        q[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        q[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        q[u][2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        q[u][3] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
                 const int kn = k + 64;
+                B[0] = kn < nf ? c.far_list[fb + kn] : -1;
+                B[1] = kn + 32 < nf ? c.far_list[fb + kn + 32] : -1;
                 const bool second = k + 32 < nf;
                 const float2 x0 = make_float2((ah.x - q[0][0].x) + (al.x - q[0][1].x),
                                               second ? (ah.x - q[1][0].x) + (al.x - q[1][1].x) : 1.f);
