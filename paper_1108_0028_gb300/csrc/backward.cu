@@ -1010,28 +1010,24 @@ int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double
     cudaStream_t st = t->stream;
     const int64_t N = t->N, nn = t->nn, nl = t->nleaves;
     if (t->nsinks == 0) return RCB_OK;
-    // scratch, allocated on the first backward after a build (through the tree's allocator)
+    // scratch, through the tree's allocator: kept across builds and grown when a build needs more
+    // (the transposed near list's entries are known only after its count, below)
+    const size_t adj_bytes = (size_t)nn * 10 * sizeof(double) + (size_t)N * 8 * sizeof(double) +
+                             (size_t)t->nsinks * 20 * sizeof(double) + (size_t)N * sizeof(float4) +
+                             (size_t)t->nsinks * 20 * sizeof(float);
+    auto grow = [&](void **q, int64_t &cap, int64_t need, size_t elem) {
+        if (*q && cap >= need) return true;
+        dev_free(t, *q);
+        *q = dev_alloc(t, (size_t)std::max<int64_t>(need, 1) * elem);
+        cap = *q ? need : 0;
+        return *q != nullptr;
+    };
     if (!t->bwd_valid) {
-        dev_free(t, t->tnear_off);
-        dev_free(t, t->tnear_sink);
-        dev_free(t, t->tfar_off);
-        dev_free(t, t->tfar_sink);
-        dev_free(t, t->adj);
-        int64_t total = 0;
-        {
-            // total near entries
-            int64_t info[16];
-            if (rcb_tree_info(t, info) != RCB_OK) return RCB_ERR_CUDA;
-            total = info[7];
-        }
-        t->tnear_off = (int32_t *)dev_alloc(t, (nl + 1) * sizeof(int32_t));
-        t->tnear_sink = (int32_t *)dev_alloc(t, std::max<int64_t>(total, 1) * sizeof(int32_t));
-        t->tfar_off = (int32_t *)dev_alloc(t, std::max<int64_t>(nl, 1) * sizeof(int32_t));   // cursor scratch
-        t->tfar_sink = (int32_t *)dev_alloc(t, N * sizeof(int32_t));                          // leaf of each particle
-        t->adj = (double *)dev_alloc(t, (size_t)nn * 10 * sizeof(double) + (size_t)N * 8 * sizeof(double) +
-                                            (size_t)t->nsinks * 20 * sizeof(double) + (size_t)N * sizeof(float4) +
-                                            (size_t)t->nsinks * 20 * sizeof(float));
-        if (!t->tnear_off || !t->tnear_sink || !t->tfar_off || !t->tfar_sink || !t->adj) return RCB_ERR_ALLOC;
+        if (!grow((void **)&t->tnear_off, t->cap_bwd_off, nl + 1, sizeof(int32_t)) ||
+            !grow((void **)&t->tfar_off, t->cap_bwd_cur, nl + 1, sizeof(int32_t)) ||
+            !grow((void **)&t->tfar_sink, t->cap_bwd_N, N, sizeof(int32_t)) ||
+            !grow((void **)&t->adj, t->cap_bwd_adj, (int64_t)adj_bytes, 1))
+            return RCB_ERR_ALLOC;
     }
     double *adj = t->adj;
     double *gxs = adj + nn * 10;
@@ -1096,6 +1092,13 @@ int gravity_backward(rcb_tree *t, const double *gacc, const double *gpot, double
         k_tnear_count<<<gridw, kBW * 32, 0, st>>>(c, cnt); note_launch();
         int rc = scan_i32(cnt, t->tnear_off, nl, t->tnear_off + nl, t->scan_tmp, st);
         if (rc) return rc;
+        // the number of entries, through the mapped status words (no pageable copy)
+        rc = copy_words(t->h_status_dev + ST_NWORDS + 4, t->tnear_off + nl, 1, st);
+        if (rc) return rc;
+        RCB_CUDA_TRY(cudaStreamSynchronize(st));
+        const int64_t total = t->h_status[ST_NWORDS + 4];
+        if (!grow((void **)&t->tnear_sink, t->cap_bwd_sink, total, sizeof(int32_t))) return RCB_ERR_ALLOC;
+        c.tnear_sink = t->tnear_sink;
         RCB_CUDA_TRY(cudaMemcpyAsync(cnt, t->tnear_off, nl * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         k_tnear_fill<<<gridw, kBW * 32, 0, st>>>(c, cnt, t->tnear_sink); note_launch();
         k_tnear_sort<<<(int)std::max<int64_t>(1, std::min<int64_t>((nl + 255) / 256, (int64_t)nsm * 16)), 256, 0, st>>>(

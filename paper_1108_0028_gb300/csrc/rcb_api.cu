@@ -105,6 +105,7 @@ void release_arrays(rcb_tree *t) {
     t->cap_near = t->cap_far = 0;
     t->cap_lists_near = t->cap_lists_far = 0;
     t->cap_tmp = 0;
+    t->cap_bwd_off = t->cap_bwd_cur = t->cap_bwd_sink = t->cap_bwd_N = t->cap_bwd_adj = 0;
 }
 
 int allocate_arrays(rcb_tree *t, int64_t N, int L) {

@@ -283,6 +283,9 @@ struct rcb_tree {
     // backward
     int32_t *tnear_off, *tnear_sink, *tfar_off, *tfar_sink;
     int bwd_valid;
+    // capacities of the backward scratch (kept across builds, grown when a build needs more):
+    // entries of tnear_off, tfar_off, tnear_sink and tfar_sink, bytes of adj
+    int64_t cap_bwd_off, cap_bwd_cur, cap_bwd_sink, cap_bwd_N, cap_bwd_adj;
     double *ones;     // unit weights for the centre-of-number split (cap_N)
     // median position split: per large cell of a level, a 256-bin digit histogram, the key prefix
     // chosen so far and the rank still sought (cap_N / (kTcta + 1) + 2 cells)
