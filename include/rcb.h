@@ -218,8 +218,7 @@ int rcb_density(rcb_tree *tree, const int64_t *offsets, const int32_t *idx, doub
  *   device current and keeps its address for the life of the process (the device's primary
  *   context must stay alive: no cudaDeviceReset in between).  All calls share the one array, so
  *   calls that overlap on the GPU (other streams, other threads) race: serialise them.
- *   The call reads the total back and synchronises `stream`; it cannot be made while the stream
- *   is being captured into a CUDA graph.
+ *   The call reads the total back to the host and synchronises `stream` before it returns.
  */
 int rcb_neighbour_offsets_noalloc(rcb_tree *tree, int64_t *offsets, int64_t *needed, void *stream);
 

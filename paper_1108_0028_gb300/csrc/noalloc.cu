@@ -7,8 +7,7 @@
 // same offsets without any allocation: the count pass writes straight into the caller's offsets
 // array, and the only other scratch, the exclusive scan's per-tile sums plus the status words,
 // lives in the fixed-size array below, compiled into the library and reused by every call.  The
-// call reads the total back and synchronises its stream, so it cannot be recorded into a CUDA
-// graph.
+// call reads the total back to the host and synchronises its stream before it returns.
 #include <cuda_runtime.h>
 
 #include <mutex>
