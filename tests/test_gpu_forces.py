@@ -264,3 +264,37 @@ def test_neighbour_ties_on_a_lattice(bump, precision):
     plain = rcb.RCBTree(*_gpu(x, m, h), theta=0.6, precision=precision)
     po, pi = plain.neighbours()
     assert np.array_equal(po.cpu().numpy(), ro) and np.array_equal(pi.cpu().numpy(), ri)
+
+
+def test_clustered_leaves_split_into_passes():
+    # tight clusters of 33-70 particles (spread 1e-6, far below the cell sizes the fixed depth
+    # reaches) each end up in one ll-cell: the neighbour test runs such a sink in passes of at
+    # most 16 particles, their rows (the whole cluster plus the usual ~50) outgrow the
+    # shared-memory slices and go to the direct fill.  Rows bit-exact, forces within the bounds,
+    # through the fused pass and through rcb_neighbours alone.
+    import paper_1108_0028_gb300 as rcb
+    x, m, h = synth.make_particles("sphere", 20000, synth.seed_for(4, 401), "loguniform10")
+    rng = np.random.default_rng(401)
+    xs, ms, hs = [x], [m], [h]
+    for c, k in zip(x[rng.choice(len(x), 6, replace=False)], (33, 40, 47, 55, 63, 70)):
+        xs.append(c + 1e-6 * rng.standard_normal((k, 3)))
+        ms.append(np.full(k, m.mean()))
+        hs.append(np.full(k, np.median(h)))
+    x, m, h = np.concatenate(xs), np.concatenate(ms), np.concatenate(hs)
+    ref = oracle.OracleTree(x, m, h)
+    ref.walk(0.7)
+    assert np.bincount(ref.leaf_of()).max() > 64
+    ro, ri = ref.neighbours()
+    assert np.diff(ro).max() > 100
+    oa, _ = ref.gravity()
+    for precision in ("mixed", "fp64"):
+        tree = rcb.RCBTree(*_gpu(x, m, h), theta=0.7, precision=precision)
+        ga, _, go, gi = tree.gravity_neighbours()
+        assert np.array_equal(go.cpu().numpy(), ro) and np.array_equal(gi.cpu().numpy(), ri)
+        e = rel_errors(ga.cpu().numpy(), oa)
+        rms_b, p999_b = (FP64_RMS, FP64_P999) if precision == "fp64" else (MIXED_RMS, MIXED_P999)
+        assert np.sqrt(np.mean(e ** 2)) < rms_b and np.quantile(e, 0.999) < p999_b
+        tree.free()
+    tree = rcb.RCBTree(*_gpu(x, m, h), theta=0.7)
+    no, ni = tree.neighbours()
+    assert np.array_equal(no.cpu().numpy(), ro) and np.array_equal(ni.cpu().numpy(), ri)
