@@ -173,7 +173,7 @@ def test_precision_switch_on_one_tree():
 FUSED_CASES = [
     ("plummer", 4096, "equal", 0.5, 1.0),
     ("sphere", 20000, "loguniform10", 0.7, 1.0),
-    ("sphere", 30000, "loguniform10", 0.6, 3.0),   # every 37th h x3: rows past the 128 slots
+    ("sphere", 30000, "loguniform10", 0.6, 3.0),   # every 37th h x3: rows of several hundred entries
     ("cube", 5000, "loguniform10", 0.0, 1.0),      # theta = 0: everything in the near list
 ]
 
