@@ -660,10 +660,17 @@ struct SubtreeSmem {
     uint16_t cfirst[2][kTcta], ccount[2][kTcta];
     int64_t csplit[kTcta];
     int8_t caxis[kTcta];
-    uint16_t newidx[2 * kTcta];
-    // reductions of the children larger than 32 particles (at most kTcta / 33 of them), written
-    // out together by one warp
-    Red bred[32];
+    union {
+        struct {
+            uint16_t newidx[2 * kTcta];
+            // reductions of the children larger than 32 particles (at most kTcta / 33 of them),
+            // written out together by one warp
+            Red bred[32];
+        };
+        // median split: every particle's key along its cell's axis, by position (newidx and
+        // bred are dead whenever subtree_median runs)
+        int64_t mkey[kTcta];
+    };
     int bci[32];
     int nbred;
     int warp_tot[33];
@@ -715,15 +722,20 @@ struct Bufs {
 // along its cell's axis, ties broken by position; the particle of rank floor(n/2) writes its key
 // as the cell's split (exactly one per cell).
 __device__ void subtree_median(const Ctx &c, SubtreeSmem &s, int cur, int n) {
+    // the keys first, in position order, so that the rank count reads one key per comparison
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int ax = s.caxis[s.cellOf[cur][p]];
+        const double *coord = ax == 0 ? s.x : (ax == 1 ? s.y : s.z);
+        s.mkey[p] = dkey(coord[s.perm[cur][p]]);
+    }
+    __syncthreads();
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
         const int ci = s.cellOf[cur][p];
         const int f = s.cfirst[cur][ci], cn = s.ccount[cur][ci];
-        const int ax = s.caxis[ci];
-        const double *coord = ax == 0 ? s.x : (ax == 1 ? s.y : s.z);
-        const int64_t kp = dkey(coord[s.perm[cur][p]]);
+        const int64_t kp = s.mkey[p];
         int below = 0;
         for (int q = f; q < f + cn; ++q) {
-            const int64_t kq = dkey(coord[s.perm[cur][q]]);
+            const int64_t kq = s.mkey[q];
             below += (kq < kp) || (kq == kp && q < p);
         }
         if (below == cn / 2) {
