@@ -63,6 +63,8 @@ def parse():
                    help="targets of the oracle's direct sum for accuracy_vs_direct")
     p.add_argument("--headline-only", action="store_true",
                    help="time only the headline step (no FP64 form, accuracy, e2e or CPU legs); for profiling")
+    p.add_argument("--table1", action="store_true",
+                   help="instead of the step: the scan of the mean ll-cell occupancy of Sec. 3.2.1 (Table 1)")
     return p.parse_args()
 
 
@@ -727,11 +729,66 @@ def run_ours(a, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_table1(a):
+    """The scan of Sec. 3.2.1 (Table 1) on the GPU: for each mean ll-cell occupancy N_ll, the tree
+    depth, the stage times of the build (construction and walk), of rcb_neighbours alone and of
+    rcb_gravity alone (near and far field), and the share of particles whose acceleration is within
+    1 % of the direct sum.  Input as in the table: a uniform sphere of 500,000 particles with h for
+    105 neighbours, theta = 0.7 (mixed form; seeded random positions stand in for the Sobol set).
+    Times are medians of library stage events over 5 repetitions after one warm-up."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1108_0028_gb300 as rcb
+    import synth
+    n = 500000
+    x, m, h = synth.make_particles("sphere", n, synth.seed_for(3, 7), "equal", n_neigh=105.0)
+    dev = torch.device("cuda", 0)
+    xt, mt, ht = (torch.from_numpy(v).to(dev) for v in (x, m, h))
+    oracle.build()
+    tg = np.sort(np.random.default_rng(11).choice(n, 4000, replace=False))
+    acc_dir, _ = oracle.direct(x, m, h, tg)
+    rows = []
+    for nll in (1, 3, 6, 12, 24, 48, 64, 128):
+        tree = rcb.RCBTree(xt, mt, ht, n_ll=nll, theta=0.7, precision="mixed", timing=True)
+        rec = {k: [] for k in ("construction", "walk", "neighbours", "near", "far", "gravity")}
+        for r in range(6):
+            tree.rebuild(xt, mt, ht)
+            st_b = tree.stage_times()
+            _, idx = tree.neighbours()
+            st_n = tree.stage_times()
+            acc, _ = tree.gravity()
+            st_g = tree.stage_times()
+            if r == 0:
+                continue
+            rec["construction"].append(st_b["build"] - st_b["walk"])
+            rec["walk"].append(st_b["walk"])
+            rec["neighbours"].append(st_n["nb_count"] + st_n["nb_fill"])
+            rec["near"].append(st_g["near"])
+            rec["far"].append(st_g["far"])
+            rec["gravity"].append(st_g["near"] + st_g["far"])
+        info = tree.info()
+        e = rel_err_stats(acc.cpu().numpy()[tg], acc_dir)
+        ev = np.linalg.norm(acc.cpu().numpy()[tg] - acc_dir, axis=1) / np.linalg.norm(acc_dir, axis=1)
+        rows.append({"n_ll": nll, "L": info["L"], "p_below_1pct": float(np.mean(ev < 0.01)),
+                     "mean_rel_err": float(ev.mean()), "rms_rel_err": e["rms"],
+                     "ms": {k: float(statistics.median(v)) for k, v in rec.items()},
+                     "neighbours_per_particle": idx.numel() / n, "near_pairs": info["near_pairs"],
+                     "far_per_particle": info["far_total"] / n})
+        tree.free()
+    print(json.dumps({"table1": rows, "N": n, "theta": 0.7, "form": "mixed", "n_neigh_target": 105,
+                      "reference": "oracle direct sum at 4000 seeded targets"}), flush=True)
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.table1:
+        run_table1(a)
+        return
     if a.impl == "reference":
         run_reference(a, rank, world)
     else:
