@@ -78,6 +78,7 @@ def lib():
                 "orc_refit": (ctypes.c_int, [_P, _P, _P]),
                 "orc_update": (ctypes.c_int, [_P, _P, _P, _P, _P]),
                 "orc_walk_mac_only": (ctypes.c_int, [_P, ctypes.c_double]),
+                "orc_walk_bisection_box": (ctypes.c_int, [_P, ctypes.c_double]),
                 "orc_kernel_W": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
                 "orc_density_csr": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
                 "orc_gravity_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -284,9 +285,21 @@ class OracleTree:
             out[perm[f:f + c]] = j
         return out
 
-    def walk(self, theta: float, sinks=None, mac_only: bool = False) -> None:
+    def walk(self, theta: float, sinks=None, mac_only: bool = False, mac_box: str = "tight") -> None:
         """mac_only: near lists from the MAC alone (Sec. 2.5 variant); every sink is walked and the
-        lists hold no neighbour candidates."""
+        lists hold no neighbour candidates.  mac_box="bisection": Eq. 4's cell size taken from each
+        cell's bisection box instead of the tight box of its particles (the other reading of the
+        cell size, for comparison; every sink is walked)."""
+        if mac_box == "bisection":
+            if sinks is not None or mac_only:
+                raise ValueError("the bisection-box walk covers every sink with the default rules")
+            r = lib().orc_walk_bisection_box(self._t, float(theta))
+            if r != OK:
+                raise RuntimeError(f"oracle walk failed: {r}")
+            self.walked = True
+            return
+        if mac_box != "tight":
+            raise ValueError(f"unknown mac_box {mac_box!r}")
         if mac_only:
             if sinks is not None:
                 raise ValueError("the MAC-only walk covers every sink")

@@ -67,6 +67,10 @@ typedef struct {
     double *split;
     i128 *S[3], *Msum;
     double *mass, *com[3], *bmin[3], *bmax[3], *rg[3], *H, *hint, *hnode, *Q[6];
+    /* for comparing readings of Eq. 4 only: the longest side of each cell's bisection box, and
+     * whether the walk reads it in place of H (see orc_walk_bisection_box) */
+    double *Hbis;
+    int mac_box;
     /* interaction lists, indexed by leaf number j = node - 2^L */
     int walked;
     double theta;
@@ -410,7 +414,7 @@ void orc_free(orc_tree *t) {
     if (t->L > 0) free_lists(t);
     free(t->perm); free(t->m); free(t->h); free(t->Pm);
     free(t->first); free(t->count); free(t->axis); free(t->split); free(t->Msum);
-    free(t->mass); free(t->H); free(t->hint); free(t->hnode);
+    free(t->mass); free(t->H); free(t->hint); free(t->hnode); free(t->Hbis);
     for (int d = 0; d < 3; ++d) {
         free(t->x[d]); free(t->P[d]); free(t->S[d]); free(t->com[d]);
         free(t->bmin[d]); free(t->bmax[d]); free(t->rg[d]);
@@ -506,7 +510,8 @@ static int walk_sink(const orc_tree *t, int64_t A, double theta2, int mac_only, 
                 else descend = 1;
             } else {
                 double R2 = dist2(t->com[0][A], t->com[1][A], t->com[2][A], t->com[0][n], t->com[1][n], t->com[2][n]);
-                if (t->H[n] * t->H[n] < theta2 * R2) { if (vpush(far, (int32_t)n, 0)) return ORC_ERR_ALLOC; }
+                const double Hn = t->mac_box ? t->Hbis[n] : t->H[n];
+                if (Hn * Hn < theta2 * R2) { if (vpush(far, (int32_t)n, 0)) return ORC_ERR_ALLOC; }
                 else if (is_leaf) { if (vpush(near, (int32_t)n, 0)) return ORC_ERR_ALLOC; }
                 else descend = 1;
             }
@@ -527,6 +532,40 @@ int orc_walk(orc_tree *t, double theta, const int32_t *sinks, int64_t nsinks) {
 }
 
 /* The MAC-only walk (Sec. 2.5): every sink, near lists without the reachability override. */
+/* The other reading of Eq. 4's cell size, for comparison (the library and the default walk read
+ * H_B from the tight box of the cell's particles): Sec. 2.1.5 keeps each node's lowest-left
+ * corner and size, which can also be read as the cell's bisection box, i.e. the root's tight box
+ * cut by the split planes of all its ancestors.  The walk below takes H_B as that box's longest
+ * side; everything else is the default walk. */
+int orc_walk_bisection_box(orc_tree *t, double theta) {
+    if (!t) return ORC_ERR_ARG;
+    int64_t nn = t->nn;
+    double *lo = xcalloc((size_t)(3 * nn), sizeof(double)), *hi = xcalloc((size_t)(3 * nn), sizeof(double));
+    free(t->Hbis);
+    t->Hbis = xcalloc((size_t)nn, sizeof(double));
+    if (!lo || !hi || !t->Hbis) { free(lo); free(hi); return ORC_ERR_ALLOC; }
+    for (int d = 0; d < 3; ++d) { lo[3 + d] = t->bmin[d][1]; hi[3 + d] = t->bmax[d][1]; }
+    for (int64_t n = 1; n < nn; ++n) {
+        double H = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            double e = hi[3 * n + d] - lo[3 * n + d];
+            if (e > H) H = e;
+        }
+        t->Hbis[n] = H;
+        if (2 * n + 1 < nn) { /* the daughters: the box cut at the split plane of the cell's axis */
+            for (int c = 0; c < 2; ++c)
+                for (int d = 0; d < 3; ++d) { lo[3 * (2 * n + c) + d] = lo[3 * n + d]; hi[3 * (2 * n + c) + d] = hi[3 * n + d]; }
+            hi[3 * (2 * n) + t->axis[n]] = t->split[n];
+            lo[3 * (2 * n + 1) + t->axis[n]] = t->split[n];
+        }
+    }
+    free(lo); free(hi);
+    t->mac_box = 1;
+    int r = walk_mode(t, theta, NULL, -1, 0);
+    t->mac_box = 0;
+    return r;
+}
+
 int orc_walk_mac_only(orc_tree *t, double theta) {
     return walk_mode(t, theta, NULL, -1, 1);
 }

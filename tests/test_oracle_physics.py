@@ -362,3 +362,30 @@ def test_median_split_error_tail_does_not_depend_on_theta():
     assert r0 < 1e-12
     assert r3 > 1e-3 and abs(r7 - r3) < 0.05 * r3, (r3, r7)
     assert rms(oracle.OracleTree(x, m, h), 0.7) < r7
+
+
+def test_mac_cell_size_readings():
+    # Eq. 4's H_B = MAX(S_i,B) read from the tight box of the cell's particles (the repository's
+    # reading) and from the cell's bisection box (the root's tight box cut by every ancestor's
+    # split plane; Sec. 2.1.5 keeps a corner and a size per node).  The bisection box is never
+    # smaller, so it opens more cells: longer near lists always, and on a uniform sphere a clearly
+    # smaller error against the direct sum; on a Plummer sphere the error barely moves while the
+    # near lists grow several-fold.
+    N = 20000
+    out = {}
+    for kind in ("sphere", "plummer"):
+        x, m, h = synth.make_particles(kind, N, synth.seed_for(9, 2), "equal")
+        tg = np.sort(np.random.default_rng(4).choice(N, 1500, replace=False))
+        ad, _ = oracle.direct(x, m, h, tg)
+        for box in ("tight", "bisection"):
+            t = oracle.OracleTree(x, m, h)
+            t.walk(0.7, mac_box=box)
+            a, _ = t.gravity()
+            e = np.linalg.norm(a[tg] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+            out[kind, box] = (float(e.mean()), float(np.mean(e < 2e-3)), len(t.lists()["near_ids"]))
+    print({f"{k[0]}/{k[1]}": v for k, v in out.items()})
+    # N = 20000: near entries x1.45 (sphere) and x2.9 (Plummer); mean error x0.70 and x0.99
+    assert out["sphere", "bisection"][2] > 1.3 * out["sphere", "tight"][2]
+    assert out["sphere", "bisection"][0] < 0.85 * out["sphere", "tight"][0]
+    assert out["plummer", "bisection"][2] > 2.5 * out["plummer", "tight"][2]
+    assert abs(out["plummer", "bisection"][0] - out["plummer", "tight"][0]) < 0.2 * out["plummer", "tight"][0]
