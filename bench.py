@@ -36,10 +36,10 @@ N_LL = 12
 FLOPS_PER_PAIR = 38        # float32 flops of one kernel-softened near-field pair, Eq. 10 with its potential (FMA = 2, MUFU = 1)
 FLOPS_PER_PAIR_NEWTON = 24  # the same pair on its Newtonian branch (q >= 2), the form most pairs take
 # DRAM bytes of one near-kernel launch at the headline workload: dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture at N = 2,097,152 (1,088,326,912 B for 1,038,400,525
+# dram__bytes_write.sum of one ncu capture at N = 2,097,152 (1,088,807,680 B for 1,038,400,525
 # pairs) scaled by the pair count to N = 4,194,304 (2,065,548,119 pairs).  Valid only for the
 # source it was taken on; any later change of gravity.cu reports null.
-NEAR_TRAFFIC = {"bytes": 2164859851, "gravity_cu_sha1": "e6cb56d882c2c250beee607f6432368039224683"}
+NEAR_TRAFFIC = {"bytes": 2165816177, "gravity_cu_sha1": "5fba030d72bbabd0aae346047f31157e9a41dfb4"}
 SMS = 152
 FP32_LANES = 128           # FP32 lanes per SM
 L2_FLUSH_BYTES = 256 << 20

@@ -38,7 +38,6 @@ namespace {
 
 constexpr int kGWarps = 4;
 constexpr int kGroupF64 = 4;
-constexpr int kNearTileMixed = 1024;
 constexpr int kNearTileF64 = 384;
 
 struct GCtx {
@@ -153,30 +152,19 @@ __device__ inline int near_entry(const GCtx &c, int64_t base, int nr, int k) {
     return k < nr ? c.near_list[base + k] : c.near_list[base + c.cap_near - 1 - (k - nr)];
 }
 
-// Stage sources [t0, t0 + tile) of the concatenated near cells.
-template <bool MIXED>
+// Stage sources [t0, t0 + tile) of the concatenated near cells (float64 near field).
 __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_t t0, int tile, void *smw) {
     const int lane = threadIdx.x & 31;
     const int64_t base = (int64_t)s * c.cap_near;
     int64_t pos = 0;
     int staged = 0;
-    float2 cA[3];
-    if (MIXED)
-        for (int d = 0; d < 3; ++d) cA[d] = c.ncomdf[3 * (int64_t)A + d];
     for (int k0 = 0; k0 < nlist; k0 += 32) {
         const int k = k0 + lane;
         int f = 0, n = 0;
-        float ox = 0.f, oy = 0.f, oz = 0.f;
         if (k < nlist) {
             const int B = near_entry(c, base, nr, k);
             f = c.nfirst[B];
             n = c.ncount[B];
-            if (MIXED) {
-                const float2 b0 = c.ncomdf[3 * (int64_t)B], b1 = c.ncomdf[3 * (int64_t)B + 1], b2 = c.ncomdf[3 * (int64_t)B + 2];
-                ox = (b0.x - cA[0].x) + (b0.y - cA[0].y);
-                oy = (b1.x - cA[1].x) + (b1.y - cA[1].y);
-                oz = (b2.x - cA[2].x) + (b2.y - cA[2].y);
-            }
         }
         int incl = n;
         for (int o = 1; o < 32; o <<= 1) {
@@ -189,30 +177,18 @@ __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_
             const int64_t c0 = __shfl_sync(0xffffffffu, my0, j);
             const int cn = __shfl_sync(0xffffffffu, n, j);
             const int cf = __shfl_sync(0xffffffffu, f, j);
-            const float bx = __shfl_sync(0xffffffffu, ox, j), by = __shfl_sync(0xffffffffu, oy, j),
-                        bz = __shfl_sync(0xffffffffu, oz, j);
             const int64_t lo = c0 > t0 ? c0 : t0;
             const int64_t hi = c0 + cn < t0 + tile ? c0 + cn : t0 + tile;
             for (int64_t q = lo + lane; q < hi; q += 32) {
                 const int b = cf + (int)(q - c0);
                 const int slot = (int)(q - t0);
-                if (MIXED) {
-                    float4 *src = reinterpret_cast<float4 *>(smw);
-                    float *hs = reinterpret_cast<float *>(src + kNearTileMixed);
-                    int32_t *si = reinterpret_cast<int32_t *>(hs + kNearTileMixed);
-                    const float4 pb = c.p32[b];
-                    src[slot] = make_float4(bx + pb.x, by + pb.y, bz + pb.z, pb.w);
-                    hs[slot] = c.h32[b];
-                    si[slot] = b;
-                } else {
-                    double *X = reinterpret_cast<double *>(smw);
-                    X[slot] = c.px[b];
-                    X[kNearTileF64 + slot] = c.py[b];
-                    X[2 * kNearTileF64 + slot] = c.pz[b];
-                    X[3 * kNearTileF64 + slot] = c.pm[b];
-                    X[4 * kNearTileF64 + slot] = c.ph[b];
-                    reinterpret_cast<int32_t *>(X + 5 * kNearTileF64)[slot] = b;
-                }
+                double *X = reinterpret_cast<double *>(smw);
+                X[slot] = c.px[b];
+                X[kNearTileF64 + slot] = c.py[b];
+                X[2 * kNearTileF64 + slot] = c.pz[b];
+                X[3 * kNearTileF64 + slot] = c.pm[b];
+                X[4 * kNearTileF64 + slot] = c.ph[b];
+                reinterpret_cast<int32_t *>(X + 5 * kNearTileF64)[slot] = b;
             }
             if (hi > lo) staged = max(staged, (int)(hi - t0));
         }
@@ -230,8 +206,9 @@ __device__ int stage_near(const GCtx &c, int s, int A, int nlist, int nr, int64_
 // walks the source pairs k = j, j + S, ... (j = l / P).  Every lane evaluates two sources at once
 // with paired float32 instructions (each half rounds as the scalar operation would) and keeps
 // its own totals, so nothing crosses lanes until the sink is finished.  Sources are stored by
-// pairs and negated, (-x_2k, -x_2k+1, -y_2k, -y_2k+1), (-z.., -m..), (h.., sorted index..), so
-// that every paired operand arrives from one shared-memory load.
+// pairs, positions and masses negated: (-x_2k, -x_2k+1, -y_2k, -y_2k+1), (-z.., -m..),
+// (h.., original indices..) and, for the neighbour test, the sorted indices, so that every paired
+// operand arrives from one shared-memory load.
 constexpr int kNearWarps = 8;   // warps per block
 constexpr int kNearMinBlocks = 2;
 constexpr int kNearTile = 256;  // staged source slots per warp (even)
@@ -851,7 +828,7 @@ __global__ void __launch_bounds__(kGWarps * 32) k_near_f64(GCtx c) {
                 int ns;
                 if (staged_all) ns = ns_all;
                 else {
-                    ns = stage_near<false>(c, s, A, nlist, nr, t0, kNearTileF64, smw);
+                    ns = stage_near(c, s, A, nlist, nr, t0, kNearTileF64, smw);
                     if (S <= kNearTileF64) {
                         staged_all = true;
                         ns_all = ns;

@@ -88,39 +88,6 @@ __device__ inline void warp_sort(int32_t (&v)[R]) {
     }
 }
 
-// The same network on each half-warp separately: 16 lanes x R keys per segment (shuffle
-// distances below 16 stay inside a half-warp), so two rows of up to 16 R entries sort at once.
-template <int R>
-__device__ inline void halfwarp_sort(int32_t (&v)[R]) {
-    const int hl = threadIdx.x & 15;
-#pragma unroll
-    for (int k = 2; k <= 16 * R; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 16) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int p = r ^ (j >> 4);
-                    if (p > r) {
-                        const bool up = ((r * 16 + hl) & k) == 0;
-                        const int32_t x = v[r], y = v[p];
-                        v[r] = up ? min(x, y) : max(x, y);
-                        v[p] = up ? max(x, y) : min(x, y);
-                    }
-                }
-            } else {
-                const bool lower = (hl & j) == 0;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int32_t y = __shfl_xor_sync(0xffffffffu, v[r], j);
-                    const bool up = ((r * 16 + hl) & k) == 0;
-                    v[r] = (lower == up) ? min(v[r], y) : max(v[r], y);
-                }
-            }
-        }
-    }
-}
-
 // The same network on each group of 8 lanes: 8 lanes x R keys per segment, so four rows of up to
 // 8 R entries sort at once.
 template <int R>
