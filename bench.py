@@ -63,6 +63,9 @@ def parse():
                    help="targets of the oracle's direct sum for accuracy_vs_direct")
     p.add_argument("--headline-only", action="store_true",
                    help="time only the headline step (no FP64 form, accuracy, e2e or CPU legs); for profiling")
+    p.add_argument("--presort", choices=["none", "morton"], default="none",
+                   help="permute the inputs into Morton order on the host before anything is timed "
+                        "(the A/B of a caller that keeps its particles in that order)")
     p.add_argument("--table1", action="store_true",
                    help="instead of the step: the scan of the mean ll-cell occupancy of Sec. 3.2.1 (Table 1)")
     return p.parse_args()
@@ -76,9 +79,64 @@ def workload_name(a):
 
 def bench_config(a, world):
     """The `config` object of the JSON line (both arms)."""
-    return {"workload": workload_name(a), "N": a.n, "theta": a.theta, "n_ll": N_LL, "form": "mixed", "split": a.split,
-            "parallelism": f"replicas x{world}",
-            "l2": "inputs (164 MB) exceed L2 and a 256 MB buffer is written between timed steps"}
+    cfg = {"workload": workload_name(a), "N": a.n, "theta": a.theta, "n_ll": N_LL, "form": "mixed", "split": a.split,
+           "parallelism": f"replicas x{world}",
+           "l2": "inputs (164 MB) exceed L2 and a 256 MB buffer is written between timed steps"}
+    if a.presort != "none":
+        cfg["presort"] = a.presort
+    return cfg
+
+
+def device_presort_ms(xt, mt, ht, reps=10):
+    """What the Morton presort would cost inside a step: keys, a device sort (torch) and the
+    gathers of x, m and h, timed with CUDA events (median of reps; the step itself does not
+    include it)."""
+    import torch
+
+    def presort():
+        lo, hi = xt.min(0).values, xt.max(0).values
+        q = ((xt - lo) / torch.where(hi > lo, hi - lo, torch.ones_like(hi)) * (2 ** 21 - 1)).to(torch.int64)
+
+        def spread(v):
+            v = v & 0x1fffff
+            for sh, mask in ((32, 0x1f00000000ffff), (16, 0x1f0000ff0000ff), (8, 0x100f00f00f00f00f),
+                             (4, 0x10c30c30c30c30c3), (2, 0x1249249249249249)):
+                v = (v | (v << sh)) & mask
+            return v
+
+        key = spread(q[:, 0]) | (spread(q[:, 1]) << 1) | (spread(q[:, 2]) << 2)
+        p = torch.argsort(key)
+        return xt[p], mt[p], ht[p]
+
+    for _ in range(3):
+        presort()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        presort()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def morton_order(x):
+    """Permutation that sorts the particles by their 63-bit Morton key (21 bits per axis of the
+    inputs' bounding box); used only to lay the inputs out in that order before timing."""
+    import numpy as np
+    lo, hi = x.min(0), x.max(0)
+    q = ((x - lo) / np.where(hi > lo, hi - lo, 1.0) * (2 ** 21 - 1)).astype(np.uint64)
+
+    def spread(v):
+        v = v & np.uint64(0x1fffff)
+        for sh, mask in ((32, 0x1f00000000ffff), (16, 0x1f0000ff0000ff), (8, 0x100f00f00f00f00f),
+                         (4, 0x10c30c30c30c30c3), (2, 0x1249249249249249)):
+            v = (v | (v << np.uint64(sh))) & np.uint64(mask)
+        return v
+
+    key = spread(q[:, 0]) | (spread(q[:, 1]) << np.uint64(1)) | (spread(q[:, 2]) << np.uint64(2))
+    return np.argsort(key, kind="stable")
 
 
 def max_over_ranks(value, dist, device):
@@ -183,9 +241,14 @@ def run_reference(a, rank, world):
     reported on its own (extrapolated_full_n_ms)."""
     if rank != 0:
         return
+    import numpy as np
+
     import oracle
     import synth
     x, m, h = synth.make_particles(a.kind, a.n, synth.seed_for(3, 0), a.mass)
+    if a.presort == "morton":
+        perm = morton_order(x)
+        x, m, h = (np.ascontiguousarray(v[perm]) for v in (x, m, h))
     oracle.build()
     t0 = time.perf_counter()
     T = oracle.OracleTree(x, m, h, n_ll=N_LL)
@@ -570,6 +633,7 @@ def extra_legs(a, world, dist, tree, x, m, h, xt, mt, ht, flush, stream, step, b
 
 
 def run_ours(a, rank, world, local_rank):
+    import numpy as np
     import torch
 
     import paper_1108_0028_gb300 as rcb
@@ -589,12 +653,18 @@ def run_ours(a, rank, world, local_rank):
 
     rcb.lib()
     x, m, h = synth.make_particles(a.kind, a.n, synth.seed_for(3, 0), a.mass)
+    if a.presort == "morton":
+        perm = morton_order(x)
+        x, m, h = (np.ascontiguousarray(v[perm]) for v in (x, m, h))
     xt = torch.from_numpy(x).to(dev)
     mt = torch.from_numpy(m).to(dev)
     ht = torch.from_numpy(h).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    presort_ms = None
+    if a.presort == "morton":
+        presort_ms = device_presort_ms(xt, mt, ht)
     tree = rcb.RCBTree(xt, mt, ht, n_ll=N_LL, theta=a.theta, precision="mixed", timing=True, split=a.split)
 
     def step():
@@ -722,6 +792,7 @@ def run_ours(a, rank, world, local_rank):
                                         "candidate_pairs", "walk_fp64_decisions", "smem_subtrees")},
         "neighbours_total": idx_total,
         "memory": memory,
+        "presort_device_ms": presort_ms,
         "hbm_peak_gbs": hbm,
     }
     print(json.dumps(line), flush=True)
